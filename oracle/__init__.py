@@ -1,0 +1,180 @@
+"""Plain FP64 CPU oracle for the manifold-corrected PN spinning-binary scan.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline / reference leg may import this package.  It shares
+no code with the CUDA library; see ``pn_oracle.c`` for the method and its
+citations (arXiv:1802.00147, Sec. 2 Eqs. 1-13, Sec. 3).
+"""
+import ctypes as _ct
+
+import numpy as _np
+
+from .build import build as _build
+
+_lib = None
+
+# per-orbit status numbering of the oracle
+RUNNING, DONE, MERGED, ESCAPED, FLI_SATURATED, NONFINITE = range(6)
+
+
+class Config(_ct.Structure):
+    _fields_ = [
+        ("pn_order", _ct.c_int), ("use_so", _ct.c_int), ("use_ss", _ct.c_int), ("use_qm", _ct.c_int),
+        ("correct", _ct.c_int),
+        ("newton_tol", _ct.c_double), ("newton_max", _ct.c_int), ("det_min", _ct.c_double),
+        ("fli_d0", _ct.c_double), ("fli_renorm", _ct.c_int), ("fli_cap", _ct.c_double),
+        ("r_merge", _ct.c_double), ("r_escape", _ct.c_double),
+    ]
+
+
+class Sys(_ct.Structure):
+    _fields_ = [
+        ("beta", _ct.c_double), ("m1", _ct.c_double), ("m2", _ct.c_double), ("eta", _ct.c_double),
+        ("kappa1", _ct.c_double), ("kappa2", _ct.c_double),
+        ("pn_order", _ct.c_int), ("use_so", _ct.c_int), ("use_ss", _ct.c_int), ("use_qm", _ct.c_int),
+    ]
+
+
+def config(pn_order=2, use_so=1, use_ss=1, use_qm=0, correct=1, newton_tol=1e-10,
+           newton_max=50, det_min=1e-5, fli_d0=1e-9, fli_renorm=100, fli_cap=0.0,
+           r_merge=6.0, r_escape=1e3):
+    return Config(pn_order, use_so, use_ss, use_qm, correct, newton_tol, newton_max,
+                  det_min, fli_d0, fli_renorm, fli_cap, r_merge, r_escape)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = _ct.CDLL(_build())
+        P = _ct.POINTER
+        d, i, i64 = _ct.c_double, _ct.c_int, _ct.c_int64
+        dp = P(d)
+        L.orc_sys_init.argtypes = [P(Sys), d, d, d, i, i, i, i]
+        for name in ("orc_H_newton", "orc_H_1pn", "orc_H_2pn", "orc_H_so", "orc_H_s1s2",
+                     "orc_H_qm", "orc_hamiltonian"):
+            f = getattr(L, name)
+            f.argtypes = [P(Sys), dp]
+            f.restype = d
+        L.orc_gradient.argtypes = [P(Sys), dp, dp]
+        L.orc_rhs.argtypes = [P(Sys), dp, dp]
+        L.orc_rk4_step.argtypes = [P(Sys), dp, d]
+        L.orc_integrals.argtypes = [P(Sys), dp, dp]
+        L.orc_correct.argtypes = [P(Sys), dp, dp, d, i, d, P(i), dp]
+        L.orc_correct.restype = i
+        L.orc_setup_cell.argtypes = [dp, dp]
+        L.orc_scan.argtypes = [i64, dp, dp, dp, dp, P(Config), d, i64, dp, dp, dp, dp,
+                               P(_ct.c_int32), dp, P(i64), P(_ct.c_int32), i]
+        L.orc_scan.restype = i
+        L.orc_trace.argtypes = [dp, d, d, d, P(Config), d, i64, i64, dp]
+        L.orc_trace.restype = i
+        L.orc_max_threads.restype = i
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(_ct.POINTER(_ct.c_double))
+
+
+def _vec(y):
+    return _np.ascontiguousarray(y, dtype=_np.float64)
+
+
+def system(beta, kappa1=1.0, kappa2=1.0, pn_order=2, use_so=1, use_ss=1, use_qm=0):
+    s = Sys()
+    lib().orc_sys_init(_ct.byref(s), float(beta), float(kappa1), float(kappa2),
+                       pn_order, use_so, use_ss, use_qm)
+    return s
+
+
+def hamiltonian(s, y, term="total"):
+    name = {"total": "orc_hamiltonian", "N": "orc_H_newton", "1PN": "orc_H_1pn",
+            "2PN": "orc_H_2pn", "SO": "orc_H_so", "S1S2": "orc_H_s1s2", "QM": "orc_H_qm"}[term]
+    y = _vec(y)
+    return getattr(lib(), name)(_ct.byref(s), _dp(y))
+
+
+def gradient(s, y):
+    y = _vec(y)
+    g = _np.zeros(12)
+    lib().orc_gradient(_ct.byref(s), _dp(y), _dp(g))
+    return g
+
+
+def rhs(s, y):
+    y = _vec(y)
+    dy = _np.zeros(12)
+    lib().orc_rhs(_ct.byref(s), _dp(y), _dp(dy))
+    return dy
+
+
+def rk4_step(s, y, h):
+    y = _vec(y).copy()
+    lib().orc_rk4_step(_ct.byref(s), _dp(y), float(h))
+    return y
+
+
+def integrals(s, y):
+    """(E, |J|, |S1|, |S2|, Jx, Jy, Jz)."""
+    y = _vec(y)
+    out = _np.zeros(7)
+    lib().orc_integrals(_ct.byref(s), _dp(y), _dp(out))
+    return out
+
+
+def correct(s, y, ref, newton_tol=1e-10, newton_max=50, det_min=1e-5):
+    """Returns (y_corrected, code, iters, (alpha, beta))."""
+    y = _vec(y).copy()
+    ref = _vec(ref)
+    it = _ct.c_int(0)
+    ab = _np.zeros(2)
+    code = lib().orc_correct(_ct.byref(s), _dp(y), _dp(ref), newton_tol, newton_max,
+                             det_min, _ct.byref(it), _dp(ab))
+    return y, code, it.value, (ab[0], ab[1])
+
+
+def setup_cells(cells):
+    """cells: (n, 9) = (x0, pfac, theta1, phi1, theta2, phi2, beta, chi1, chi2)."""
+    cells = _np.ascontiguousarray(cells, dtype=_np.float64).reshape(-1, 9)
+    out = _np.zeros((cells.shape[0], 12))
+    for i in range(cells.shape[0]):
+        lib().orc_setup_cell(_dp(cells[i]), _dp(out[i]))
+    return out
+
+
+def scan(y0, beta, h, nsteps, cfg=None, kappa1=None, kappa2=None, nthreads=0):
+    """Integrate n orbits with correction + FLI.  Returns a dict of arrays."""
+    cfg = cfg or config()
+    y0 = _np.ascontiguousarray(y0, dtype=_np.float64).reshape(-1, 12)
+    n = y0.shape[0]
+    beta = _np.ascontiguousarray(_np.broadcast_to(beta, (n,)), dtype=_np.float64)
+    k1 = None if kappa1 is None else _np.ascontiguousarray(_np.broadcast_to(kappa1, (n,)), dtype=_np.float64)
+    k2 = None if kappa2 is None else _np.ascontiguousarray(_np.broadcast_to(kappa2, (n,)), dtype=_np.float64)
+    out = dict(y=_np.zeros((n, 12)), ys=_np.zeros((n, 12)), integrals=_np.zeros((n, 6)),
+               fli=_np.zeros(n), status=_np.zeros(n, dtype=_np.int32), t_stop=_np.zeros(n),
+               newton_iters=_np.zeros(n, dtype=_np.int64), n_skip=_np.zeros(n, dtype=_np.int32))
+    P = _ct.POINTER
+    rc = lib().orc_scan(n, _dp(y0), _dp(beta),
+                        None if k1 is None else _dp(k1), None if k2 is None else _dp(k2),
+                        _ct.byref(cfg), float(h), int(nsteps),
+                        _dp(out["y"]), _dp(out["ys"]), _dp(out["integrals"]), _dp(out["fli"]),
+                        out["status"].ctypes.data_as(P(_ct.c_int32)), _dp(out["t_stop"]),
+                        out["newton_iters"].ctypes.data_as(P(_ct.c_int64)),
+                        out["n_skip"].ctypes.data_as(P(_ct.c_int32)), int(nthreads))
+    if rc != 0:
+        raise ValueError("orc_scan rejected its arguments")
+    return out
+
+
+def trace(y0, beta, h, nsteps, every=1, cfg=None, kappa1=1.0, kappa2=1.0):
+    cfg = cfg or config()
+    y0 = _vec(y0)
+    m = int(nsteps) // int(every)
+    out = _np.zeros((m, 12))
+    lib().orc_trace(_dp(y0), float(beta), float(kappa1), float(kappa2), _ct.byref(cfg),
+                    float(h), int(nsteps), int(every), _dp(out))
+    return out
+
+
+def max_threads():
+    return lib().orc_max_threads()

@@ -1,0 +1,509 @@
+/*
+ * pn_oracle.c -- plain, slow, obviously-correct FP64 CPU oracle.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by tests/, __graft_entry__.smoke() and
+ * bench.py's CPU-baseline / reference leg, never by the product path.  It
+ * shares no code with the CUDA library.  Compiled with -O2
+ * -ffp-contract=off: every + and * is a separately rounded IEEE operation.
+ *
+ * Method (arXiv:1802.00147):
+ *   Sec. 2, Eq. 1      H = H_N + H_1PN + H_2PN + H_SO + H_SS   (3PN and 2.5PN off)
+ *   Eqs. 3-5           spin-spin and quadrupole-monopole terms
+ *   Eq. 6              dr/dt = dH/dp, dp/dt = -dH/dr          (conservative)
+ *   Eqs. 7-9           dS_i/dt = Omega_i x S_i, Omega_i = dH/dS_i
+ *   Sec. 2, Eq. 10     spin lengths restored after every step
+ *   Eqs. 11-13         dual scaling p = alpha p*, r = beta r*, (alpha, beta)
+ *                      from E and |J| by Newton's method (Sec. 3A)
+ *   Sec. 3B/3C         FLI from two nearby trajectories (Wu et al. 2006)
+ *
+ * The orbital terms H_N, H_1PN, H_2PN and H_SO are not printed in the paper
+ * (Sec. 2 defers to Buonanno et al. 2006); they are the standard ADM
+ * expressions in reduced variables.  H_SO's coefficients are fixed by the
+ * L/r^3 terms of Eqs. 8-9; H_S1S2 and H_QM carry the 1/eta that Eqs. 8-9
+ * imply (spins in units of M^2).  The 1PN/2PN orbital coefficients are pinned
+ * by the gauge-invariant circular-orbit energy in tests/test_oracle_pins.py.
+ */
+#include "pn_oracle.h"
+#include <math.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---------------------------------------------------------------- vectors */
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const double *a, const double *b, double *c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+static double norm3(const double *a) { return sqrt(dot3(a, a)); }
+
+void orc_sys_init(orc_sys *s, double beta, double kappa1, double kappa2,
+                  int pn_order, int use_so, int use_ss, int use_qm)
+{
+    /* Sec. 2: m1 <= m2, beta = m1/m2, M = m1 + m2 = 1, eta = mu/M = m1 m2. */
+    s->beta = beta;
+    s->m1 = beta / (1.0 + beta);
+    s->m2 = 1.0 / (1.0 + beta);
+    s->eta = s->m1 * s->m2;
+    s->kappa1 = kappa1;
+    s->kappa2 = kappa2;
+    s->pn_order = pn_order;
+    s->use_so = use_so;
+    s->use_ss = use_ss;
+    s->use_qm = use_qm;
+}
+
+/* ------------------------------------------------------------ Hamiltonian */
+/* H_N = p^2/2 - 1/r */
+double orc_H_newton(const orc_sys *s, const double y[12])
+{
+    (void)s;
+    const double *r = y, *p = y + 3;
+    return 0.5 * dot3(p, p) - 1.0 / norm3(r);
+}
+
+/* H_1PN = (3 eta - 1) p^4 / 8 - [(3 + eta) p^2 + eta (n.p)^2] / (2 r) + 1/(2 r^2) */
+double orc_H_1pn(const orc_sys *s, const double y[12])
+{
+    const double *r = y, *p = y + 3;
+    double eta = s->eta, rr = norm3(r), p2 = dot3(p, p), np = dot3(r, p) / rr;
+    return (3.0 * eta - 1.0) * p2 * p2 / 8.0
+         - ((3.0 + eta) * p2 + eta * np * np) / (2.0 * rr)
+         + 1.0 / (2.0 * rr * rr);
+}
+
+/* H_2PN = (1 - 5 eta + 5 eta^2) p^6 / 16
+ *       + [(5 - 20 eta - 3 eta^2) p^4 - 2 eta^2 p^2 (n.p)^2 - 3 eta^2 (n.p)^4] / (8 r)
+ *       + [(5 + 8 eta) p^2 + 3 eta (n.p)^2] / (2 r^2)
+ *       - (1 + 3 eta) / (4 r^3) */
+double orc_H_2pn(const orc_sys *s, const double y[12])
+{
+    const double *r = y, *p = y + 3;
+    double eta = s->eta, rr = norm3(r), p2 = dot3(p, p), np = dot3(r, p) / rr;
+    return (1.0 - 5.0 * eta + 5.0 * eta * eta) * p2 * p2 * p2 / 16.0
+         + ((5.0 - 20.0 * eta - 3.0 * eta * eta) * p2 * p2
+            - 2.0 * eta * eta * p2 * np * np
+            - 3.0 * eta * eta * np * np * np * np) / (8.0 * rr)
+         + ((5.0 + 8.0 * eta) * p2 + 3.0 * eta * np * np) / (2.0 * rr * rr)
+         - (1.0 + 3.0 * eta) / (4.0 * rr * rr * rr);
+}
+
+/* Spin-orbit coefficients read off the L/r^3 terms of Eqs. 8-9. */
+static double g_so1(const orc_sys *s) { return 2.0 + 3.0 / (2.0 * s->beta); }
+static double g_so2(const orc_sys *s) { return 2.0 + 3.0 * s->beta / 2.0; }
+
+/* H_SO = (1/r^3) L . [(2 + 3/(2 beta)) S1 + (2 + 3 beta/2) S2],  L = r x p */
+double orc_H_so(const orc_sys *s, const double y[12])
+{
+    const double *r = y, *p = y + 3, *S1 = y + 6, *S2 = y + 9;
+    double L[3], rr = norm3(r);
+    cross3(r, p, L);
+    return (g_so1(s) * dot3(L, S1) + g_so2(s) * dot3(L, S2)) / (rr * rr * rr);
+}
+
+/* Eq. 3 with the 1/eta of Eqs. 8-9:  H_S1S2 = [3 (S1.n)(S2.n) - S1.S2] / (eta r^3) */
+double orc_H_s1s2(const orc_sys *s, const double y[12])
+{
+    const double *r = y, *S1 = y + 6, *S2 = y + 9;
+    double rr = norm3(r), n[3] = {r[0] / rr, r[1] / rr, r[2] / rr};
+    return (3.0 * dot3(S1, n) * dot3(S2, n) - dot3(S1, S2)) / (s->eta * rr * rr * rr);
+}
+
+/* Eqs. 4-5 with the 1/eta of Eqs. 8-9 and multipliers kappa_i:
+ * H_QM = kappa1 [3 (S1.n)^2 - S1^2] / (2 beta eta r^3)
+ *      + kappa2 beta [3 (S2.n)^2 - S2^2] / (2 eta r^3) */
+double orc_H_qm(const orc_sys *s, const double y[12])
+{
+    const double *r = y, *S1 = y + 6, *S2 = y + 9;
+    double rr = norm3(r), n[3] = {r[0] / rr, r[1] / rr, r[2] / rr};
+    double a1 = dot3(S1, n), a2 = dot3(S2, n), r3 = rr * rr * rr;
+    return s->kappa1 * (3.0 * a1 * a1 - dot3(S1, S1)) / (2.0 * s->beta * s->eta * r3)
+         + s->kappa2 * s->beta * (3.0 * a2 * a2 - dot3(S2, S2)) / (2.0 * s->eta * r3);
+}
+
+/* Eq. 1 (conservative part, 3PN not given). */
+double orc_hamiltonian(const orc_sys *s, const double y[12])
+{
+    double H = orc_H_newton(s, y);
+    if (s->pn_order >= 1) H += orc_H_1pn(s, y);
+    if (s->pn_order >= 2) H += orc_H_2pn(s, y);
+    if (s->use_so) H += orc_H_so(s, y);
+    if (s->use_ss) H += orc_H_s1s2(s, y);
+    if (s->use_qm) H += orc_H_qm(s, y);
+    return H;
+}
+
+/* --------------------------------------------------------------- gradient */
+/* The orbital terms depend on (p2 = p.p, np = n.p, rr = |r|):
+ *   dH/dp = 2 H_p2 p + H_np n
+ *   dH/dr = H_rr n + H_np (p - np n) / rr
+ * Spin terms are differentiated directly, with d(S.n)/dr = (S - (S.n) n)/rr. */
+void orc_gradient(const orc_sys *s, const double y[12], double g[12])
+{
+    const double *r = y, *p = y + 3, *S1 = y + 6, *S2 = y + 9;
+    double eta = s->eta;
+    double rr = norm3(r), n[3] = {r[0] / rr, r[1] / rr, r[2] / rr};
+    double p2 = dot3(p, p), np = dot3(n, p);
+    double H_p2, H_np, H_rr;
+    int i;
+
+    /* H_N */
+    H_p2 = 0.5;
+    H_np = 0.0;
+    H_rr = 1.0 / (rr * rr);
+    /* H_1PN */
+    if (s->pn_order >= 1) {
+        H_p2 += (3.0 * eta - 1.0) * 2.0 * p2 / 8.0 - (3.0 + eta) / (2.0 * rr);
+        H_np += -eta * np / rr;
+        H_rr += ((3.0 + eta) * p2 + eta * np * np) / (2.0 * rr * rr) - 1.0 / (rr * rr * rr);
+    }
+    /* H_2PN */
+    if (s->pn_order >= 2) {
+        double c4 = 5.0 - 20.0 * eta - 3.0 * eta * eta;
+        H_p2 += 3.0 * (1.0 - 5.0 * eta + 5.0 * eta * eta) * p2 * p2 / 16.0
+              + (2.0 * c4 * p2 - 2.0 * eta * eta * np * np) / (8.0 * rr)
+              + (5.0 + 8.0 * eta) / (2.0 * rr * rr);
+        H_np += (-4.0 * eta * eta * p2 * np - 12.0 * eta * eta * np * np * np) / (8.0 * rr)
+              + 3.0 * eta * np / (rr * rr);
+        H_rr += -(c4 * p2 * p2 - 2.0 * eta * eta * p2 * np * np - 3.0 * eta * eta * np * np * np * np)
+                    / (8.0 * rr * rr)
+              - ((5.0 + 8.0 * eta) * p2 + 3.0 * eta * np * np) / (rr * rr * rr)
+              + 3.0 * (1.0 + 3.0 * eta) / (4.0 * rr * rr * rr * rr);
+    }
+    for (i = 0; i < 3; i++) {
+        g[i] = H_rr * n[i] + H_np * (p[i] - np * n[i]) / rr;
+        g[3 + i] = 2.0 * H_p2 * p[i] + H_np * n[i];
+        g[6 + i] = 0.0;
+        g[9 + i] = 0.0;
+    }
+
+    if (s->use_so) {
+        /* H_SO = (L . Seff) / rr^3 with L . Seff = p . (Seff x r) = r . (p x Seff) */
+        double Seff[3], L[3], Sxr[3], pxS[3], r3 = rr * rr * rr, g1 = g_so1(s), g2 = g_so2(s);
+        for (i = 0; i < 3; i++) Seff[i] = g1 * S1[i] + g2 * S2[i];
+        cross3(r, p, L);
+        cross3(Seff, r, Sxr);
+        cross3(p, Seff, pxS);
+        double LS = dot3(L, Seff);
+        for (i = 0; i < 3; i++) {
+            g[i] += pxS[i] / r3 - 3.0 * LS * n[i] / (r3 * rr);
+            g[3 + i] += Sxr[i] / r3;
+            g[6 + i] += g1 * L[i] / r3;
+            g[9 + i] += g2 * L[i] / r3;
+        }
+    }
+    if (s->use_ss) {
+        double a1 = dot3(S1, n), a2 = dot3(S2, n), S12 = dot3(S1, S2);
+        double k = 1.0 / (eta * rr * rr * rr);
+        for (i = 0; i < 3; i++) {
+            g[i] += -3.0 * k * (3.0 * a1 * a2 - S12) * n[i] / rr
+                  + 3.0 * k * (a2 * (S1[i] - a1 * n[i]) + a1 * (S2[i] - a2 * n[i])) / rr;
+            g[6 + i] += k * (3.0 * a2 * n[i] - S2[i]);
+            g[9 + i] += k * (3.0 * a1 * n[i] - S1[i]);
+        }
+    }
+    if (s->use_qm) {
+        double a1 = dot3(S1, n), a2 = dot3(S2, n), r3 = rr * rr * rr;
+        double q1 = s->kappa1 / (2.0 * s->beta * eta), q2 = s->kappa2 * s->beta / (2.0 * eta);
+        double Q = q1 * (3.0 * a1 * a1 - dot3(S1, S1)) + q2 * (3.0 * a2 * a2 - dot3(S2, S2));
+        for (i = 0; i < 3; i++) {
+            g[i] += -3.0 * Q * n[i] / (r3 * rr)
+                  + (6.0 * q1 * a1 * (S1[i] - a1 * n[i]) + 6.0 * q2 * a2 * (S2[i] - a2 * n[i])) / (r3 * rr);
+            g[6 + i] += q1 * (6.0 * a1 * n[i] - 2.0 * S1[i]) / r3;
+            g[9 + i] += q2 * (6.0 * a2 * n[i] - 2.0 * S2[i]) / r3;
+        }
+    }
+}
+
+/* ------------------------------------------------------ equations of motion */
+void orc_rhs(const orc_sys *s, const double y[12], double dy[12])
+{
+    double g[12];
+    int i;
+    orc_gradient(s, y, g);
+    for (i = 0; i < 3; i++) {
+        dy[i] = g[3 + i];      /* Eq. 6: dr/dt = dH/dp */
+        dy[3 + i] = -g[i];     /* Eq. 6: dp/dt = -dH/dr (a_2.5PN = 0) */
+    }
+    cross3(g + 6, y + 6, dy + 6); /* Eq. 7: dS1/dt = Omega_1 x S1 */
+    cross3(g + 9, y + 9, dy + 9); /* Eq. 7: dS2/dt = Omega_2 x S2 */
+}
+
+/* Classical fourth-order Runge-Kutta step. */
+void orc_rk4_step(const orc_sys *s, double y[12], double h)
+{
+    double k1[12], k2[12], k3[12], k4[12], tmp[12];
+    int i;
+    orc_rhs(s, y, k1);
+    for (i = 0; i < 12; i++) tmp[i] = y[i] + 0.5 * h * k1[i];
+    orc_rhs(s, tmp, k2);
+    for (i = 0; i < 12; i++) tmp[i] = y[i] + 0.5 * h * k2[i];
+    orc_rhs(s, tmp, k3);
+    for (i = 0; i < 12; i++) tmp[i] = y[i] + h * k3[i];
+    orc_rhs(s, tmp, k4);
+    for (i = 0; i < 12; i++) y[i] = y[i] + h * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]) / 6.0;
+}
+
+/* --------------------------------------------------------------- integrals */
+void orc_integrals(const orc_sys *s, const double y[12], double out[7])
+{
+    double L[3], J[3];
+    int i;
+    cross3(y, y + 3, L);
+    for (i = 0; i < 3; i++) J[i] = L[i] + y[6 + i] + y[9 + i]; /* J = L + S1 + S2 */
+    out[0] = orc_hamiltonian(s, y);
+    out[1] = norm3(J);
+    out[2] = norm3(y + 6);
+    out[3] = norm3(y + 9);
+    out[4] = J[0];
+    out[5] = J[1];
+    out[6] = J[2];
+}
+
+/* ------------------------------------------------------ manifold correction */
+int orc_correct(const orc_sys *s, double y[12], const double ref[4],
+                double newton_tol, int newton_max, double det_min,
+                int *iters, double alpha_beta[2])
+{
+    double rs[3], ps[3], yb[12], g[12];
+    double alpha = 1.0, beta = 1.0;
+    int it, i, converged = 0;
+
+    /* Eq. 10: restore both spin lengths (skipped for a zero-length spin). */
+    for (i = 0; i < 2; i++) {
+        double *S = y + 6 + 3 * i, len = norm3(S);
+        if (ref[2 + i] > 0.0 && len > 0.0) {
+            S[0] = S[0] * (ref[2 + i] / len);
+            S[1] = S[1] * (ref[2 + i] / len);
+            S[2] = S[2] * (ref[2 + i] / len);
+        }
+    }
+
+    /* Eqs. 11-13: p = alpha p*, r = beta r*; the two conditions
+     * H(beta r*, alpha p*, S) = E0 and |J(beta r*, alpha p*, S)| = J0 make the
+     * least-squares function of Eq. 12 vanish; Newton from (1, 1). */
+    for (i = 0; i < 3; i++) {
+        rs[i] = y[i];
+        ps[i] = y[3 + i];
+    }
+    memcpy(yb, y, sizeof(yb));
+    for (it = 1; it <= newton_max; it++) {
+        double J[3], rxp[3], rsxp[3], rxps[3], Jn, F1, F2, A, B, C, D, det, da, db;
+        for (i = 0; i < 3; i++) {
+            yb[i] = beta * rs[i];
+            yb[3 + i] = alpha * ps[i];
+        }
+        F1 = orc_hamiltonian(s, yb) - ref[0];
+        cross3(yb, yb + 3, rxp);
+        for (i = 0; i < 3; i++) J[i] = rxp[i] + yb[6 + i] + yb[9 + i];
+        Jn = norm3(J);
+        F2 = Jn - ref[1];
+        orc_gradient(s, yb, g);
+        A = dot3(g + 3, ps);           /* dF1/dalpha = dH/dp . p* */
+        B = dot3(g, rs);               /* dF1/dbeta  = dH/dr . r* */
+        cross3(yb, ps, rsxp);          /* d(r x p)/dalpha = (beta r*) x p* */
+        cross3(rs, yb + 3, rxps);      /* d(r x p)/dbeta  = r* x (alpha p*) */
+        C = dot3(J, rsxp) / Jn;        /* dF2/dalpha */
+        D = dot3(J, rxps) / Jn;        /* dF2/dbeta */
+        det = A * D - B * C;
+        /* The dual scaling is singular where alpha p*.dH/dp = beta r*.dH/dr
+         * (twice per orbit); there rounding noise in F would be amplified
+         * by 1/det.  Below det_min relative cancellation the step's
+         * scaling is skipped (the paper does not treat this case). */
+        if (!(fabs(det) > det_min * (fabs(A * D) + fabs(B * C))) || !isfinite(det)) break;
+        da = (F1 * D - B * F2) / det;
+        db = (A * F2 - C * F1) / det;
+        alpha = alpha - da;
+        beta = beta - db;
+        if (!isfinite(alpha) || !isfinite(beta)) break;
+        if (fabs(da) <= newton_tol && fabs(db) <= newton_tol) {
+            converged = 1;
+            break;
+        }
+    }
+    if (iters) *iters = it > newton_max ? newton_max : it;
+    if (alpha_beta) {
+        alpha_beta[0] = alpha;
+        alpha_beta[1] = beta;
+    }
+    if (!converged)
+        return ORC_CORR_SKIPPED; /* keep the spin-corrected r*, p* */
+    for (i = 0; i < 3; i++) {
+        y[i] = beta * rs[i];
+        y[3 + i] = alpha * ps[i];
+    }
+    return ORC_CORR_OK;
+}
+
+/* ------------------------------------------------------------ cell set-up */
+void orc_setup_cell(const double cell[9], double y[12])
+{
+    double x0 = cell[0], pfac = cell[1];
+    double beta = cell[6], m1 = beta / (1.0 + beta), m2 = 1.0 / (1.0 + beta);
+    double s1 = cell[7] * m1 * m1, s2 = cell[8] * m2 * m2;
+    y[0] = x0;
+    y[1] = 0.0;
+    y[2] = 0.0;
+    y[3] = 0.0;
+    y[4] = pfac / sqrt(x0); /* fraction of the Newtonian circular momentum */
+    y[5] = 0.0;
+    y[6] = s1 * sin(cell[2]) * cos(cell[3]);
+    y[7] = s1 * sin(cell[2]) * sin(cell[3]);
+    y[8] = s1 * cos(cell[2]);
+    y[9] = s2 * sin(cell[4]) * cos(cell[5]);
+    y[10] = s2 * sin(cell[4]) * sin(cell[5]);
+    y[11] = s2 * cos(cell[4]);
+}
+
+/* ------------------------------------------------------------- integrator */
+static void reference_integrals(const orc_sys *s, const double y[12], double ref[4])
+{
+    double I[7];
+    orc_integrals(s, y, I);
+    ref[0] = I[0];
+    ref[1] = I[1];
+    ref[2] = I[2];
+    ref[3] = I[3];
+}
+
+static int all_finite(const double y[12])
+{
+    int i;
+    for (i = 0; i < 12; i++)
+        if (!isfinite(y[i])) return 0;
+    return 1;
+}
+
+static double distance12(const double a[12], const double b[12])
+{
+    double d2 = 0.0;
+    int i;
+    for (i = 0; i < 12; i++) d2 += (b[i] - a[i]) * (b[i] - a[i]);
+    return sqrt(d2);
+}
+
+static void integrate_one(const orc_config *cfg, const orc_sys *s, const double y0[12],
+                          double h, int64_t nsteps, double y[12], double ys[12],
+                          double integ[6], double *fli_out, int32_t *status_out,
+                          double *t_stop_out, int64_t *iters_out, int32_t *skip_out)
+{
+    double ref[4], refs[4], acc = 0.0, d0 = cfg->fli_d0;
+    int64_t k, iters = 0;
+    int32_t st = ORC_DONE, skips = 0;
+    double t_stop = (double)nsteps * h;
+
+    memcpy(y, y0, 12 * sizeof(double));
+    memcpy(ys, y0, 12 * sizeof(double));
+    ys[0] = ys[0] + d0; /* shadow displaced by d0 along x */
+    reference_integrals(s, y, ref);
+    reference_integrals(s, ys, refs);
+
+    for (k = 1; k <= nsteps; k++) {
+        int it = 0;
+        orc_rk4_step(s, y, h);
+        if (cfg->correct) {
+            if (orc_correct(s, y, ref, cfg->newton_tol, cfg->newton_max, cfg->det_min, &it, 0))
+                skips++;
+            iters += it;
+        }
+        orc_rk4_step(s, ys, h);
+        if (cfg->correct) {
+            if (orc_correct(s, ys, refs, cfg->newton_tol, cfg->newton_max, cfg->det_min, &it, 0))
+                skips++;
+            iters += it;
+        }
+        /* termination tests on the main trajectory */
+        if (!all_finite(y) || !all_finite(ys)) { st = ORC_NONFINITE; t_stop = (double)k * h; break; }
+        {
+            double rr = norm3(y);
+            if (cfg->r_merge > 0.0 && rr < cfg->r_merge) { st = ORC_MERGED; t_stop = (double)k * h; break; }
+            if (cfg->r_escape > 0.0 && rr > cfg->r_escape) { st = ORC_ESCAPED; t_stop = (double)k * h; break; }
+        }
+        /* FLI renormalisation every fli_renorm steps */
+        if (cfg->fli_renorm > 0 && k % cfg->fli_renorm == 0) {
+            double d = distance12(y, ys);
+            int i;
+            acc += log10(d / d0);
+            for (i = 0; i < 12; i++) ys[i] = y[i] + (d0 / d) * (ys[i] - y[i]);
+            reference_integrals(s, ys, refs); /* the shadow keeps its own integrals */
+            if (cfg->fli_cap > 0.0 && acc >= cfg->fli_cap) { st = ORC_FLI_SATURATED; t_stop = (double)k * h; break; }
+        }
+    }
+    {
+        double I[7];
+        orc_integrals(s, y, I);
+        integ[0] = ref[0];
+        integ[1] = I[0];
+        integ[2] = ref[1];
+        integ[3] = I[1];
+        integ[4] = I[2];
+        integ[5] = I[3];
+    }
+    *fli_out = acc + log10(distance12(y, ys) / d0);
+    *status_out = st;
+    *t_stop_out = t_stop;
+    *iters_out = iters;
+    *skip_out = skips;
+}
+
+int orc_scan(int64_t n, const double *y0, const double *beta,
+             const double *kappa1, const double *kappa2,
+             const orc_config *cfg, double h, int64_t nsteps,
+             double *y_out, double *ys_out, double *integrals, double *fli,
+             int32_t *status, double *t_stop, int64_t *newton_iters,
+             int32_t *n_skip, int nthreads)
+{
+    int64_t i;
+    if (n < 0 || nsteps < 0 || !y0 || !beta || !cfg || !y_out || !ys_out || !integrals ||
+        !fli || !status || !t_stop || !newton_iters || !n_skip)
+        return -1;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+    for (i = 0; i < n; i++) {
+        orc_sys s;
+        orc_sys_init(&s, beta[i], kappa1 ? kappa1[i] : 1.0, kappa2 ? kappa2[i] : 1.0,
+                     cfg->pn_order, cfg->use_so, cfg->use_ss, cfg->use_qm);
+        integrate_one(cfg, &s, y0 + 12 * i, h, nsteps, y_out + 12 * i, ys_out + 12 * i,
+                      integrals + 6 * i, fli + i, status + i, t_stop + i, newton_iters + i,
+                      n_skip + i);
+    }
+    (void)nthreads;
+    return 0;
+}
+
+int orc_trace(const double y0[12], double beta, double kappa1, double kappa2,
+              const orc_config *cfg, double h, int64_t nsteps, int64_t every,
+              double *trace)
+{
+    orc_sys s;
+    double y[12], ref[4];
+    int64_t k, m = 0;
+    if (every <= 0 || !trace) return -1;
+    orc_sys_init(&s, beta, kappa1, kappa2, cfg->pn_order, cfg->use_so, cfg->use_ss, cfg->use_qm);
+    memcpy(y, y0, sizeof(y));
+    reference_integrals(&s, y, ref);
+    for (k = 1; k <= nsteps; k++) {
+        int it;
+        orc_rk4_step(&s, y, h);
+        if (cfg->correct) orc_correct(&s, y, ref, cfg->newton_tol, cfg->newton_max, cfg->det_min, &it, 0);
+        if (k % every == 0) {
+            memcpy(trace + 12 * m, y, sizeof(y));
+            m++;
+        }
+    }
+    return 0;
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

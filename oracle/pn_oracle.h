@@ -1,0 +1,119 @@
+/*
+ * pn_oracle.h -- plain, slow, obviously-correct FP64 CPU oracle for the
+ * manifold-corrected post-Newtonian spinning-binary scan of
+ * Ran, Liu & Zhong, "GPU accelerated manifold correction method for
+ * spinning compact binaries" (arXiv:1802.00147).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path loads this library:
+ * only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline /
+ * reference leg may.  It shares no code, header, table or constant with the
+ * CUDA library (paper_1802_00147_gb300/csrc); the two are written
+ * independently from the paper's equations.
+ *
+ * Units: G = c = M = 1 (Sec. 2).  r in M, p in mu, H in mu, t in M, spins in
+ * M^2 (the reading under which Eqs. 8-9 are the exact spin gradients of H and
+ * J = L + S1 + S2 is conserved by Eqs. 6-7).
+ *
+ * State vector y[12] = (r[3], p[3], S1[3], S2[3]), FP64, per orbit.
+ */
+#ifndef PN_ORACLE_H
+#define PN_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Per-orbit physical system (Sec. 2): mass ratio beta = m1/m2 <= 1, M = 1. */
+typedef struct {
+    double beta, m1, m2, eta;   /* eta = mu/M = m1 m2 */
+    double kappa1, kappa2;      /* quadrupole-monopole multipliers (1 for black holes) */
+    int pn_order;               /* 0: Newtonian, 1: +1PN, 2: +2PN orbital terms */
+    int use_so, use_ss, use_qm; /* 1.5PN spin-orbit, 2PN S1S2, QM terms (Eqs. 3-5) */
+} orc_sys;
+
+/* Integration / correction / FLI configuration (one per scan). */
+typedef struct {
+    int pn_order, use_so, use_ss, use_qm;
+    int correct;          /* 1: manifold correction (Eqs. 10-13) after every step */
+    double newton_tol;    /* stop when max(|d alpha|, |d beta|) <= tol (Sec. 3A: 1e-10) */
+    int newton_max;       /* iteration cap (50) */
+    double det_min;       /* skip the scaling when |det| <= det_min (|J11 J22| + |J12 J21|) */
+    double fli_d0;        /* initial / renormalised separation of the two trajectories */
+    int fli_renorm;       /* renormalise every this many steps */
+    double fli_cap;       /* stop when the FLI reaches this value (<= 0: never) */
+    double r_merge;       /* stop when |r| < r_merge (<= 0: never) */
+    double r_escape;      /* stop when |r| > r_escape (<= 0: never) */
+} orc_config;
+
+/* Per-orbit final status (oracle's own numbering). */
+enum {
+    ORC_RUNNING = 0, ORC_DONE = 1, ORC_MERGED = 2, ORC_ESCAPED = 3,
+    ORC_FLI_SATURATED = 4, ORC_NONFINITE = 5
+};
+
+/* Correction outcome. */
+enum { ORC_CORR_OK = 0, ORC_CORR_SKIPPED = 1 };
+
+void orc_sys_init(orc_sys *s, double beta, double kappa1, double kappa2,
+                  int pn_order, int use_so, int use_ss, int use_qm);
+
+/* Hamiltonian pieces (Eq. 1 without 3PN and 2.5PN; Eqs. 3-5). */
+double orc_H_newton(const orc_sys *s, const double y[12]);
+double orc_H_1pn(const orc_sys *s, const double y[12]);
+double orc_H_2pn(const orc_sys *s, const double y[12]);
+double orc_H_so(const orc_sys *s, const double y[12]);
+double orc_H_s1s2(const orc_sys *s, const double y[12]);
+double orc_H_qm(const orc_sys *s, const double y[12]);
+double orc_hamiltonian(const orc_sys *s, const double y[12]);
+
+/* Analytic gradient g = (dH/dr, dH/dp, dH/dS1, dH/dS2). */
+void orc_gradient(const orc_sys *s, const double y[12], double g[12]);
+
+/* Equations of motion (Eqs. 6-7, conservative): dy/dt. */
+void orc_rhs(const orc_sys *s, const double y[12], double dy[12]);
+
+/* One classical RK4 step of size h, in place. */
+void orc_rk4_step(const orc_sys *s, double y[12], double h);
+
+/* Integrals: out = (E, |J|, |S1|, |S2|, Jx, Jy, Jz). */
+void orc_integrals(const orc_sys *s, const double y[12], double out[7]);
+
+/* Manifold correction (Eqs. 10-13) toward ref = (E0, J0, |S1|0, |S2|0), in
+ * place.  Returns ORC_CORR_OK or ORC_CORR_SKIPPED; *iters gets the number of
+ * Newton iterations; alpha_beta (nullable) gets the scale factors. */
+int orc_correct(const orc_sys *s, double y[12], const double ref[4],
+                double newton_tol, int newton_max, double det_min,
+                int *iters, double alpha_beta[2]);
+
+/* Initial conditions of a scan cell: cell = (x0, pfac, theta1, phi1,
+ * theta2, phi2, beta, chi1, chi2).  r = (x0,0,0), p = (0, pfac/sqrt(x0), 0),
+ * S_i = chi_i m_i^2 (sin th_i cos ph_i, sin th_i sin ph_i, cos th_i). */
+void orc_setup_cell(const double cell[9], double y[12]);
+
+/* Integrate n independent orbits for nsteps steps of size h with manifold
+ * correction and FLI (two trajectories).  Arrays are AoS: y0/y_out/ys_out
+ * n*12; kappa1/kappa2 nullable (1.0); outputs:
+ *   integrals n*6 = (E0, E, J0, |J|, |S1|, |S2|) of the main trajectory,
+ *   fli n, status n, t_stop n, newton_iters n (sum over both trajectories),
+ *   n_skip n (corrections rejected).
+ * nthreads <= 0: all OpenMP threads.  Returns 0, or -1 on bad arguments. */
+int orc_scan(int64_t n, const double *y0, const double *beta,
+             const double *kappa1, const double *kappa2,
+             const orc_config *cfg, double h, int64_t nsteps,
+             double *y_out, double *ys_out, double *integrals, double *fli,
+             int32_t *status, double *t_stop, int64_t *newton_iters,
+             int32_t *n_skip, int nthreads);
+
+/* Same integrator without the shadow trajectory, recording the state after
+ * every `every` steps into trace[(nsteps/every) * 12] (single orbit). */
+int orc_trace(const double y0[12], double beta, double kappa1, double kappa2,
+              const orc_config *cfg, double h, int64_t nsteps, int64_t every,
+              double *trace);
+
+int orc_max_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

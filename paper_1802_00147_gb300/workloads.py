@@ -1,0 +1,111 @@
+"""Seeded synthetic scan workloads (inputs only -- none of the method's arithmetic).
+
+Both the CUDA path and the CPU oracle receive the arrays made here; the
+initial-condition set-up itself (spin vectors, circular momentum, shadow
+offset) is computed independently by each side.
+
+A *cell* is one orbit's scan parameters, 11 FP64 fields:
+
+    0 x0      initial separation, r = (x0, 0, 0)
+    1 pfac    p_y as a fraction of the Newtonian circular momentum 1/sqrt(x0)
+    2 theta1  polar angle of S1 from the z axis (the initial L direction)
+    3 phi1    azimuth of S1
+    4 theta2  polar angle of S2
+    5 phi2    azimuth of S2
+    6 beta    mass ratio m1/m2 <= 1 (Sec. 2 of arXiv:1802.00147)
+    7 chi1    dimensionless spin magnitude of body 1
+    8 chi2    dimensionless spin magnitude of body 2
+    9 kappa1  quadrupole-monopole multiplier of body 1 (1 = black hole)
+   10 kappa2  quadrupole-monopole multiplier of body 2
+
+The scans stand in for the paper's phase-space scans (Sec. 3C, Figs. 6-7,
+Table 3), which use no external dataset.  Random draws use numpy's PCG64
+generator with the given seed.
+"""
+import numpy as np
+
+NFIELDS = 11
+X0, PFAC, TH1, PH1, TH2, PH2, BETA, CHI1, CHI2, KAP1, KAP2 = range(NFIELDS)
+
+
+def _grid(nx, nt, x_lo, x_hi):
+    x0 = np.linspace(x_lo, x_hi, nx)
+    th = np.linspace(0.0, np.pi, nt)
+    X, T = np.meshgrid(x0, th, indexing="ij")
+    return X.ravel(), T.ravel()
+
+
+def grid_cells(nx, nt, x_lo, x_hi, seed, beta=None, chi=None, kappa=None, pfac=0.9):
+    """(x0, theta) grid with both spins at polar angle theta and seeded azimuths.
+
+    beta / chi / kappa: None for the fixed values 1, or a (lo, hi) range for a
+    seeded uniform draw per cell (chi1, chi2 and kappa1, kappa2 drawn
+    independently)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    X, T = _grid(nx, nt, x_lo, x_hi)
+    n = X.size
+    c = np.zeros((n, NFIELDS))
+    c[:, X0] = X
+    c[:, PFAC] = pfac
+    c[:, TH1] = T
+    c[:, TH2] = T
+    c[:, PH1] = rng.uniform(0.0, 2.0 * np.pi, n)
+    c[:, PH2] = rng.uniform(0.0, 2.0 * np.pi, n)
+    c[:, BETA] = 1.0 if beta is None else rng.uniform(beta[0], beta[1], n)
+    if chi is None:
+        c[:, CHI1] = c[:, CHI2] = 1.0
+    else:
+        c[:, CHI1] = rng.uniform(chi[0], chi[1], n)
+        c[:, CHI2] = rng.uniform(chi[0], chi[1], n)
+    if kappa is None:
+        c[:, KAP1] = c[:, KAP2] = 1.0
+    else:
+        c[:, KAP1] = rng.uniform(kappa[0], kappa[1], n)
+        c[:, KAP2] = rng.uniform(kappa[0], kappa[1], n)
+    return c
+
+
+def small_scan(seed=1):
+    """16 x 16 = 256 orbits: x0 in [15, 40], theta in [0, pi], m1 = m2, chi = 1."""
+    return grid_cells(16, 16, 15.0, 40.0, seed)
+
+
+def full_scan(seed=2, nx=314, nt=314):
+    """314 x 314 = 98,596 orbits: x0 in [10, 50], theta in [0, pi],
+    beta ~ U[0.5, 1], chi_i ~ U[0.5, 1]."""
+    return grid_cells(nx, nt, 10.0, 50.0, seed, beta=(0.5, 1.0), chi=(0.5, 1.0))
+
+
+def uneven_batch(n=100_000, seed=3):
+    """Uneven batch: beta ~ U[0.1, 1], chi_i ~ U[0, 1], isotropic spin
+    directions, x0 ~ U[10, 50], p_y 50-100% of circular."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    c = np.zeros((n, NFIELDS))
+    c[:, X0] = rng.uniform(10.0, 50.0, n)
+    c[:, PFAC] = rng.uniform(0.5, 1.0, n)
+    c[:, TH1] = np.arccos(rng.uniform(-1.0, 1.0, n))
+    c[:, PH1] = rng.uniform(0.0, 2.0 * np.pi, n)
+    c[:, TH2] = np.arccos(rng.uniform(-1.0, 1.0, n))
+    c[:, PH2] = rng.uniform(0.0, 2.0 * np.pi, n)
+    c[:, BETA] = rng.uniform(0.1, 1.0, n)
+    c[:, CHI1] = rng.uniform(0.0, 1.0, n)
+    c[:, CHI2] = rng.uniform(0.0, 1.0, n)
+    c[:, KAP1] = c[:, KAP2] = 1.0
+    return c
+
+
+def adaptive_grid(n=1024, seed=4):
+    """n x n grid of the small-scan parameters (x0 in [15, 40], theta in [0, pi])."""
+    return grid_cells(n, n, 15.0, 40.0, seed)
+
+
+def qm_grid(n=1024, seed=5):
+    """n x n small-scan grid with kappa_i ~ U[1, 10] (quadrupole-monopole study)."""
+    return grid_cells(n, n, 15.0, 40.0, seed, kappa=(1.0, 10.0))
+
+
+def subset(cells, m, seed=6):
+    """A seeded subset of m cells (sorted indices) and the indices themselves."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    idx = np.sort(rng.choice(cells.shape[0], size=min(m, cells.shape[0]), replace=False))
+    return cells[idx], idx

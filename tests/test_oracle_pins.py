@@ -1,0 +1,438 @@
+"""Pins of the CPU oracle against things other than itself (no GPU needed).
+
+Every pin is chosen so that a plausible slip in the oracle -- a dropped term,
+a wrong sign or coefficient, a transposed operand -- fails one of them:
+
+* central finite differences of H       -> analytic gradient (all terms)
+* Eqs. 8-9 of arXiv:1802.00147 as printed -> spin gradients Omega_i of H
+* gauge-invariant 2PN circular-orbit energy E(x) (closed form) -> 1PN/2PN orbital terms
+* Kepler closure after one period (closed form T = 2 pi a^{3/2}) -> H_N, RK4
+* conservation of J = L + S1 + S2 and |S_i| by the flow        -> Eqs. 6-7 signs
+* time reversal (r, p, S) -> (r, -p, -S)                         -> RK4 + correction
+* RK4 global error order 4
+* exact restoration of E, |J|, |S_i| by the correction (Eqs. 10-13)
+* the Newton root of Eq. 13 vs an independent 2-D root finder
+* FLI of an integrable orbit grows as a power law; the paper's case II
+  orbits 1 / 2 are regular / chaotic (Sec. 3B, Fig. 3)
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_orbits.json")
+
+
+def paper_orbit(name):
+    with open(GOLDEN) as f:
+        g = json.load(f)[name]
+    beta = g["beta"]
+    m1, m2 = beta / (1 + beta), 1 / (1 + beta)
+    y = np.r_[g["r"], g["p"], g["chi1"] * m1 * m1 * np.array(g["S1_hat"]),
+              g["chi2"] * m2 * m2 * np.array(g["S2_hat"])].astype(float)
+    return beta, y
+
+
+def random_state(rng, r_lo=8.0, r_hi=30.0):
+    r = rng.uniform(r_lo, r_hi)
+    d = rng.normal(size=3)
+    rv = r * d / np.linalg.norm(d)
+    pv = rng.normal(size=3) * (0.6 / np.sqrt(r))
+    S1 = rng.normal(size=3) * 0.1
+    S2 = rng.normal(size=3) * 0.1
+    return np.r_[rv, pv, S1, S2]
+
+
+# ------------------------------------------------------------------ gradient
+@pytest.mark.parametrize("beta", [1.0, 0.5, 0.2])
+def test_gradient_matches_central_differences(orc, beta):
+    rng = np.random.default_rng(11)
+    s = orc.system(beta, kappa1=2.5, kappa2=7.0, pn_order=2, use_so=1, use_ss=1, use_qm=1)
+    for _ in range(5):
+        y = random_state(rng)
+        g = orc.gradient(s, y)
+        fd = np.zeros(12)
+        for i in range(12):
+            e = np.zeros(12)
+            e[i] = 1e-5 * max(1.0, abs(y[i]))
+            fd[i] = (orc.hamiltonian(s, y + e) - orc.hamiltonian(s, y - e)) / (2 * e[i])
+        scale = np.abs(g).max()
+        assert np.max(np.abs(g - fd)) < 1e-7 * scale, (g, fd)
+
+
+@pytest.mark.parametrize("term", ["1PN", "2PN", "SO", "S1S2", "QM"])
+def test_each_term_is_differentiated(orc, term):
+    """Gradient of each Hamiltonian term alone (others off) against FD of that term."""
+    rng = np.random.default_rng(5)
+    flags = dict(pn_order=0, use_so=0, use_ss=0, use_qm=0)
+    if term == "1PN":
+        flags["pn_order"] = 1
+    elif term == "2PN":
+        flags["pn_order"] = 2
+    else:
+        flags[{"SO": "use_so", "S1S2": "use_ss", "QM": "use_qm"}[term]] = 1
+    s = orc.system(0.4, kappa1=3.0, kappa2=2.0, **flags)
+    y = random_state(rng)
+    g = orc.gradient(s, y)
+    fd = np.zeros(12)
+    for i in range(12):
+        e = np.zeros(12)
+        e[i] = 1e-5 * max(1.0, abs(y[i]))
+        fd[i] = (orc.hamiltonian(s, y + e) - orc.hamiltonian(s, y - e)) / (2 * e[i])
+    # subtract the Newtonian part, which every configuration contains
+    assert np.max(np.abs(g - fd)) < 1e-7 * np.abs(g).max()
+
+
+# ------------------------------------------------- Eqs. 8-9 (spin precession)
+def omega_paper(beta, y):
+    """Omega_1, Omega_2 exactly as printed in Eqs. 8-9 (QM on, kappa = 1)."""
+    r, p, S1, S2 = y[:3], y[3:6], y[6:9], y[9:12]
+    eta = beta / (1 + beta) ** 2
+    rr = np.linalg.norm(r)
+    n = r / rr
+    L = np.cross(r, p)
+    O1 = ((2 + 3 / (2 * beta)) * L / rr ** 3 + (3 * n * (S2 @ n) - S2) / (eta * rr ** 3)
+          + 3 / rr ** 3 * (1 + 1 / beta) ** 2 * n * (S1 @ n))
+    O2 = ((2 + 3 * beta / 2) * L / rr ** 3 + (3 * n * (S1 @ n) - S1) / (eta * rr ** 3)
+          + 3 / rr ** 3 * (1 + beta) ** 2 * n * (S2 @ n))
+    return O1, O2
+
+
+@pytest.mark.parametrize("beta", [1.0, 1 / 3, 0.15])
+def test_spin_gradients_reproduce_eqs_8_9(orc, beta):
+    rng = np.random.default_rng(7)
+    s = orc.system(beta, pn_order=2, use_so=1, use_ss=1, use_qm=1)
+    for _ in range(4):
+        y = random_state(rng)
+        fd = np.zeros(6)
+        for i in range(6):
+            e = np.zeros(12)
+            e[6 + i] = 1e-6
+            fd[i] = (orc.hamiltonian(s, y + e) - orc.hamiltonian(s, y - e)) / 2e-6
+        O1, O2 = omega_paper(beta, y)
+        rr = np.linalg.norm(y[:3])
+        # Eqs. 8-9 drop the -S_i part of the QM gradient (it is parallel to S_i
+        # and drops out of Omega_i x S_i); add it back for a component check.
+        O1_full = O1 - (1 + 1 / beta) ** 2 * y[6:9] / rr ** 3
+        O2_full = O2 - (1 + beta) ** 2 * y[9:12] / rr ** 3
+        assert np.allclose(fd[:3], O1_full, rtol=1e-7, atol=1e-12 * np.abs(O1).max())
+        assert np.allclose(fd[3:], O2_full, rtol=1e-7, atol=1e-12 * np.abs(O2).max())
+        # and the precession the printed Omegas generate equals the oracle's EOM
+        dy = orc.rhs(s, y)
+        assert np.allclose(dy[6:9], np.cross(O1, y[6:9]), rtol=1e-12, atol=1e-18)
+        assert np.allclose(dy[9:12], np.cross(O2, y[9:12]), rtol=1e-12, atol=1e-18)
+
+
+# --------------------------------------------- 2PN circular-orbit energy E(x)
+def circular_energy_numeric(orc, s, r):
+    """Circular orbit of the oracle's H at separation r: returns (x, E)."""
+    from scipy.optimize import brentq
+
+    def radial_force(py):
+        # dH/dr at fixed angular momentum L = r p_y:  dH/dx - (p_y / r) dH/dp_y
+        y = np.r_[r, 0, 0, 0, py, 0, np.zeros(6)]
+        g = orc.gradient(s, y)
+        return g[0] - (py / r) * g[4]
+
+    py = brentq(radial_force, 0.5 / np.sqrt(r), 1.5 / np.sqrt(r), xtol=1e-17, rtol=1e-15)
+    y = np.r_[r, 0, 0, 0, py, 0, np.zeros(6)]
+    omega = orc.gradient(s, y)[4] / r          # d(phi)/dt = (dH/dp_y) / r
+    return omega ** (2.0 / 3.0), orc.hamiltonian(s, y)
+
+
+def circular_energy_closed_form(x, eta):
+    """Gauge-invariant 2PN binding energy per unit reduced mass of a circular
+    orbit, x = (M omega)^{2/3} (standard PN result, e.g. Blanchet 2014)."""
+    return -0.5 * x * (1 - (0.75 + eta / 12) * x - (27 / 8 - 19 * eta / 8 + eta ** 2 / 24) * x ** 2)
+
+
+@pytest.mark.parametrize("beta", [1.0, 1 / 3])
+def test_circular_orbit_energy_matches_2pn_closed_form(orc, beta):
+    s = orc.system(beta, pn_order=2, use_so=0, use_ss=0, use_qm=0)
+    eta = s.eta
+    ratios = []
+    for r in (100.0, 200.0, 400.0):
+        x, E = circular_energy_numeric(orc, s, r)
+        resid = E - circular_energy_closed_form(x, eta)
+        ratios.append(resid / x ** 4)   # the first omitted (3PN) order
+    ratios = np.array(ratios)
+    # an error in any 1PN / 2PN coefficient leaves a residual ~x^2 or ~x^3,
+    # whose ratio to x^4 would grow by 2x-4x per halving of x
+    assert np.all(np.abs(ratios) < 20), ratios
+    assert np.max(np.abs(np.diff(ratios))) < 0.1 * np.max(np.abs(ratios)) + 0.05, ratios
+
+
+# ------------------------------------------------------------ Kepler limit
+def kepler_system(orc):
+    return orc.system(1.0, pn_order=0, use_so=0, use_ss=0, use_qm=0)
+
+
+def test_kepler_orbit_closes_after_one_period(orc):
+    s = kepler_system(orc)
+    y0 = np.r_[10.0, 0, 0, 0, 0.28, 0, np.zeros(6)]
+    E = orc.hamiltonian(s, y0)
+    a = -1 / (2 * E)
+    T = 2 * np.pi * a ** 1.5
+    errs = []
+    for N in (1000, 2000):
+        y = y0.copy()
+        h = T / N
+        for _ in range(N):
+            y = orc.rk4_step(s, y, h)
+        errs.append(np.linalg.norm(y[:3] - y0[:3]) / 10.0)
+    assert errs[1] < 1e-8
+    assert 10 < errs[0] / errs[1] < 24      # RK4: global error ~ h^4
+    # eccentricity from the closed form e = sqrt(1 + 2 E L^2)
+    L = 10.0 * 0.28
+    e = np.sqrt(1 + 2 * E * L * L)
+    assert abs(e - (1 - 10.0 * 0.28 ** 2)) < 1e-12   # apocentre start: e = 1 - r v^2
+
+
+def test_kepler_period_and_correction(orc):
+    """With the manifold correction on, E and |J| stay exact and the orbit
+    still closes after one closed-form period."""
+    s = kepler_system(orc)
+    y0 = np.r_[10.0, 0, 0, 0, 0.28, 0, np.zeros(6)]
+    ref = orc.integrals(s, y0)[:4]
+    E = ref[0]
+    T = 2 * np.pi * (-1 / (2 * E)) ** 1.5
+    N = 2000
+    y = y0.copy()
+    for _ in range(N):
+        y = orc.rk4_step(s, y, T / N)
+        y, code, it, _ = orc.correct(s, y, ref)
+        assert code == 0
+    I = orc.integrals(s, y)
+    assert abs(I[0] - E) < 1e-15
+    assert abs(I[1] - ref[1]) < 1e-14
+    assert np.linalg.norm(y[:3] - y0[:3]) / 10.0 < 1e-8
+
+
+# ------------------------------------------------------ conservation of J
+def test_flow_conserves_J_vector_and_spin_lengths(orc):
+    rng = np.random.default_rng(3)
+    s = orc.system(0.5, kappa1=4.0, kappa2=2.0, pn_order=2, use_so=1, use_ss=1, use_qm=1)
+    y = random_state(rng, 12, 14)
+    I0 = orc.integrals(s, y)
+    drift = {}
+    for h in (0.1, 0.05):
+        yy = y.copy()
+        for _ in range(int(round(50 / h))):
+            yy = orc.rk4_step(s, yy, h)
+        I = orc.integrals(s, yy)
+        drift[h] = np.linalg.norm(I[4:7] - I0[4:7]) / np.linalg.norm(I0[4:7])
+        assert abs(I[2] - I0[2]) < 1e-9 * I0[2]
+        assert abs(I[3] - I0[3]) < 1e-9 * I0[3]
+    assert drift[0.05] < 1e-9
+    # the drift is RK4 truncation (shrinks ~16x per halving), not a wrong EOM
+    assert drift[0.1] / max(drift[0.05], 1e-300) > 6
+
+
+def test_wrong_spin_sign_would_break_J(orc):
+    """Planted-mistake control: precessing the spins the other way (S x Omega)
+    does not conserve J, so the test above can fail."""
+    rng = np.random.default_rng(3)
+    s = orc.system(0.5, pn_order=2, use_so=1, use_ss=1, use_qm=0)
+    y = random_state(rng, 12, 14)
+
+    def bad_rhs(y):
+        dy = orc.rhs(s, y)
+        dy[6:] = -dy[6:]
+        return dy
+
+    I0 = orc.integrals(s, y)
+    h = 0.05
+    for _ in range(1000):
+        k1 = bad_rhs(y)
+        k2 = bad_rhs(y + h / 2 * k1)
+        k3 = bad_rhs(y + h / 2 * k2)
+        k4 = bad_rhs(y + h * k3)
+        y = y + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+    I = orc.integrals(s, y)
+    assert np.linalg.norm(I[4:7] - I0[4:7]) / np.linalg.norm(I0[4:7]) > 1e-6
+
+
+# ------------------------------------------------------------ time reversal
+def test_time_reversal_returns_to_start(orc):
+    rng = np.random.default_rng(9)
+    s = orc.system(0.5, kappa1=3.0, kappa2=1.5, pn_order=2, use_so=1, use_ss=1, use_qm=1)
+    y0 = random_state(rng, 12, 16)
+    ref = orc.integrals(s, y0)[:4]
+    flip = np.r_[np.ones(3), -np.ones(9)]
+    y = y0.copy()
+    for _ in range(400):
+        y = orc.rk4_step(s, y, 0.05)
+        y, _, _, _ = orc.correct(s, y, ref)
+    y = y * flip
+    ref_b = orc.integrals(s, y)[:4]
+    assert abs(ref_b[0] - ref[0]) < 1e-15 and abs(ref_b[1] - ref[1]) < 1e-13
+    for _ in range(400):
+        y = orc.rk4_step(s, y, 0.05)
+        y, _, _, _ = orc.correct(s, y, ref_b)
+    y = y * flip
+    assert np.linalg.norm(y[:3] - y0[:3]) / np.linalg.norm(y0[:3]) < 1e-10
+    assert np.linalg.norm(y[3:6] - y0[3:6]) / np.linalg.norm(y0[3:6]) < 1e-10
+    assert np.linalg.norm(y[6:] - y0[6:]) / np.linalg.norm(y0[6:]) < 1e-10
+
+
+# ---------------------------------------------------------------- RK4 order
+def test_rk4_energy_error_is_fourth_order(orc):
+    beta, y0 = paper_orbit("case_II_orbit_1")
+    s = orc.system(beta)
+    E0 = orc.hamiltonian(s, y0)
+    err = []
+    for h in (1.0, 0.5):
+        y = y0.copy()
+        for _ in range(int(round(200 / h))):
+            y = orc.rk4_step(s, y, h)
+        err.append(abs(orc.hamiltonian(s, y) - E0))
+    assert 10 < err[0] / err[1] < 24
+
+
+# ------------------------------------------------------ manifold correction
+def test_correction_restores_all_six_integrals(orc):
+    rng = np.random.default_rng(21)
+    for beta in (1.0, 0.3):
+        s = orc.system(beta, kappa1=2.0, kappa2=5.0, use_qm=1)
+        for _ in range(5):
+            y0 = random_state(rng, 10, 25)
+            ref = orc.integrals(s, y0)
+            y = orc.rk4_step(s, y0, 15.0)             # a crude step: visible errors
+            Ibad = orc.integrals(s, y)
+            assert abs(Ibad[0] - ref[0]) > 1e-12 * abs(ref[0])
+            y, code, it, (a, b) = orc.correct(s, y, ref[:4])
+            assert code == 0 and it <= 6
+            I = orc.integrals(s, y)
+            assert abs(I[0] - ref[0]) <= 1e-14 * abs(ref[0])
+            assert abs(I[1] - ref[1]) <= 1e-14 * ref[1]
+            assert abs(I[2] - ref[2]) <= 1e-15 * ref[2]
+            assert abs(I[3] - ref[3]) <= 1e-15 * ref[3]
+
+
+def test_correction_is_identity_on_the_manifold(orc):
+    rng = np.random.default_rng(4)
+    s = orc.system(0.7)
+    y0 = random_state(rng, 10, 25)
+    ref = orc.integrals(s, y0)[:4]
+    y, code, it, (a, b) = orc.correct(s, y0, ref)
+    assert code == 0 and it == 1
+    assert abs(a - 1) < 1e-15 and abs(b - 1) < 1e-15
+    assert np.allclose(y, y0, rtol=1e-15, atol=0)
+
+
+def test_newton_root_matches_independent_root_finder(orc):
+    """The (alpha, beta) of Eq. 13 from the oracle's Newton equal the root that
+    scipy's hybrid solver finds for the same two conditions."""
+    from scipy.optimize import root
+    rng = np.random.default_rng(8)
+    s = orc.system(0.6)
+    y0 = random_state(rng, 12, 20)
+    ref = orc.integrals(s, y0)[:4]
+    ystar = orc.rk4_step(s, y0, 5.0)
+    # spins first (Eq. 10), exactly as the oracle does
+    S = ystar.copy()
+    for i, L in ((6, ref[2]), (9, ref[3])):
+        S[i:i + 3] = S[i:i + 3] * (L / np.linalg.norm(S[i:i + 3]))
+
+    def F(v):
+        a, b = v
+        yb = S.copy()
+        yb[:3] = b * S[:3]
+        yb[3:6] = a * S[3:6]
+        I = orc.integrals(s, yb)
+        return [(I[0] - ref[0]) / abs(ref[0]), (I[1] - ref[1]) / ref[1]]
+
+    sol = root(F, [1.0, 1.0], method="hybr", options=dict(xtol=1e-15))
+    _, code, _, (a, b) = orc.correct(s, ystar, ref)
+    assert code == 0
+    assert abs(a - sol.x[0]) < 1e-12 and abs(b - sol.x[1]) < 1e-12
+
+
+def test_singular_scaling_is_skipped(orc):
+    """Where alpha p.dH/dp = beta r.dH/dr the dual scaling has no unique
+    solution; the oracle leaves r*, p* unscaled (spins still corrected)."""
+    s = orc.system(1.0, pn_order=0, use_so=0, use_ss=0, use_qm=0)
+    # Newtonian: p.dH/dp - r.dH/dr = p^2 - 1/r = 0 on the circle p = 1/sqrt(r)
+    r = 20.0
+    y = np.r_[r, 0, 0, 0, 1 / np.sqrt(r), 0, np.zeros(6)]
+    ref = orc.integrals(s, y)[:4].copy()
+    ref[0] -= 1e-9
+    y2, code, it, _ = orc.correct(s, y, ref)
+    assert code == 1
+    assert np.array_equal(y2, y)
+
+
+# ------------------------------------------------------------------ FLI
+def test_fli_of_integrable_orbit_grows_as_power_law(orc):
+    beta, y0 = paper_orbit("case_I_orbit_1")
+    cfg = orc.config(r_merge=0, r_escape=0)
+    f4 = orc.scan(y0[None], beta, 1.0, 10_000, cfg)["fli"][0]
+    f5 = orc.scan(y0[None], beta, 1.0, 100_000, cfg)["fli"][0]
+    assert f5 < 5.0
+    assert f5 - f4 < 1.6        # ~log10(10) per decade, not exponential
+
+
+def test_fli_classifies_paper_case_II_orbits(orc):
+    """Sec. 3B / Fig. 3: case II orbit 1 regular, orbit 2 chaotic (FLI 5.8
+    threshold of Sec. 3C, t = 1e5)."""
+    with open(GOLDEN) as f:
+        thr = json.load(f)["fli_threshold"]["value"]
+    cfg = orc.config(r_merge=0, r_escape=0)
+    b1, y1 = paper_orbit("case_II_orbit_1")
+    b2, y2 = paper_orbit("case_II_orbit_2")
+    f1 = orc.scan(y1[None], b1, 1.0, 100_000, cfg)["fli"][0]
+    f2 = orc.scan(y2[None], b2, 1.0, 100_000, cfg)["fli"][0]
+    assert f1 < thr < f2, (f1, f2)
+
+
+def test_corrected_energy_error_at_table_2_level(orc):
+    """Table 2: with correction the energy error at t = 1e4 is ~1e-15 (case I)
+    and <= 1e-11 (case II)."""
+    cfg = orc.config(r_merge=0, r_escape=0)
+    for name in ("case_I_orbit_1", "case_I_orbit_2", "case_II_orbit_1", "case_II_orbit_2"):
+        beta, y0 = paper_orbit(name)
+        I = orc.scan(y0[None], beta, 1.0, 10_000, cfg)["integrals"][0]
+        assert abs(I[1] - I[0]) <= 1e-14 * abs(I[0]), name
+        assert abs(I[3] - I[2]) <= 1e-14 * I[2], name
+
+
+def test_uncorrected_rk4_drifts(orc):
+    """Without correction the energy error grows (Table 2 'linear growth')."""
+    beta, y0 = paper_orbit("case_II_orbit_2")
+    cfg = orc.config(correct=0, r_merge=0, r_escape=0)
+    e = []
+    for T in (2000, 8000):
+        I = orc.scan(y0[None], beta, 1.0, T, cfg)["integrals"][0]
+        e.append(abs(I[1] - I[0]) / abs(I[0]))
+    assert e[0] > 1e-11 and e[1] > 2 * e[0]
+
+
+# ---------------------------------------------------- set-up and statuses
+def test_setup_cell_geometry(orc):
+    cells = np.array([[20.0, 0.9, 0.7, 1.1, 2.0, 4.0, 0.5, 0.8, 0.6]])
+    y = orc.setup_cells(cells)[0]
+    m1, m2 = 0.5 / 1.5, 1 / 1.5
+    assert np.allclose(y[:3], [20, 0, 0]) and np.allclose(y[3:6], [0, 0.9 / np.sqrt(20), 0])
+    assert abs(np.linalg.norm(y[6:9]) - 0.8 * m1 ** 2) < 1e-16
+    assert abs(np.linalg.norm(y[9:12]) - 0.6 * m2 ** 2) < 1e-16
+    assert abs(np.arccos(y[8] / np.linalg.norm(y[6:9])) - 0.7) < 1e-13
+    assert abs(np.arctan2(y[10], y[9]) - (4.0 - 2 * np.pi)) < 1e-13
+
+
+def test_termination_statuses(orc):
+    beta = 1.0
+    cells = np.array([[20.0, 0.9, 1.0, 0.0, 1.0, 1.0, 1.0, 1.0, 1.0],     # runs to the end
+                      [9.0, 0.45, 1.0, 0.0, 1.0, 1.0, 1.0, 1.0, 1.0],     # plunges: r < 6
+                      [20.0, 2.0, 1.0, 0.0, 1.0, 1.0, 1.0, 1.0, 1.0]])    # unbound: r > 1e3
+    y0 = orc.setup_cells(cells)
+    out = orc.scan(y0, beta, 1.0, 8000, orc.config())
+    assert list(out["status"]) == [orc.DONE, orc.MERGED, orc.ESCAPED]
+    assert out["t_stop"][0] == 8000.0 and out["t_stop"][1] < 8000 and out["t_stop"][2] < 8000
+    bad = y0[:1].copy()
+    bad[0, 4] = np.nan
+    out = orc.scan(bad, beta, 1.0, 10, orc.config())
+    assert out["status"][0] == orc.NONFINITE and out["t_stop"][0] == 1.0
+    b2, y2 = paper_orbit("case_II_orbit_2")
+    out = orc.scan(y2[None], b2, 1.0, 100_000, orc.config(r_merge=0, r_escape=0, fli_cap=4.0))
+    assert out["status"][0] == orc.FLI_SATURATED and out["t_stop"][0] % 100 == 0
