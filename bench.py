@@ -1,0 +1,347 @@
+"""Benchmark of the batched manifold-corrected PN scan on GB300.
+
+One step = one pass of the whole hot path over one batch: grid set-up and
+reference integrals on the device, integration of every orbit to t_end
+(RK4 + manifold correction + FLI for both trajectories, persistent
+work-queue kernel replayed from a CUDA graph), final integrals and the
+scan-level reduction.  Workload: the 314 x 314 (x0, theta) scan, seeded
+synthetic cells, h = 1, t_end = 2e4.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+(the reference arm of this build: plain FP64 C, OpenMP over orbits) on a
+bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FP64 orbit-steps/s (RK+manifold corr.+FLI), 314² scan; adaptive-scan speedup"
+UNIT = "orbit-steps/s"
+T_END = 2.0e4
+H_STEP = 1.0
+
+# Algorithmic FP64 flops of the kernel's formulation (fma = 2, add/sub/mul = 1,
+# sqrt/rsqrt/reciprocal/division/log10 = 1 each), per trajectory-step:
+#   4 x 226 (RHS) + 171 (RK4 stages) + 138 (correction: spin lengths, Newton
+#   monomial set-up, scaling) = 1213, plus 73 per Newton iteration; per
+#   orbit-step two trajectories, 5 for the termination test and 1.75 for the
+#   FLI renormalisation amortised over 100 steps.
+FLOPS_PER_TRAJ_STEP = 4 * 226 + 171 + 138
+FLOPS_PER_NEWTON_ITER = 73
+FLOPS_PER_ORBIT_STEP_EXTRA = 5 + 1.75
+# Nominal FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz.
+FP64_PEAK_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def algorithmic_flops(orbit_steps, newton_iters):
+    return (orbit_steps * (2 * FLOPS_PER_TRAJ_STEP + FLOPS_PER_ORBIT_STEP_EXTRA)
+            + newton_iters * FLOPS_PER_NEWTON_ITER)
+
+
+def workload(rank=0, orbits=0):
+    from paper_1802_00147_gb300 import workloads as W
+    cells = W.full_scan(seed=2 + rank)
+    if orbits and orbits < cells.shape[0]:
+        cells = W.subset(cells, orbits, seed=40)[0]
+    return cells
+
+
+def workload_desc(n):
+    return {
+        "workload": "314x314 (x0, theta) phase-space scan: x0 in [10,50], theta in [0,pi] "
+                    "(both spins), beta~U[0.5,1], chi~U[0.5,1], seeded azimuths, p_y = 0.9 circular; "
+                    "RK4 h=1 to t_end=2e4, manifold correction every step (Newton tol 1e-10), "
+                    "FLI from two trajectories d0=1e-9 renormalised every 100 steps, threshold 6",
+        "orbits": int(n), "h": H_STEP, "t_end": T_END,
+        "l2": "inputs smaller than L2; a 256 MiB buffer is written before every timed step",
+    }
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU oracle
+def cpu_oracle_rate(cells, target_s=15.0, steps_cap=20000):
+    """Time the CPU oracle (OpenMP over orbits, all host cores) on a bounded
+    sample of the workload; returns (orbit-steps/s, sample description, cores)."""
+    import oracle
+    from paper_1802_00147_gb300 import workloads as W
+    cores = oracle.max_threads()
+    # calibrate on a small sample
+    cal, _ = W.subset(cells, max(cores * 4, 64), seed=31)
+    t0 = time.perf_counter()
+    o = oracle.scan(oracle.setup_cells(cal[:, :9]), cal[:, W.BETA], H_STEP, 500, oracle.config())
+    dt = time.perf_counter() - t0
+    rate0 = o["t_stop"].sum() / H_STEP / dt
+    nsteps = steps_cap
+    m = int(max(cores, min(cells.shape[0], rate0 * target_s / nsteps)))
+    m = max(cores, (m // cores) * cores)
+    sub, _ = W.subset(cells, m, seed=32)
+    y0 = oracle.setup_cells(sub[:, :9])
+    t0 = time.perf_counter()
+    o = oracle.scan(y0, sub[:, W.BETA], H_STEP, nsteps, oracle.config())
+    dt = time.perf_counter() - t0
+    steps_done = float(o["t_stop"].sum() / H_STEP)
+    return (steps_done / dt, "%d seeded orbits of the 314x314 scan to t_end=%g (%d orbit-steps, %.1f s)"
+            % (m, nsteps * H_STEP, steps_done, dt), cores, dt)
+
+
+# -------------------------------------------------------------- reference
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cells = workload()
+    # calibrate once; every step is the same bounded sample
+    rate, sample, cores, dt = cpu_oracle_rate(cells, target_s=8.0)
+    import oracle
+    from paper_1802_00147_gb300 import workloads as W
+    m = int(sample.split()[0])
+    sub, _ = W.subset(cells, m, seed=32)
+    y0 = oracle.setup_cells(sub[:, :9])
+    for _ in range(args.warmup):
+        oracle.scan(y0, sub[:, W.BETA], H_STEP, int(T_END / H_STEP), oracle.config())
+    t0 = time.perf_counter()
+    steps = 0.0
+    for _ in range(args.steps):
+        o = oracle.scan(y0, sub[:, W.BETA], H_STEP, int(T_END / H_STEP), oracle.config())
+        steps += float(o["t_stop"].sum() / H_STEP)
+    dt = time.perf_counter() - t0
+    value = steps / dt
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(workload_desc(cells.shape[0]), sample=sample),
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "each step: " + sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- ours
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1802_00147_gb300 as pn
+    from paper_1802_00147_gb300 import build as pnbuild
+    from paper_1802_00147_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    pnbuild.build()
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+    cells_h = workload(rank, args.orbits)
+    n = cells_h.shape[0]
+    t_end = args.t_end
+    dev = torch.device("cuda", local_rank)
+    cells_d = torch.as_tensor(np.ascontiguousarray(cells_h[:, :9]), device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    scan = pn.Scan(cells_h[:, W.BETA], device=True)
+    scan.setup(cells_d)
+    if args.profile:
+        shape = {"schedule": 2, "block_size": 128, "chunk_steps": 500, "blocks_per_sm": 0}
+        fp64_measured = float("nan")
+    else:
+        shape = scan.autotune(2000)
+        fp64_measured = scan.fp64_peak(400_000)
+
+    def step():
+        flush.fill_(1)
+        scan.setup(cells_d)
+        scan.run(t_end, H_STEP)
+        return scan.summary()          # final integrals + reduction; synchronises
+
+    for _ in range(args.warmup):
+        summ = step()
+    if dist:
+        td.barrier()
+    torch.cuda.synchronize()
+    kern_ms = []
+    steps_total = 0
+    iters_total = 0
+    with ClockSampler(local_rank) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            summ = step()
+            kern_ms.append(scan.last_run_timing()[0])
+            steps_total += summ["orbit_steps"]
+            iters_total += summ["newton_iters"]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            td.barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if dist:
+        t = torch.tensor([elapsed], device=dev)
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        elapsed = float(t.item())
+        tot = torch.tensor([float(steps_total)], device=dev)
+        td.all_reduce(tot, op=td.ReduceOp.SUM)
+        steps_all = float(tot.item())
+    else:
+        steps_all = float(steps_total)
+    value = steps_all / elapsed
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "orbits": n, "t_end": t_end, "value": value,
+                              "ms_per_step": elapsed / args.steps * 1e3,
+                              "kernel_ms": float(np.mean(kern_ms))}), flush=True)
+        scan.close()
+        return
+
+    # end-to-end through the C ABI with host buffers (H2D of the cells and
+    # D2H of the per-orbit results inside the timed region)
+    host = pn.Scan(cells_h[:, W.BETA], device=False)
+    cells9 = np.ascontiguousarray(cells_h[:, :9])
+    out = dict(states=np.empty((n, 12)), integrals=np.empty((n, 6)), fli=np.empty(n),
+               status=np.empty(n, np.int32), t_stop=np.empty(n))
+    host.setup(cells9)
+    host.run(t_end, H_STEP)
+    pn.scan_read(host.h, **out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = 0
+    e2e_k = max(1, args.steps)
+    for _ in range(e2e_k):
+        flush.fill_(1)
+        host.setup(cells9)
+        host.run(t_end, H_STEP)
+        pn.scan_read(host.h, **out)
+        e2e_steps += int(np.round(out["t_stop"].sum() / H_STEP))
+    e2e_dt = time.perf_counter() - t0
+    host.close()
+    h2d = cells9.nbytes
+    d2h = sum(a.nbytes for a in out.values())
+
+    if rank != 0:
+        return
+    ms_kernel = float(np.mean(kern_ms))
+    flops = algorithmic_flops(summ["orbit_steps"], summ["newton_iters"])
+    achieved = flops / (ms_kernel * 1e-3) / 1e12
+    cpu_rate, cpu_sample, cores, _ = cpu_oracle_rate(cells_h, target_s=15.0)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(workload_desc(n), schedule=shape, parallelism="dp%d (independent scans)" % world),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_NOMINAL_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_NOMINAL_TFLOPS, "traffic": None,
+                     "kernel": "k_integrate_queue", "kernel_ms": ms_kernel,
+                     "flops_per_launch": flops,
+                     "peak_measured_dfma": fp64_measured,
+                     "frac_of_measured": achieved / fp64_measured},
+        "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": cpu_sample},
+        "e2e": {"value": e2e_steps / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": 5 * args.steps,
+        "clocks": clk.summary(),
+        "scan": {k: summ[k] for k in ("n_chaotic", "status_count", "max_dE", "max_dJ", "max_dJ_all",
+                                      "n_final_fallback", "max_dS", "fli_mean", "newton_iters",
+                                      "n_skip", "orbit_steps")},
+    }
+    print(json.dumps(line), flush=True)
+    scan.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--orbits", type=int, default=0,
+                    help="seeded subset of the 314x314 scan (0: all 98,596); profiling only")
+    ap.add_argument("--t-end", type=float, default=T_END, help="integration time (profiling only)")
+    ap.add_argument("--profile", action="store_true",
+                    help="time the device path only (no autotune, e2e or CPU leg) for ncu runs")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(local_rank)
+        td.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as td
+        td.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * pnscan.h -- C ABI of the GB300 scan library (libpnscan.so).
+ *
+ * Batched phase-space scan of the conservative post-Newtonian Hamiltonian of
+ * spinning compact binaries, after Ran, Liu & Zhong, "GPU accelerated
+ * manifold correction method for spinning compact binaries"
+ * (arXiv:1802.00147):
+ *   - H = H_N + H_1PN + H_2PN + H_SO(1.5PN) + H_S1S2(2PN) [+ H_QM]      Sec. 2, Eqs. 1-5
+ *   - Hamilton's equations and spin precession                          Eqs. 6-9
+ *   - a fixed-step explicit Runge-Kutta step (classical RK4)            Sec. 3A
+ *   - manifold correction after every step: spin lengths (Eq. 10), then
+ *     dual scaling p = alpha p*, r = beta r* with (alpha, beta) from E and
+ *     |J| by Newton's method                                            Eqs. 11-13, Sec. 3A
+ *   - fast Lyapunov indicator from two nearby trajectories with periodic
+ *     renormalisation                                                   Secs. 3B-3C
+ *
+ * Units: G = c = M = 1.  r in M, p in mu, energies in mu, t in M, spins in
+ * M^2 (S_i = chi_i m_i^2 S_hat_i).  A state is 12 doubles
+ * (rx, ry, rz, px, py, pz, S1x, S1y, S1z, S2x, S2y, S2z).
+ *
+ * Conventions shared by every entry point:
+ *   - Return 0 (PNSCAN_OK) or a negative PNSCAN_ERR_* code; scan_strerror()
+ *     names it.  Per-orbit failures are reported in the status array, never
+ *     in the return code.
+ *   - Pointers are host pointers unless scan_params.device_ptrs == 1, in
+ *     which case every array argument (of scan_params and of the calls on
+ *     the handle) is a device pointer on the current CUDA device.
+ *   - The caller owns every input and output array; the handle owns its
+ *     device buffers (allocated with scan_params.alloc_fn if given, else
+ *     cudaMalloc) and frees them in scan_destroy.
+ *   - Work is issued on scan_params.cuda_stream (a cudaStream_t; NULL is the
+ *     legacy default stream).  scan_setup and scan_run return once the work
+ *     is queued; scan_read and scan_summary synchronise the stream.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ *
+ * The library computes nothing on the CPU: there is no host fallback.
+ */
+#ifndef PNSCAN_H
+#define PNSCAN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define PNSCAN_OK 0
+#define PNSCAN_ERR_ARG (-1)      /* invalid argument or size */
+#define PNSCAN_ERR_CUDA (-2)     /* a CUDA runtime call failed */
+#define PNSCAN_ERR_OOM (-3)      /* device allocation failed */
+#define PNSCAN_ERR_TIMEOUT (-4)  /* host watchdog expired waiting for the stream */
+#define PNSCAN_ERR_STATE (-5)    /* call out of order (e.g. scan_run before any initial state) */
+#define PNSCAN_ERR_KERNEL (-6)   /* a bounded device-side wait gave up; results of the run are invalid */
+#define PNSCAN_ERR_NODEVICE (-7) /* no CUDA device */
+
+/* ---- per-orbit status (scan_read) ---- */
+#define PNSCAN_ORBIT_RUNNING 0        /* not yet at t_end of the last run (never after a completed run) */
+#define PNSCAN_ORBIT_DONE 1           /* reached t_end */
+#define PNSCAN_ORBIT_MERGED 2         /* |r| < r_merge */
+#define PNSCAN_ORBIT_ESCAPED 3        /* |r| > r_escape */
+#define PNSCAN_ORBIT_FLI_SATURATED 4  /* FLI >= fli_cap at a renormalisation */
+#define PNSCAN_ORBIT_NONFINITE 5      /* a state component became Inf/NaN */
+
+/* ---- integrator scheduling ---- */
+#define PNSCAN_SCHED_AUTO 0    /* use the autotuned choice (scan_autotune), else QUEUE */
+#define PNSCAN_SCHED_STATIC 1  /* one orbit per thread, one pass over the batch */
+#define PNSCAN_SCHED_QUEUE 2   /* persistent work-queue kernel over (32-orbit group, step chunk) tasks */
+
+/* Per-scan configuration.  scan_params_default() fills the paper's values. */
+typedef struct scan_params {
+    int64_t n;               /* number of orbits (>= 0) */
+    const double *beta_m;    /* [n] mass ratio m1/m2 in (0, 1] (Sec. 2); required if n > 0 */
+    const double *kappa1;    /* [n] quadrupole-monopole multipliers; NULL = 1 (black holes) */
+    const double *kappa2;    /* [n] */
+    int pn_order;            /* 0: Newtonian, 1: +1PN, 2: +2PN orbital terms (default 2) */
+    int use_so;              /* 1.5PN spin-orbit (default 1) */
+    int use_ss;              /* 2PN S1-S2 spin-spin, Eq. 3 (default 1) */
+    int use_qm;              /* spin-induced quadrupole-monopole, Eqs. 4-5 (default 0) */
+    int correct;             /* manifold correction after every step (default 1) */
+    double newton_tol;       /* Newton stop: |d alpha|, |d beta| <= tol (default 1e-10, Sec. 3A) */
+    int newton_max;          /* Newton iteration cap (default 50) */
+    double newton_det_min;   /* a step whose dual-scaling Jacobian has |det| <= det_min
+                                (|J11 J22| + |J12 J21|) restores E by scaling p alone
+                                (default 1e-5) */
+    double fli_d0;           /* separation of the two trajectories (default 1e-9) */
+    int fli_renorm_steps;    /* renormalise every this many steps (default 100; <= 0: never) */
+    double fli_thresh;       /* FLI above this is chaotic (default 6) */
+    double fli_cap;          /* stop an orbit when FLI >= cap (default 0: never) */
+    double r_merge;          /* stop when |r| < r_merge (default 6; <= 0: never) */
+    double r_escape;         /* stop when |r| > r_escape (default 1e3; <= 0: never) */
+    int device_ptrs;         /* 1: array arguments are device pointers (default 0) */
+    void *cuda_stream;       /* cudaStream_t for all work of the handle (default NULL) */
+    int schedule;            /* PNSCAN_SCHED_* (default AUTO) */
+    int block_size;          /* threads per block, 32..128, multiple of 32 (0: 128) */
+    int chunk_steps;         /* steps per work-queue task (0: 500) */
+    int blocks_per_sm;       /* resident blocks per SM for the queue kernel (0: occupancy maximum) */
+    int use_graph;           /* 1: capture the queue run in a CUDA graph and replay it (default 1) */
+    double sync_timeout_s;   /* host watchdog for synchronising calls (default 0: wait forever) */
+    void *(*alloc_fn)(size_t bytes, void *ctx);  /* optional device allocator (e.g. PyTorch's) */
+    void (*free_fn)(void *ptr, void *ctx);
+    void *alloc_ctx;
+} scan_params;
+
+typedef struct scan_handle scan_handle;   /* opaque, library-owned */
+
+/* Scan-level reduction (Sec. 3C scan outcome), filled by scan_summary. */
+typedef struct scan_summary_t {
+    int64_t n;
+    int64_t n_chaotic;          /* orbits DONE or FLI_SATURATED with FLI > fli_thresh */
+    int64_t status_count[6];    /* orbits per PNSCAN_ORBIT_* value */
+    int64_t newton_iters;       /* Newton iterations, all orbits, both trajectories */
+    int64_t n_skip;             /* corrections whose scaling was skipped */
+    int64_t orbit_steps;        /* sum over orbits of steps taken since the initial state */
+    double max_dE;              /* max |E - E0| / |E0| over DONE orbits */
+    double max_dJ;              /* max ||J| - J0| / J0 over DONE orbits whose last step was dual-scaled */
+    double max_dJ_all;          /* the same over all DONE orbits */
+    int64_t n_final_fallback;   /* DONE orbits whose last step fell where the dual scaling is
+                                   singular (E restored by velocity scaling, |J| not) */
+    double max_dS;              /* max ||S_i| - |S_i|0| / |S_i|0 over DONE orbits */
+    double fli_max;             /* max(FLI, 0) over DONE orbits */
+    double fli_mean;            /* mean FLI over DONE orbits */
+} scan_summary_t;
+
+/* Fill *p with the defaults listed above (n = 0, no arrays).  Returns
+ * PNSCAN_ERR_ARG if p is NULL. */
+int scan_params_default(scan_params *p);
+
+/* Validate *p, copy the per-orbit parameters to the device and allocate the
+ * structure-of-arrays orbit state (about 330 bytes per orbit).  On success
+ * *out receives a new handle; on failure *out is NULL.  Errors: ARG (bad
+ * sizes, flags or beta_m outside (0,1]), OOM, CUDA, NODEVICE. */
+int scan_create(const scan_params *p, scan_handle **out);
+
+/* Initial conditions of a scan grid on the device (Sec. 3C).  cells is n x 9
+ * row-major: (x0, pfac, theta1, phi1, theta2, phi2, beta, chi1, chi2) with
+ * r = (x0, 0, 0), p = (0, pfac / sqrt(x0), 0) and
+ * S_i = chi_i m_i^2 (sin th_i cos ph_i, sin th_i sin ph_i, cos th_i),
+ * m1 = beta/(1+beta), m2 = 1/(1+beta).  Then computes the reference
+ * integrals (E0, J0, |S_i|0) and places the shadow trajectory fli_d0 away
+ * along x; resets time, FLI and status.  Errors: ARG, CUDA. */
+int scan_setup(scan_handle *h, const double *cells);
+
+/* Integrate every running orbit from its current time to t_end with step
+ * h_step (number of steps = round((t_end - t) / h_step), t the handle's
+ * current time).  If initial_states (n x 12 row-major) is not NULL it first
+ * replaces the state and resets as scan_setup does; if it is NULL the run
+ * continues from the device-resident state (chunked runs reproduce one long
+ * run exactly).  Errors: ARG (t_end < t, h_step <= 0 or too many steps),
+ * STATE (no state loaded yet), CUDA, KERNEL (reported by the next
+ * synchronising call). */
+int scan_run(scan_handle *h, const double *initial_states, double t_end, double h_step);
+
+/* Copy results out (synchronises the stream).  Any output pointer may be NULL.
+ *   states    n x 12  main trajectory at t_stop (or t_end)
+ *   integrals n x 6   (E0, E, J0, |J|, |S1|, |S2|) of the main trajectory
+ *   fli       n       FLI = sum_k log10(d_k/d0) + log10(d(t)/d0)
+ *   status    n       PNSCAN_ORBIT_*
+ *   t_stop    n       time at which the orbit stopped (t_end if DONE)
+ * Errors: STATE, CUDA, KERNEL, TIMEOUT. */
+int scan_read(scan_handle *h, double *states, double *integrals, double *fli,
+              int32_t *status, double *t_stop);
+
+/* Diagnostics (synchronises).  shadow n x 12 (shadow trajectory),
+ * newton_iters n (Newton iterations of both trajectories), n_skip n (steps
+ * of either trajectory whose dual scaling was singular or did not converge),
+ * last_kind n (correction of the main trajectory's last step: 0 dual
+ * scaling, 2 velocity scaling of p alone, 1 none).  Any pointer may be NULL. */
+int scan_read_diag(scan_handle *h, double *shadow, int32_t *newton_iters, int32_t *n_skip,
+                   int32_t *last_kind);
+
+/* Scan-level reduction on the device: chaotic count, integral drifts, status
+ * histogram (synchronises; *out is a host struct).  Errors: ARG, STATE, CUDA. */
+int scan_summary(scan_handle *h, scan_summary_t *out);
+
+/* Pick the integrator schedule, block size, chunk length and blocks per SM
+ * by timing candidate launches on a copy of the handle's current state for
+ * `steps` steps (the state itself is left unchanged).  The choice is kept in
+ * the handle and used by later scan_run calls with schedule AUTO; it is also
+ * written to the optional outputs.  Errors: ARG, STATE, CUDA. */
+int scan_autotune(scan_handle *h, int steps, int *schedule, int *block_size, int *chunk_steps,
+                  int *blocks_per_sm);
+
+/* Device time of the integrator launches of the last scan_run (CUDA events
+ * on the handle's stream; synchronises).  *ms and *launches may be NULL. */
+int scan_last_run_timing(scan_handle *h, double *ms, int *launches);
+
+/* Time `iters` x 4 x threads x blocks dependent DFMA on the handle's stream
+ * and return the achieved FP64 rate (TFLOP/s, 2 flops per DFMA).  blocks =
+ * threads = 0 picks 4 warps on every SM.  Used to measure the FP64 pipe's
+ * peak.  Errors: ARG, CUDA. */
+int scan_fp64_peak(scan_handle *h, int iters, double *tflops);
+
+/* Free the handle's device buffers and the handle (NULL is a no-op). */
+void scan_destroy(scan_handle *h);
+
+/* Static description of an error code. */
+const char *scan_strerror(int code);
+
+/* Library version string. */
+const char *scan_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PNSCAN_H */

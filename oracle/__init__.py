@@ -63,7 +63,7 @@ def lib():
         L.orc_correct.restype = i
         L.orc_setup_cell.argtypes = [dp, dp]
         L.orc_scan.argtypes = [i64, dp, dp, dp, dp, P(Config), d, i64, dp, dp, dp, dp,
-                               P(_ct.c_int32), dp, P(i64), P(_ct.c_int32), i]
+                               P(_ct.c_int32), dp, P(i64), P(_ct.c_int32), P(_ct.c_int32), i]
         L.orc_scan.restype = i
         L.orc_trace.argtypes = [dp, d, d, d, P(Config), d, i64, i64, dp]
         L.orc_trace.restype = i
@@ -123,7 +123,8 @@ def integrals(s, y):
 
 
 def correct(s, y, ref, newton_tol=1e-10, newton_max=50, det_min=1e-5):
-    """Returns (y_corrected, code, iters, (alpha, beta))."""
+    """Returns (y_corrected, code, iters, (alpha, beta)); code 0 dual scaling,
+    2 velocity scaling (singular dual scaling), 1 nothing applied."""
     y = _vec(y).copy()
     ref = _vec(ref)
     it = _ct.c_int(0)
@@ -152,7 +153,8 @@ def scan(y0, beta, h, nsteps, cfg=None, kappa1=None, kappa2=None, nthreads=0):
     k2 = None if kappa2 is None else _np.ascontiguousarray(_np.broadcast_to(kappa2, (n,)), dtype=_np.float64)
     out = dict(y=_np.zeros((n, 12)), ys=_np.zeros((n, 12)), integrals=_np.zeros((n, 6)),
                fli=_np.zeros(n), status=_np.zeros(n, dtype=_np.int32), t_stop=_np.zeros(n),
-               newton_iters=_np.zeros(n, dtype=_np.int64), n_skip=_np.zeros(n, dtype=_np.int32))
+               newton_iters=_np.zeros(n, dtype=_np.int64), n_skip=_np.zeros(n, dtype=_np.int32),
+               last_kind=_np.zeros(n, dtype=_np.int32))
     P = _ct.POINTER
     rc = lib().orc_scan(n, _dp(y0), _dp(beta),
                         None if k1 is None else _dp(k1), None if k2 is None else _dp(k2),
@@ -160,7 +162,8 @@ def scan(y0, beta, h, nsteps, cfg=None, kappa1=None, kappa2=None, nthreads=0):
                         _dp(out["y"]), _dp(out["ys"]), _dp(out["integrals"]), _dp(out["fli"]),
                         out["status"].ctypes.data_as(P(_ct.c_int32)), _dp(out["t_stop"]),
                         out["newton_iters"].ctypes.data_as(P(_ct.c_int64)),
-                        out["n_skip"].ctypes.data_as(P(_ct.c_int32)), int(nthreads))
+                        out["n_skip"].ctypes.data_as(P(_ct.c_int32)),
+                        out["last_kind"].ctypes.data_as(P(_ct.c_int32)), int(nthreads))
     if rc != 0:
         raise ValueError("orc_scan rejected its arguments")
     return out

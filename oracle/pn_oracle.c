@@ -311,8 +311,8 @@ int orc_correct(const orc_sys *s, double y[12], const double ref[4],
         det = A * D - B * C;
         /* The dual scaling is singular where alpha p*.dH/dp = beta r*.dH/dr
          * (twice per orbit); there rounding noise in F would be amplified
-         * by 1/det.  Below det_min relative cancellation the step's
-         * scaling is skipped (the paper does not treat this case). */
+         * by 1/det.  Below det_min relative cancellation the dual scaling
+         * is not used for this step (the paper does not treat this case). */
         if (!(fabs(det) > det_min * (fabs(A * D) + fabs(B * C))) || !isfinite(det)) break;
         da = (F1 * D - B * F2) / det;
         db = (A * F2 - C * F1) / det;
@@ -324,18 +324,51 @@ int orc_correct(const orc_sys *s, double y[12], const double ref[4],
             break;
         }
     }
-    if (iters) *iters = it > newton_max ? newton_max : it;
-    if (alpha_beta) {
-        alpha_beta[0] = alpha;
-        alpha_beta[1] = beta;
+    if (it > newton_max) it = newton_max;
+    if (converged) {
+        for (i = 0; i < 3; i++) {
+            y[i] = beta * rs[i];
+            y[3 + i] = alpha * ps[i];
+        }
+        if (iters) *iters = it;
+        if (alpha_beta) {
+            alpha_beta[0] = alpha;
+            alpha_beta[1] = beta;
+        }
+        return ORC_CORR_OK;
     }
-    if (!converged)
-        return ORC_CORR_SKIPPED; /* keep the spin-corrected r*, p* */
-    for (i = 0; i < 3; i++) {
-        y[i] = beta * rs[i];
-        y[3 + i] = alpha * ps[i];
+    /* Singular (or non-converged) dual scaling: restore the energy alone by
+     * velocity scaling, p = a p*, H(r*, a p*, S) = E0, Newton in a from 1
+     * (the momentum-scaling correction of Sec. 1, Wu et al. 2007).  |J| is
+     * left to the next step's dual scaling. */
+    {
+        double a = 1.0, g2[12];
+        int k, ok = 0;
+        memcpy(yb, y, sizeof(yb));
+        for (k = 1; k <= newton_max; k++) {
+            double F, A, da;
+            for (i = 0; i < 3; i++) yb[3 + i] = a * ps[i];
+            F = orc_hamiltonian(s, yb) - ref[0];
+            orc_gradient(s, yb, g2);
+            A = dot3(g2 + 3, ps);             /* dH/da = dH/dp . p* */
+            da = F / A;
+            if (!isfinite(da)) break;
+            a = a - da;
+            if (fabs(da) <= newton_tol) {
+                ok = 1;
+                break;
+            }
+        }
+        if (k > newton_max) k = newton_max;
+        if (iters) *iters = it + k;
+        if (alpha_beta) {
+            alpha_beta[0] = ok ? a : 1.0;
+            alpha_beta[1] = 1.0;
+        }
+        if (!ok) return ORC_CORR_SKIPPED;  /* keep the spin-corrected r*, p* */
+        for (i = 0; i < 3; i++) y[3 + i] = a * ps[i];
+        return ORC_CORR_VELOCITY;
     }
-    return ORC_CORR_OK;
 }
 
 /* ------------------------------------------------------------ cell set-up */
@@ -388,11 +421,12 @@ static double distance12(const double a[12], const double b[12])
 static void integrate_one(const orc_config *cfg, const orc_sys *s, const double y0[12],
                           double h, int64_t nsteps, double y[12], double ys[12],
                           double integ[6], double *fli_out, int32_t *status_out,
-                          double *t_stop_out, int64_t *iters_out, int32_t *skip_out)
+                          double *t_stop_out, int64_t *iters_out, int32_t *skip_out,
+                          int32_t *last_kind_out)
 {
     double ref[4], refs[4], acc = 0.0, d0 = cfg->fli_d0;
     int64_t k, iters = 0;
-    int32_t st = ORC_DONE, skips = 0;
+    int32_t st = ORC_DONE, skips = 0, last_kind = ORC_CORR_OK;
     double t_stop = (double)nsteps * h;
 
     memcpy(y, y0, 12 * sizeof(double));
@@ -405,8 +439,8 @@ static void integrate_one(const orc_config *cfg, const orc_sys *s, const double 
         int it = 0;
         orc_rk4_step(s, y, h);
         if (cfg->correct) {
-            if (orc_correct(s, y, ref, cfg->newton_tol, cfg->newton_max, cfg->det_min, &it, 0))
-                skips++;
+            last_kind = orc_correct(s, y, ref, cfg->newton_tol, cfg->newton_max, cfg->det_min, &it, 0);
+            if (last_kind != ORC_CORR_OK) skips++;
             iters += it;
         }
         orc_rk4_step(s, ys, h);
@@ -447,6 +481,7 @@ static void integrate_one(const orc_config *cfg, const orc_sys *s, const double 
     *t_stop_out = t_stop;
     *iters_out = iters;
     *skip_out = skips;
+    *last_kind_out = last_kind;
 }
 
 int orc_scan(int64_t n, const double *y0, const double *beta,
@@ -454,11 +489,11 @@ int orc_scan(int64_t n, const double *y0, const double *beta,
              const orc_config *cfg, double h, int64_t nsteps,
              double *y_out, double *ys_out, double *integrals, double *fli,
              int32_t *status, double *t_stop, int64_t *newton_iters,
-             int32_t *n_skip, int nthreads)
+             int32_t *n_skip, int32_t *last_kind, int nthreads)
 {
     int64_t i;
     if (n < 0 || nsteps < 0 || !y0 || !beta || !cfg || !y_out || !ys_out || !integrals ||
-        !fli || !status || !t_stop || !newton_iters || !n_skip)
+        !fli || !status || !t_stop || !newton_iters || !n_skip || !last_kind)
         return -1;
 #ifdef _OPENMP
     if (nthreads <= 0) nthreads = omp_get_max_threads();
@@ -470,7 +505,7 @@ int orc_scan(int64_t n, const double *y0, const double *beta,
                      cfg->pn_order, cfg->use_so, cfg->use_ss, cfg->use_qm);
         integrate_one(cfg, &s, y0 + 12 * i, h, nsteps, y_out + 12 * i, ys_out + 12 * i,
                       integrals + 6 * i, fli + i, status + i, t_stop + i, newton_iters + i,
-                      n_skip + i);
+                      n_skip + i, last_kind + i);
     }
     (void)nthreads;
     return 0;

@@ -52,8 +52,9 @@ enum {
     ORC_FLI_SATURATED = 4, ORC_NONFINITE = 5
 };
 
-/* Correction outcome. */
-enum { ORC_CORR_OK = 0, ORC_CORR_SKIPPED = 1 };
+/* Correction outcome: dual scaling applied; singular dual scaling replaced
+ * by velocity scaling of p alone; nothing converged (r*, p* kept). */
+enum { ORC_CORR_OK = 0, ORC_CORR_SKIPPED = 1, ORC_CORR_VELOCITY = 2 };
 
 void orc_sys_init(orc_sys *s, double beta, double kappa1, double kappa2,
                   int pn_order, int use_so, int use_ss, int use_qm);
@@ -80,8 +81,11 @@ void orc_rk4_step(const orc_sys *s, double y[12], double h);
 void orc_integrals(const orc_sys *s, const double y[12], double out[7]);
 
 /* Manifold correction (Eqs. 10-13) toward ref = (E0, J0, |S1|0, |S2|0), in
- * place.  Returns ORC_CORR_OK or ORC_CORR_SKIPPED; *iters gets the number of
- * Newton iterations; alpha_beta (nullable) gets the scale factors. */
+ * place.  Returns ORC_CORR_OK, ORC_CORR_VELOCITY (the dual scaling was
+ * singular, |det| <= det_min (|J11 J22| + |J12 J21|), or did not converge:
+ * p alone was scaled to restore E) or ORC_CORR_SKIPPED; *iters gets the
+ * number of Newton iterations of both solves; alpha_beta (nullable) gets the
+ * scale factors applied. */
 int orc_correct(const orc_sys *s, double y[12], const double ref[4],
                 double newton_tol, int newton_max, double det_min,
                 int *iters, double alpha_beta[2]);
@@ -96,14 +100,15 @@ void orc_setup_cell(const double cell[9], double y[12]);
  * n*12; kappa1/kappa2 nullable (1.0); outputs:
  *   integrals n*6 = (E0, E, J0, |J|, |S1|, |S2|) of the main trajectory,
  *   fli n, status n, t_stop n, newton_iters n (sum over both trajectories),
- *   n_skip n (corrections rejected).
+ *   n_skip n (steps whose dual scaling was replaced by velocity scaling or
+ *   skipped), last_kind n (ORC_CORR_* of the main trajectory's last step).
  * nthreads <= 0: all OpenMP threads.  Returns 0, or -1 on bad arguments. */
 int orc_scan(int64_t n, const double *y0, const double *beta,
              const double *kappa1, const double *kappa2,
              const orc_config *cfg, double h, int64_t nsteps,
              double *y_out, double *ys_out, double *integrals, double *fli,
              int32_t *status, double *t_stop, int64_t *newton_iters,
-             int32_t *n_skip, int nthreads);
+             int32_t *n_skip, int32_t *last_kind, int nthreads);
 
 /* Same integrator without the shadow trajectory, recording the state after
  * every `every` steps into trace[(nsteps/every) * 12] (single orbit). */

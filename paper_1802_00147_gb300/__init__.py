@@ -1,0 +1,314 @@
+"""GB300 (sm_103a) batched scan of manifold-corrected post-Newtonian spinning
+compact binaries (arXiv:1802.00147).
+
+This module is a thin ctypes binding over ``libpnscan.so`` (C ABI in
+``include/pnscan.h``): it marshals arguments and nothing else.  Every step of
+the scan runs in the library's CUDA kernels; there is no CPU fallback, and
+loading fails loudly if the library has not been built
+(``python -m paper_1802_00147_gb300.build`` or ``__graft_entry__.build()``).
+
+Functions keep the C names (``scan_create``, ``scan_setup``, ``scan_run``,
+``scan_read``, ``scan_summary``, ...).  ``Scan`` bundles them for numpy host
+arrays or torch CUDA tensors.
+"""
+import ctypes as _ct
+import os as _os
+
+import numpy as _np
+
+__all__ = [
+    "ScanParams", "ScanSummary", "ScanError", "lib", "library_path",
+    "scan_params_default", "scan_create", "scan_setup", "scan_run", "scan_read",
+    "scan_read_diag", "scan_summary", "scan_autotune", "scan_last_run_timing",
+    "scan_fp64_peak", "scan_destroy", "scan_strerror", "scan_version", "Scan",
+    "OK", "ORBIT_RUNNING", "ORBIT_DONE", "ORBIT_MERGED", "ORBIT_ESCAPED",
+    "ORBIT_FLI_SATURATED", "ORBIT_NONFINITE", "SCHED_AUTO", "SCHED_STATIC", "SCHED_QUEUE",
+]
+
+_HERE = _os.path.dirname(_os.path.abspath(__file__))
+library_path = _os.path.join(_HERE, "libpnscan.so")
+
+OK = 0
+ERR_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_STATE, ERR_KERNEL, ERR_NODEVICE = -1, -2, -3, -4, -5, -6, -7
+ORBIT_RUNNING, ORBIT_DONE, ORBIT_MERGED, ORBIT_ESCAPED, ORBIT_FLI_SATURATED, ORBIT_NONFINITE = range(6)
+SCHED_AUTO, SCHED_STATIC, SCHED_QUEUE = 0, 1, 2
+
+_ALLOC_FN = _ct.CFUNCTYPE(_ct.c_void_p, _ct.c_size_t, _ct.c_void_p)
+_FREE_FN = _ct.CFUNCTYPE(None, _ct.c_void_p, _ct.c_void_p)
+
+
+class ScanParams(_ct.Structure):
+    _fields_ = [
+        ("n", _ct.c_int64),
+        ("beta_m", _ct.c_void_p), ("kappa1", _ct.c_void_p), ("kappa2", _ct.c_void_p),
+        ("pn_order", _ct.c_int), ("use_so", _ct.c_int), ("use_ss", _ct.c_int), ("use_qm", _ct.c_int),
+        ("correct", _ct.c_int),
+        ("newton_tol", _ct.c_double), ("newton_max", _ct.c_int), ("newton_det_min", _ct.c_double),
+        ("fli_d0", _ct.c_double), ("fli_renorm_steps", _ct.c_int), ("fli_thresh", _ct.c_double),
+        ("fli_cap", _ct.c_double), ("r_merge", _ct.c_double), ("r_escape", _ct.c_double),
+        ("device_ptrs", _ct.c_int), ("cuda_stream", _ct.c_void_p),
+        ("schedule", _ct.c_int), ("block_size", _ct.c_int), ("chunk_steps", _ct.c_int),
+        ("blocks_per_sm", _ct.c_int), ("use_graph", _ct.c_int), ("sync_timeout_s", _ct.c_double),
+        ("alloc_fn", _ALLOC_FN), ("free_fn", _FREE_FN), ("alloc_ctx", _ct.c_void_p),
+    ]
+
+
+class ScanSummary(_ct.Structure):
+    _fields_ = [
+        ("n", _ct.c_int64), ("n_chaotic", _ct.c_int64), ("status_count", _ct.c_int64 * 6),
+        ("newton_iters", _ct.c_int64), ("n_skip", _ct.c_int64), ("orbit_steps", _ct.c_int64),
+        ("max_dE", _ct.c_double), ("max_dJ", _ct.c_double), ("max_dJ_all", _ct.c_double),
+        ("n_final_fallback", _ct.c_int64), ("max_dS", _ct.c_double),
+        ("fli_max", _ct.c_double), ("fli_mean", _ct.c_double),
+    ]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "status_count"}
+        d["status_count"] = list(self.status_count)
+        return d
+
+
+class ScanError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (where, scan_strerror(code), code))
+
+
+_lib = None
+
+
+def lib():
+    """Load libpnscan.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not _os.path.exists(library_path):
+            raise ImportError("libpnscan.so is missing: build it with __graft_entry__.build() "
+                              "or python -m paper_1802_00147_gb300.build (no CPU fallback exists)")
+        L = _ct.CDLL(library_path)
+        P, vp, i, d = _ct.POINTER, _ct.c_void_p, _ct.c_int, _ct.c_double
+        L.scan_params_default.argtypes = [P(ScanParams)]
+        L.scan_create.argtypes = [P(ScanParams), P(vp)]
+        L.scan_setup.argtypes = [vp, vp]
+        L.scan_run.argtypes = [vp, vp, d, d]
+        L.scan_read.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.scan_read_diag.argtypes = [vp, vp, vp, vp, vp]
+        L.scan_summary.argtypes = [vp, P(ScanSummary)]
+        L.scan_autotune.argtypes = [vp, i, P(i), P(i), P(i), P(i)]
+        L.scan_last_run_timing.argtypes = [vp, P(d), P(i)]
+        L.scan_fp64_peak.argtypes = [vp, i, P(d)]
+        L.scan_destroy.argtypes = [vp]
+        L.scan_destroy.restype = None
+        L.scan_strerror.argtypes = [i]
+        L.scan_strerror.restype = _ct.c_char_p
+        L.scan_version.restype = _ct.c_char_p
+        for name in ("scan_params_default", "scan_create", "scan_setup", "scan_run", "scan_read",
+                     "scan_read_diag", "scan_summary", "scan_autotune", "scan_last_run_timing",
+                     "scan_fp64_peak"):
+            getattr(L, name).restype = i
+        _lib = L
+    return _lib
+
+
+def _check(code, where):
+    if code != OK:
+        raise ScanError(code, where)
+
+
+def _ptr(a):
+    """Address of a numpy array or a torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, _np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+# ------------------------------------------------------------ raw C names
+def scan_params_default():
+    p = ScanParams()
+    _check(lib().scan_params_default(_ct.byref(p)), "scan_params_default")
+    return p
+
+
+def scan_create(params):
+    h = _ct.c_void_p()
+    _check(lib().scan_create(_ct.byref(params), _ct.byref(h)), "scan_create")
+    return h
+
+
+def scan_setup(h, cells):
+    _check(lib().scan_setup(h, _ptr(cells)), "scan_setup")
+
+
+def scan_run(h, initial_states, t_end, h_step):
+    _check(lib().scan_run(h, _ptr(initial_states), float(t_end), float(h_step)), "scan_run")
+
+
+def scan_read(h, states=None, integrals=None, fli=None, status=None, t_stop=None):
+    _check(lib().scan_read(h, _ptr(states), _ptr(integrals), _ptr(fli), _ptr(status), _ptr(t_stop)),
+           "scan_read")
+
+
+def scan_read_diag(h, shadow=None, newton_iters=None, n_skip=None, last_kind=None):
+    _check(lib().scan_read_diag(h, _ptr(shadow), _ptr(newton_iters), _ptr(n_skip), _ptr(last_kind)),
+           "scan_read_diag")
+
+
+def scan_summary(h):
+    s = ScanSummary()
+    _check(lib().scan_summary(h, _ct.byref(s)), "scan_summary")
+    return s
+
+
+def scan_autotune(h, steps):
+    out = [_ct.c_int() for _ in range(4)]
+    _check(lib().scan_autotune(h, int(steps), *[_ct.byref(o) for o in out]), "scan_autotune")
+    return dict(schedule=out[0].value, block_size=out[1].value, chunk_steps=out[2].value,
+                blocks_per_sm=out[3].value)
+
+
+def scan_last_run_timing(h):
+    ms, n = _ct.c_double(), _ct.c_int()
+    _check(lib().scan_last_run_timing(h, _ct.byref(ms), _ct.byref(n)), "scan_last_run_timing")
+    return ms.value, n.value
+
+
+def scan_fp64_peak(h, iters=200_000):
+    t = _ct.c_double()
+    _check(lib().scan_fp64_peak(h, int(iters), _ct.byref(t)), "scan_fp64_peak")
+    return t.value
+
+
+def scan_destroy(h):
+    if h:
+        lib().scan_destroy(h)
+
+
+def scan_strerror(code):
+    return lib().scan_strerror(int(code)).decode()
+
+
+def scan_version():
+    return lib().scan_version().decode()
+
+
+# --------------------------------------------------------------- wrapper
+class Scan:
+    """One scan handle over n orbits.
+
+    ``device=False``: host numpy arrays in and out (copies inside the calls).
+    ``device=True``: torch CUDA tensors in and out; the handle's device
+    buffers come from PyTorch's caching allocator and work runs on the current
+    torch stream.
+    """
+
+    def __init__(self, beta, kappa1=None, kappa2=None, device=False, stream=None, **opts):
+        p = scan_params_default()
+        self.device = bool(device)
+        self._keep = {}
+        if self.device:
+            import torch
+            self._torch = torch
+            dev = torch.device("cuda", torch.cuda.current_device())
+            beta = torch.as_tensor(beta, dtype=torch.float64, device=dev).contiguous()
+            kappa1 = None if kappa1 is None else torch.as_tensor(kappa1, dtype=torch.float64, device=dev).contiguous()
+            kappa2 = None if kappa2 is None else torch.as_tensor(kappa2, dtype=torch.float64, device=dev).contiguous()
+            st = stream if stream is not None else torch.cuda.current_stream()
+            p.cuda_stream = st.cuda_stream
+            p.device_ptrs = 1
+            blocks = self._keep
+
+            def _alloc(nbytes, ctx):
+                t = torch.empty(int(nbytes), dtype=torch.uint8, device=dev)
+                blocks[t.data_ptr()] = t
+                return t.data_ptr()
+
+            def _free(ptr, ctx):
+                blocks.pop(ptr, None)
+
+            self._cb = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+            p.alloc_fn, p.free_fn = self._cb
+        else:
+            beta = _np.ascontiguousarray(beta, dtype=_np.float64)
+            kappa1 = None if kappa1 is None else _np.ascontiguousarray(kappa1, dtype=_np.float64)
+            kappa2 = None if kappa2 is None else _np.ascontiguousarray(kappa2, dtype=_np.float64)
+        self.n = int(beta.shape[0])
+        p.n = self.n
+        p.beta_m, p.kappa1, p.kappa2 = _ptr(beta), _ptr(kappa1), _ptr(kappa2)
+        for k, v in opts.items():
+            if not hasattr(p, k):
+                raise TypeError("unknown scan parameter %r" % k)
+            setattr(p, k, v)
+        self.params = p
+        self._args = (beta, kappa1, kappa2)
+        self.h = scan_create(p)
+
+    def close(self):
+        if getattr(self, "h", None):
+            scan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _arr(self, a, cols):
+        if self.device:
+            t = self._torch.as_tensor(a, dtype=self._torch.float64, device="cuda").contiguous()
+            assert t.numel() == self.n * cols
+            return t
+        a = _np.ascontiguousarray(a, dtype=_np.float64)
+        assert a.size == self.n * cols
+        return a
+
+    def setup(self, cells):
+        """cells: n x 9 (x0, pfac, theta1, phi1, theta2, phi2, beta, chi1, chi2)."""
+        c = self._arr(cells[:, :9], 9)
+        scan_setup(self.h, c)
+        self._cells = c
+
+    def run(self, t_end, h_step, initial_states=None):
+        s = None if initial_states is None else self._arr(initial_states, 12)
+        scan_run(self.h, s, t_end, h_step)
+        self._init = s
+
+    def _out(self, shape, dtype):
+        if self.device:
+            tdt = {_np.float64: self._torch.float64, _np.int32: self._torch.int32}[dtype]
+            return self._torch.empty(shape, dtype=tdt, device="cuda")
+        return _np.empty(shape, dtype=dtype)
+
+    def read(self):
+        n = self.n
+        out = dict(states=self._out((n, 12), _np.float64), integrals=self._out((n, 6), _np.float64),
+                   fli=self._out((n,), _np.float64), status=self._out((n,), _np.int32),
+                   t_stop=self._out((n,), _np.float64))
+        scan_read(self.h, out["states"], out["integrals"], out["fli"], out["status"], out["t_stop"])
+        return out
+
+    def read_diag(self):
+        n = self.n
+        out = dict(shadow=self._out((n, 12), _np.float64), newton_iters=self._out((n,), _np.int32),
+                   n_skip=self._out((n,), _np.int32), last_kind=self._out((n,), _np.int32))
+        scan_read_diag(self.h, out["shadow"], out["newton_iters"], out["n_skip"], out["last_kind"])
+        return out
+
+    def summary(self):
+        return scan_summary(self.h).as_dict()
+
+    def autotune(self, steps):
+        return scan_autotune(self.h, steps)
+
+    def last_run_timing(self):
+        return scan_last_run_timing(self.h)
+
+    def fp64_peak(self, iters=200_000):
+        return scan_fp64_peak(self.h, iters)

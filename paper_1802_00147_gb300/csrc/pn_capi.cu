@@ -1,0 +1,631 @@
+// pn_capi.cu -- implementation of the C ABI declared in include/pnscan.h:
+// handle lifecycle, host <-> device staging, integrator scheduling (static
+// or persistent work queue, optionally replayed from a captured CUDA graph),
+// the launch-shape autotuner, the host watchdog and timing.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "../../include/pnscan.h"
+#include "pn_kernels.cuh"
+
+using namespace pnscan;
+
+struct scan_handle {
+    scan_params p;            // copy; array pointers are not retained
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;     // caller's stream
+    cudaStream_t cap_stream = nullptr; // private stream used for graph capture
+    DevState S{};
+    void* state_block = nullptr;
+    size_t state_bytes = 0;
+    void* queue_block = nullptr;       // QueueState storage
+    size_t queue_bytes = 0;
+    QueueState q{};
+    Summary* dsum = nullptr;
+    double* staging = nullptr;         // n x 12 device staging for host I/O
+    bool loaded = false;
+    double t_now = 0.0;
+    int32_t nstep_now = 0;
+    RunCfg base{};
+    // launch shape (tuned or from params)
+    int sched = PNSCAN_SCHED_QUEUE;
+    int block = 128;
+    int chunk = 500;
+    int bps = 0;
+    bool tuned = false;
+    // timing of the last run
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int last_launches = 0;
+    bool timed = false;
+    // CUDA graph of the queue run
+    cudaGraphExec_t gexec = nullptr;
+    RunCfg gcfg{};
+    int gshape[4] = {0, 0, 0, 0};
+};
+
+namespace {
+
+const char* kVersion = "pnscan 0.1 (sm_103a, FP64)";
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? PNSCAN_OK : (e == cudaErrorMemoryAllocation ? PNSCAN_ERR_OOM : PNSCAN_ERR_CUDA); }
+
+void* dev_alloc(scan_handle* h, size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    if (h->p.alloc_fn) return h->p.alloc_fn(bytes, h->p.alloc_ctx);
+    void* ptr = nullptr;
+    if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return ptr;
+}
+
+void dev_free(scan_handle* h, void* ptr)
+{
+    if (!ptr) return;
+    if (h->p.free_fn) h->p.free_fn(ptr, h->p.alloc_ctx);
+    else cudaFree(ptr);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Carve the structure-of-arrays state out of one allocation.
+size_t layout_state(DevState& S, char* base, int64_t n)
+{
+    const int64_t ld = (n + 31) / 32 * 32;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { char* p = base ? base + off : nullptr; off = align256(off + bytes); return p; };
+    S.n = n;
+    S.ld = ld;
+    S.y = (double*)take(sizeof(double) * 12 * ld);
+    S.ys = (double*)take(sizeof(double) * 12 * ld);
+    S.ref = (double*)take(sizeof(double) * 8 * ld);
+    S.fli_acc = (double*)take(sizeof(double) * ld);
+    S.t = (double*)take(sizeof(double) * ld);
+    S.nstep = (int32_t*)take(sizeof(int32_t) * ld);
+    S.status = (int32_t*)take(sizeof(int32_t) * ld);
+    S.newton_iters = (int32_t*)take(sizeof(int32_t) * ld);
+    S.n_skip = (int32_t*)take(sizeof(int32_t) * ld);
+    S.last_kind = (int32_t*)take(sizeof(int32_t) * ld);
+    S.beta = (double*)take(sizeof(double) * ld);
+    S.kappa1 = (double*)take(sizeof(double) * ld);
+    S.kappa2 = (double*)take(sizeof(double) * ld);
+    S.out = (double*)take(sizeof(double) * 5 * ld);
+    return off;
+}
+
+int sync(scan_handle* h)
+{
+    if (h->p.sync_timeout_s > 0.0) {
+        const auto t0 = std::chrono::steady_clock::now();
+        for (;;) {
+            cudaError_t e = cudaStreamQuery(h->stream);
+            if (e == cudaSuccess) break;
+            if (e != cudaErrorNotReady) return cuda_err(e);
+            const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (el > h->p.sync_timeout_s) return PNSCAN_ERR_TIMEOUT;
+            std::this_thread::sleep_for(std::chrono::microseconds(200));
+        }
+    } else {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_err(e);
+    }
+    // a bounded device-side wait of the work queue that gave up?
+    int err = 0;
+    cudaError_t e = cudaMemcpy(&err, h->q.error, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_err(e);
+    return err ? PNSCAN_ERR_KERNEL : PNSCAN_OK;
+}
+
+RunCfg make_run(const scan_handle* h, double h_step, int32_t nsteps)
+{
+    RunCfg rc = h->base;
+    rc.h = h_step;
+    rc.nstep_base = h->nstep_now;
+    rc.nsteps = nsteps;
+    return rc;
+}
+
+// Copy an array argument to the device staging buffer (or use it in place).
+int stage_in(scan_handle* h, const double* src, size_t count, const double** dev)
+{
+    if (h->p.device_ptrs) {
+        *dev = src;
+        return PNSCAN_OK;
+    }
+    cudaError_t e = cudaMemcpyAsync(h->staging, src, count * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    *dev = h->staging;
+    return cuda_err(e);
+}
+
+int begin_state(scan_handle* h)
+{
+    RunCfg rc = make_run(h, 1.0, 0);
+    int rc_ = cuda_err(launch_init(h->S, rc, h->stream));
+    if (rc_ != PNSCAN_OK) return rc_;
+    h->loaded = true;
+    h->t_now = 0.0;
+    h->nstep_now = 0;
+    return PNSCAN_OK;
+}
+
+int reset_queue(scan_handle* h, cudaStream_t st)
+{
+    return cuda_err(cudaMemsetAsync(h->queue_block, 0, h->queue_bytes, st));
+}
+
+int queue_grid(scan_handle* h, int block, int bps)
+{
+    int occ = queue_blocks_per_sm(block, h->base.flags.use_qm != 0);
+    if (occ <= 0) occ = 1;
+    if (bps <= 0 || bps > occ) bps = occ;
+    return h->num_sms * bps;
+}
+
+// Launch the integrator for one run on stream st (no timing).
+int launch_run(scan_handle* h, const RunCfg& rc, int sched, int block, int chunk, int bps,
+               const DevState& S, cudaStream_t st)
+{
+    if (sched == PNSCAN_SCHED_STATIC) return cuda_err(launch_integrate_static(S, rc, block, st));
+    int r = reset_queue(h, st);
+    if (r != PNSCAN_OK) return r;
+    return cuda_err(launch_integrate_queue(S, rc, h->q, block, queue_grid(h, block, bps), chunk, st));
+}
+
+bool same_run(const RunCfg& a, const RunCfg& b)
+{
+    return a.flags.pn_order == b.flags.pn_order && a.flags.use_so == b.flags.use_so &&
+           a.flags.use_ss == b.flags.use_ss && a.flags.use_qm == b.flags.use_qm &&
+           a.newton.tol == b.newton.tol && a.newton.max_iter == b.newton.max_iter &&
+           a.newton.det_min == b.newton.det_min && a.correct == b.correct && a.h == b.h &&
+           a.d0 == b.d0 && a.renorm == b.renorm && a.fli_cap == b.fli_cap &&
+           a.rmerge2 == b.rmerge2 && a.rescape2 == b.rescape2 && a.nstep_base == b.nstep_base &&
+           a.nsteps == b.nsteps;
+}
+
+int run_graph(scan_handle* h, const RunCfg& rc)
+{
+    const int shape[4] = {h->sched, h->block, h->chunk, h->bps};
+    if (!h->gexec || !same_run(h->gcfg, rc) || std::memcmp(h->gshape, shape, sizeof(shape)) != 0) {
+        if (h->gexec) {
+            cudaGraphExecDestroy(h->gexec);
+            h->gexec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_err(e);
+        int r = launch_run(h, rc, h->sched, h->block, h->chunk, h->bps, h->S, h->cap_stream);
+        e = cudaStreamEndCapture(h->cap_stream, &g);
+        if (r != PNSCAN_OK) {
+            if (g) cudaGraphDestroy(g);
+            return r;
+        }
+        if (e != cudaSuccess) return cuda_err(e);
+        e = cudaGraphInstantiate(&h->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_err(e);
+        h->gcfg = rc;
+        std::memcpy(h->gshape, shape, sizeof(shape));
+    }
+    return cuda_err(cudaGraphLaunch(h->gexec, h->stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+int scan_params_default(scan_params* p)
+{
+    if (!p) return PNSCAN_ERR_ARG;
+    std::memset(p, 0, sizeof(*p));
+    p->pn_order = 2;
+    p->use_so = 1;
+    p->use_ss = 1;
+    p->use_qm = 0;
+    p->correct = 1;
+    p->newton_tol = 1e-10;
+    p->newton_max = 50;
+    p->newton_det_min = 1e-5;
+    p->fli_d0 = 1e-9;
+    p->fli_renorm_steps = 100;
+    p->fli_thresh = 6.0;
+    p->fli_cap = 0.0;
+    p->r_merge = 6.0;
+    p->r_escape = 1e3;
+    p->schedule = PNSCAN_SCHED_AUTO;
+    p->use_graph = 1;
+    return PNSCAN_OK;
+}
+
+int scan_create(const scan_params* p, scan_handle** out)
+{
+    if (!out) return PNSCAN_ERR_ARG;
+    *out = nullptr;
+    if (!p || p->n < 0 || p->n > (int64_t)1 << 31) return PNSCAN_ERR_ARG;
+    if (p->n > 0 && !p->beta_m) return PNSCAN_ERR_ARG;
+    if (p->pn_order < 0 || p->pn_order > 2) return PNSCAN_ERR_ARG;
+    if (!(p->newton_tol > 0.0) || p->newton_max < 1 || p->newton_max > 1000 || !(p->newton_det_min >= 0.0))
+        return PNSCAN_ERR_ARG;
+    if (!(p->fli_d0 > 0.0)) return PNSCAN_ERR_ARG;
+    if (p->block_size && (p->block_size < 32 || p->block_size > 128 || p->block_size % 32)) return PNSCAN_ERR_ARG;
+    if (p->chunk_steps < 0 || p->blocks_per_sm < 0) return PNSCAN_ERR_ARG;
+    if (p->schedule < 0 || p->schedule > 2) return PNSCAN_ERR_ARG;
+    if ((p->alloc_fn == nullptr) != (p->free_fn == nullptr)) return PNSCAN_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return PNSCAN_ERR_NODEVICE;
+    }
+    // beta must lie in (0, 1] (m1 <= m2, Sec. 2)
+    const int64_t n = p->n;
+    if (!p->device_ptrs && n > 0) {
+        for (int64_t i = 0; i < n; i++)
+            if (!(p->beta_m[i] > 0.0 && p->beta_m[i] <= 1.0)) return PNSCAN_ERR_ARG;
+    }
+
+    scan_handle* h = new (std::nothrow) scan_handle();
+    if (!h) return PNSCAN_ERR_OOM;
+    h->p = *p;
+    h->p.beta_m = h->p.kappa1 = h->p.kappa2 = nullptr;
+    h->stream = (cudaStream_t)p->cuda_stream;
+    cudaGetDevice(&h->device);
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    int r = PNSCAN_OK;
+    auto fail = [&](int code) { scan_destroy(h); return code; };
+
+    h->state_bytes = layout_state(h->S, nullptr, n);
+    h->state_block = dev_alloc(h, h->state_bytes);
+    if (!h->state_block) return fail(PNSCAN_ERR_OOM);
+    layout_state(h->S, (char*)h->state_block, n);
+
+    const int64_t groups = (n + 31) / 32;
+    h->queue_bytes = align256(sizeof(unsigned long long)) + align256(sizeof(int)) + align256(sizeof(int) * (groups + 1));
+    h->queue_block = dev_alloc(h, h->queue_bytes + align256(sizeof(Summary)));
+    if (!h->queue_block) return fail(PNSCAN_ERR_OOM);
+    {
+        char* b = (char*)h->queue_block;
+        h->q.next = (unsigned long long*)b;
+        h->q.error = (int*)(b + align256(sizeof(unsigned long long)));
+        h->q.group_done = (int*)(b + align256(sizeof(unsigned long long)) + align256(sizeof(int)));
+        h->dsum = (Summary*)(b + h->queue_bytes);
+    }
+    if (!p->device_ptrs) {
+        h->staging = (double*)dev_alloc(h, sizeof(double) * 12 * (size_t)(n > 0 ? n : 1));
+        if (!h->staging) return fail(PNSCAN_ERR_OOM);
+    }
+    if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess)
+        return fail(PNSCAN_ERR_CUDA);
+    r = reset_queue(h, h->stream);
+    if (r != PNSCAN_OK) return fail(r);
+
+    // per-orbit physical parameters
+    if (n > 0) {
+        const cudaMemcpyKind kind = p->device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        if (cudaMemcpyAsync(h->S.beta, p->beta_m, sizeof(double) * n, kind, h->stream) != cudaSuccess)
+            return fail(PNSCAN_ERR_CUDA);
+        for (int k = 0; k < 2; k++) {
+            const double* src = k == 0 ? p->kappa1 : p->kappa2;
+            double* dst = k == 0 ? h->S.kappa1 : h->S.kappa2;
+            if (src) {
+                if (cudaMemcpyAsync(dst, src, sizeof(double) * n, kind, h->stream) != cudaSuccess)
+                    return fail(PNSCAN_ERR_CUDA);
+            } else {
+                std::vector<double> ones((size_t)n, 1.0);
+                if (cudaMemcpyAsync(dst, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+                    cudaStreamSynchronize(h->stream) != cudaSuccess)
+                    return fail(PNSCAN_ERR_CUDA);
+            }
+        }
+    }
+    // per-run constants
+    RunCfg& b = h->base;
+    b.flags.pn_order = p->pn_order;
+    b.flags.use_so = p->use_so != 0;
+    b.flags.use_ss = p->use_ss != 0;
+    b.flags.use_qm = p->use_qm != 0;
+    b.newton.tol = p->newton_tol;
+    b.newton.max_iter = p->newton_max;
+    b.newton.det_min = p->newton_det_min;
+    b.correct = p->correct != 0;
+    b.d0 = p->fli_d0;
+    b.renorm = p->fli_renorm_steps;
+    b.fli_cap = p->fli_cap;
+    b.rmerge2 = p->r_merge > 0.0 ? p->r_merge * p->r_merge : 0.0;
+    b.rescape2 = p->r_escape > 0.0 ? p->r_escape * p->r_escape : 0.0;
+    h->sched = p->schedule == PNSCAN_SCHED_STATIC ? PNSCAN_SCHED_STATIC : PNSCAN_SCHED_QUEUE;
+    h->block = p->block_size ? p->block_size : 128;
+    h->chunk = p->chunk_steps ? p->chunk_steps : 500;
+    h->bps = p->blocks_per_sm;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(PNSCAN_ERR_CUDA);
+    *out = h;
+    return PNSCAN_OK;
+}
+
+int scan_setup(scan_handle* h, const double* cells)
+{
+    if (!h || (!cells && h->S.n > 0)) return PNSCAN_ERR_ARG;
+    const double* d = nullptr;
+    int r = PNSCAN_OK;
+    if (h->S.n > 0) {
+        r = stage_in(h, cells, (size_t)h->S.n * 9, &d);
+        if (r != PNSCAN_OK) return r;
+        r = cuda_err(launch_setup_cells(d, h->S.n, h->S, h->stream));
+        if (r != PNSCAN_OK) return r;
+    }
+    return begin_state(h);
+}
+
+int scan_run(scan_handle* h, const double* initial_states, double t_end, double h_step)
+{
+    if (!h || !(h_step > 0.0) || !std::isfinite(t_end)) return PNSCAN_ERR_ARG;
+    int r = PNSCAN_OK;
+    if (initial_states) {
+        if (h->S.n > 0) {
+            const double* d = nullptr;
+            r = stage_in(h, initial_states, (size_t)h->S.n * 12, &d);
+            if (r != PNSCAN_OK) return r;
+            r = cuda_err(launch_load_states(d, h->S.n, h->S, h->stream));
+            if (r != PNSCAN_OK) return r;
+        }
+        r = begin_state(h);
+        if (r != PNSCAN_OK) return r;
+    }
+    if (!h->loaded) return PNSCAN_ERR_STATE;
+    const double span = t_end - h->t_now;
+    if (span < -1e-9 * std::fabs(h_step)) return PNSCAN_ERR_ARG;
+    const double steps_d = std::nearbyint(span / h_step);
+    if (steps_d < 0.0 || steps_d + h->nstep_now > 2.0e9) return PNSCAN_ERR_ARG;
+    const int32_t nsteps = (int32_t)steps_d;
+    h->timed = false;
+    h->last_launches = 0;
+    if (nsteps > 0 && h->S.n > 0) {
+        const RunCfg rc = make_run(h, h_step, nsteps);
+        if (cudaEventRecord(h->ev0, h->stream) != cudaSuccess) return PNSCAN_ERR_CUDA;
+        if (h->sched == PNSCAN_SCHED_QUEUE && h->p.use_graph) r = run_graph(h, rc);
+        else r = launch_run(h, rc, h->sched, h->block, h->chunk, h->bps, h->S, h->stream);
+        if (r != PNSCAN_OK) return r;
+        if (cudaEventRecord(h->ev1, h->stream) != cudaSuccess) return PNSCAN_ERR_CUDA;
+        h->timed = true;
+        h->last_launches = 1;
+    }
+    h->t_now = h->t_now + nsteps * h_step;
+    h->nstep_now += nsteps;
+    return PNSCAN_OK;
+}
+
+int scan_read(scan_handle* h, double* states, double* integrals, double* fli, int32_t* status, double* t_stop)
+{
+    if (!h) return PNSCAN_ERR_ARG;
+    if (!h->loaded) return PNSCAN_ERR_STATE;
+    const int64_t n = h->S.n;
+    int r = PNSCAN_OK;
+    if (n > 0) {
+        const RunCfg rc = make_run(h, 1.0, 0);
+        r = cuda_err(launch_finalize(h->S, rc, h->stream));
+        if (r != PNSCAN_OK) return r;
+        const cudaMemcpyKind d2x = h->p.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        // AoS outputs go through the staging buffer when host pointers are used
+        struct { double* dst; int which; size_t per; } aos[2] = {{states, 0, 12}, {integrals, 2, 6}};
+        for (auto& a : aos) {
+            if (!a.dst) continue;
+            double* dd = h->p.device_ptrs ? a.dst : h->staging;
+            r = cuda_err(launch_gather(h->S, a.which == 0 ? dd : nullptr, nullptr, a.which == 2 ? dd : nullptr, h->stream));
+            if (r != PNSCAN_OK) return r;
+            if (!h->p.device_ptrs) {
+                r = cuda_err(cudaMemcpyAsync(a.dst, h->staging, sizeof(double) * a.per * n, d2x, h->stream));
+                if (r != PNSCAN_OK) return r;
+            }
+        }
+        if (fli && cudaMemcpyAsync(fli, h->S.out + 4 * h->S.ld, sizeof(double) * n, d2x, h->stream) != cudaSuccess)
+            return PNSCAN_ERR_CUDA;
+        if (status && cudaMemcpyAsync(status, h->S.status, sizeof(int32_t) * n, d2x, h->stream) != cudaSuccess)
+            return PNSCAN_ERR_CUDA;
+        if (t_stop && cudaMemcpyAsync(t_stop, h->S.t, sizeof(double) * n, d2x, h->stream) != cudaSuccess)
+            return PNSCAN_ERR_CUDA;
+    }
+    return sync(h);
+}
+
+int scan_read_diag(scan_handle* h, double* shadow, int32_t* newton_iters, int32_t* n_skip,
+                   int32_t* last_kind)
+{
+    if (!h) return PNSCAN_ERR_ARG;
+    if (!h->loaded) return PNSCAN_ERR_STATE;
+    const int64_t n = h->S.n;
+    if (n > 0) {
+        const cudaMemcpyKind d2x = h->p.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (shadow) {
+            double* dd = h->p.device_ptrs ? shadow : h->staging;
+            int r = cuda_err(launch_gather(h->S, nullptr, dd, nullptr, h->stream));
+            if (r != PNSCAN_OK) return r;
+            if (!h->p.device_ptrs &&
+                cudaMemcpyAsync(shadow, h->staging, sizeof(double) * 12 * n, d2x, h->stream) != cudaSuccess)
+                return PNSCAN_ERR_CUDA;
+        }
+        if (newton_iters &&
+            cudaMemcpyAsync(newton_iters, h->S.newton_iters, sizeof(int32_t) * n, d2x, h->stream) != cudaSuccess)
+            return PNSCAN_ERR_CUDA;
+        if (n_skip && cudaMemcpyAsync(n_skip, h->S.n_skip, sizeof(int32_t) * n, d2x, h->stream) != cudaSuccess)
+            return PNSCAN_ERR_CUDA;
+        if (last_kind &&
+            cudaMemcpyAsync(last_kind, h->S.last_kind, sizeof(int32_t) * n, d2x, h->stream) != cudaSuccess)
+            return PNSCAN_ERR_CUDA;
+    }
+    return sync(h);
+}
+
+int scan_summary(scan_handle* h, scan_summary_t* out)
+{
+    if (!h || !out) return PNSCAN_ERR_ARG;
+    if (!h->loaded) return PNSCAN_ERR_STATE;
+    const RunCfg rc = make_run(h, 1.0, 0);
+    int r = cuda_err(launch_finalize(h->S, rc, h->stream));
+    if (r != PNSCAN_OK) return r;
+    r = cuda_err(launch_reduce(h->S, h->p.fli_thresh, h->dsum, h->stream));
+    if (r != PNSCAN_OK) return r;
+    Summary s;
+    if (cudaMemcpyAsync(&s, h->dsum, sizeof(Summary), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        return PNSCAN_ERR_CUDA;
+    r = sync(h);
+    if (r != PNSCAN_OK) return r;
+    auto bits = [](unsigned long long b) { double d; std::memcpy(&d, &b, sizeof(d)); return d; };
+    std::memset(out, 0, sizeof(*out));
+    out->n = h->S.n;
+    out->n_chaotic = (int64_t)s.n_chaotic;
+    for (int k = 0; k < 6; k++) out->status_count[k] = (int64_t)s.status_count[k];
+    out->newton_iters = (int64_t)s.newton_iters;
+    out->n_skip = (int64_t)s.n_skip;
+    out->orbit_steps = (int64_t)s.steps;
+    out->max_dE = bits(s.max_dE_bits);
+    out->max_dJ = bits(s.max_dJ_bits);
+    out->max_dJ_all = bits(s.max_dJ_all_bits);
+    out->n_final_fallback = (int64_t)s.n_final_fallback;
+    out->max_dS = bits(s.max_dS_bits);
+    out->fli_max = bits(s.fli_max_bits);
+    out->fli_mean = s.status_count[PNSCAN_ORBIT_DONE] ? s.fli_sum / (double)s.status_count[PNSCAN_ORBIT_DONE] : 0.0;
+    return PNSCAN_OK;
+}
+
+int scan_autotune(scan_handle* h, int steps, int* schedule, int* block_size, int* chunk_steps, int* blocks_per_sm)
+{
+    if (!h || steps <= 0) return PNSCAN_ERR_ARG;
+    if (!h->loaded) return PNSCAN_ERR_STATE;
+    int r = PNSCAN_OK;
+    if (h->S.n > 0) {
+        // scratch copy of the state: candidates run on it, the handle's state is untouched
+        DevState T{};
+        const size_t bytes = layout_state(T, nullptr, h->S.n);
+        void* blk = dev_alloc(h, bytes);
+        if (!blk) return PNSCAN_ERR_OOM;
+        layout_state(T, (char*)blk, h->S.n);
+        struct Cand { int sched, block, chunk, bps; };
+        std::vector<Cand> cands;
+        for (int blk_sz : {64, 128}) cands.push_back({PNSCAN_SCHED_STATIC, blk_sz, 0, 0});
+        const int occ128 = queue_blocks_per_sm(128, h->base.flags.use_qm != 0);
+        for (int blk_sz : {64, 128})
+            for (int ch : {steps / 16, steps / 8, steps / 4}) {
+                if (ch < 1) continue;
+                cands.push_back({PNSCAN_SCHED_QUEUE, blk_sz, ch, 0});
+                if (blk_sz == 128 && occ128 > 1) cands.push_back({PNSCAN_SCHED_QUEUE, blk_sz, ch, 1});
+            }
+        double best = 1e300;
+        Cand bestc = cands[0];
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        const RunCfg rc = make_run(h, 1.0, steps);
+        for (const Cand& c : cands) {
+            if (cudaMemcpyAsync(blk, h->state_block, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess) {
+                r = PNSCAN_ERR_CUDA;
+                break;
+            }
+            cudaEventRecord(e0, h->stream);
+            r = launch_run(h, rc, c.sched, c.block, c.chunk, c.bps, T, h->stream);
+            cudaEventRecord(e1, h->stream);
+            if (r != PNSCAN_OK) break;
+            r = sync(h);
+            if (r != PNSCAN_OK) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bestc = c;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        dev_free(h, blk);
+        if (r != PNSCAN_OK) return r;
+        h->sched = bestc.sched;
+        h->block = bestc.block;
+        // a tuned chunk is a fraction of the tuning run; keep the same number
+        // of chunks per run length as a lower bound on the task count
+        h->chunk = bestc.sched == PNSCAN_SCHED_QUEUE ? bestc.chunk : h->chunk;
+        h->bps = bestc.bps;
+        h->tuned = true;
+    }
+    if (schedule) *schedule = h->sched;
+    if (block_size) *block_size = h->block;
+    if (chunk_steps) *chunk_steps = h->chunk;
+    if (blocks_per_sm) *blocks_per_sm = h->bps;
+    return PNSCAN_OK;
+}
+
+int scan_last_run_timing(scan_handle* h, double* ms, int* launches)
+{
+    if (!h) return PNSCAN_ERR_ARG;
+    float t = 0.f;
+    if (h->timed) {
+        if (cudaEventSynchronize(h->ev1) != cudaSuccess) return PNSCAN_ERR_CUDA;
+        if (cudaEventElapsedTime(&t, h->ev0, h->ev1) != cudaSuccess) return PNSCAN_ERR_CUDA;
+    }
+    if (ms) *ms = t;
+    if (launches) *launches = h->last_launches;
+    return PNSCAN_OK;
+}
+
+int scan_fp64_peak(scan_handle* h, int iters, double* tflops)
+{
+    if (!h || !tflops || iters <= 0) return PNSCAN_ERR_ARG;
+    const int threads = 128, blocks = h->num_sms;   // 4 warps per SM: one per sub-partition
+    double* buf = (double*)dev_alloc(h, sizeof(double) * threads * blocks);
+    if (!buf) return PNSCAN_ERR_OOM;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int r = cuda_err(launch_fp64_probe(buf, blocks, threads, iters / 10 + 1, h->stream));   // warm-up
+    cudaEventRecord(e0, h->stream);
+    if (r == PNSCAN_OK) r = cuda_err(launch_fp64_probe(buf, blocks, threads, iters, h->stream));
+    cudaEventRecord(e1, h->stream);
+    if (r == PNSCAN_OK) r = cuda_err(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    if (r == PNSCAN_OK) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    dev_free(h, buf);
+    if (r != PNSCAN_OK) return r;
+    *tflops = 2.0 * 4.0 * (double)iters * threads * blocks / (ms * 1e-3) / 1e12;
+    return PNSCAN_OK;
+}
+
+void scan_destroy(scan_handle* h)
+{
+    if (!h) return;
+    if (h->stream || h->cap_stream) cudaStreamSynchronize(h->stream);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    dev_free(h, h->staging);
+    dev_free(h, h->queue_block);
+    dev_free(h, h->state_block);
+    delete h;
+}
+
+const char* scan_strerror(int code)
+{
+    switch (code) {
+    case PNSCAN_OK: return "ok";
+    case PNSCAN_ERR_ARG: return "invalid argument";
+    case PNSCAN_ERR_CUDA: return "CUDA runtime error";
+    case PNSCAN_ERR_OOM: return "device allocation failed";
+    case PNSCAN_ERR_TIMEOUT: return "host watchdog expired";
+    case PNSCAN_ERR_STATE: return "call out of order (no state loaded)";
+    case PNSCAN_ERR_KERNEL: return "device-side bounded wait gave up";
+    case PNSCAN_ERR_NODEVICE: return "no CUDA device";
+    default: return "unknown error";
+    }
+}
+
+const char* scan_version(void) { return kVersion; }
+
+}  // extern "C"

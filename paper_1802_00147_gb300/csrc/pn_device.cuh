@@ -1,0 +1,416 @@
+// pn_device.cuh -- FP64 device arithmetic of the manifold-corrected PN scan
+// (arXiv:1802.00147): Hamiltonian and equations of motion (Sec. 2, Eqs. 1-9),
+// classical RK4, manifold correction (Eqs. 10-13) and the FLI bookkeeping.
+//
+// Everything here runs in registers of one thread per orbit.  On GB300 the
+// FP64 pipe retires two DFMA per SM per clock, so these routines are written
+// to minimise FP64 instructions: every product-sum is an fma, per-orbit
+// constants are pre-multiplied once, and the Newton solve of Eq. 13 evaluates
+// H at the scaled point from monomials in (alpha, 1/beta) instead of
+// re-evaluating the Hamiltonian.
+//
+// Units: G = c = M = 1; r in M, p in mu, H in mu, t in M, spins in M^2
+// (the reading under which Eqs. 8-9 are the exact spin gradients of H).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pnscan {
+
+// ------------------------------------------------------------------ state
+struct Vec12 {
+    double r[3], p[3], s1[3], s2[3];
+};
+
+// Per-orbit constants derived from (beta, kappa1, kappa2) and the term flags.
+// Orbital Hamiltonian H_O(p2, np, u), u = 1/|r|, np = n.p (Sec. 2):
+//   H_N   = p2/2 - u
+//   H_1PN = a1 p2^2 + u (b1 p2 + b2 np^2) + h1 u^2
+//   H_2PN = a2 p2^3 + u (c1 p2^2 + c2 p2 np^2 + c3 np^4) + u^2 (d1 p2 + d2 np^2) + e1 u^3
+// a1 = (3 eta - 1)/8, b1 = -(3 + eta)/2, b2 = -eta/2, h1 = 1/2,
+// a2 = (1 - 5 eta + 5 eta^2)/16, c1 = (5 - 20 eta - 3 eta^2)/8, c2 = -eta^2/4,
+// c3 = -3 eta^2/8, d1 = (5 + 8 eta)/2, d2 = 3 eta/2, e1 = -(1 + 3 eta)/4.
+// Spin terms: H_SO = u^3 L.(g1 S1 + g2 S2), g1 = 2 + 3/(2 beta), g2 = 2 + 3 beta/2
+// (Eqs. 8-9); H_S1S2 = ieta u^3 [3 (S1.n)(S2.n) - S1.S2] (Eq. 3 with the 1/eta
+// of Eqs. 8-9); H_QM = u^3 [q1 (3 (S1.n)^2 - S1^2) + q2 (3 (S2.n)^2 - S2^2)],
+// q1 = kappa1/(2 beta eta), q2 = kappa2 beta/(2 eta) (Eqs. 4-5).
+struct Coef {
+    // value of H (integrals, Newton monomials)
+    double a1, b1, b2, h1, a2, c1, c2, c3, d1, d2, e1;
+    double g1, g2, ieta, q1, q2;
+    // derivative polynomials, pre-multiplied
+    double a1x4, a2x6, c1x4, c2x2, d1x2;        // 2 dH/dp2
+    double b2x2, c2x2b, c3x4, d2x2;             // W = H_np / np
+    double h1x2, d1x2u, d2x2u, e1x3;            // dH/du
+    double ieta3, q1x6, q2x6, q1x15, q2x15, ieta15, q1x3, q2x3;
+};
+
+struct Flags {
+    int pn_order;          // 0, 1, 2
+    int use_so, use_ss, use_qm;
+};
+
+__host__ __device__ inline Coef make_coef(double beta, double kappa1, double kappa2, Flags f)
+{
+    Coef c;
+    const double eta = beta / ((1.0 + beta) * (1.0 + beta));
+    const double pn1 = f.pn_order >= 1 ? 1.0 : 0.0;
+    const double pn2 = f.pn_order >= 2 ? 1.0 : 0.0;
+    c.a1 = pn1 * (3.0 * eta - 1.0) / 8.0;
+    c.b1 = pn1 * -(3.0 + eta) / 2.0;
+    c.b2 = pn1 * -eta / 2.0;
+    c.h1 = pn1 * 0.5;
+    c.a2 = pn2 * (1.0 - 5.0 * eta + 5.0 * eta * eta) / 16.0;
+    c.c1 = pn2 * (5.0 - 20.0 * eta - 3.0 * eta * eta) / 8.0;
+    c.c2 = pn2 * -(eta * eta) / 4.0;
+    c.c3 = pn2 * -3.0 * eta * eta / 8.0;
+    c.d1 = pn2 * (5.0 + 8.0 * eta) / 2.0;
+    c.d2 = pn2 * 3.0 * eta / 2.0;
+    c.e1 = pn2 * -(1.0 + 3.0 * eta) / 4.0;
+    c.g1 = f.use_so ? 2.0 + 3.0 / (2.0 * beta) : 0.0;
+    c.g2 = f.use_so ? 2.0 + 1.5 * beta : 0.0;
+    c.ieta = f.use_ss ? 1.0 / eta : 0.0;
+    c.q1 = f.use_qm ? kappa1 / (2.0 * beta * eta) : 0.0;
+    c.q2 = f.use_qm ? kappa2 * beta / (2.0 * eta) : 0.0;
+    // 2 dH/dp2 = 1 + 4 a1 p2 + 2 b1 u + 6 a2 p2^2 + u (4 c1 p2 + 2 c2 np^2) + 2 d1 u^2
+    c.a1x4 = 4.0 * c.a1;
+    c.a2x6 = 6.0 * c.a2;
+    c.c1x4 = 4.0 * c.c1;
+    c.c2x2 = 2.0 * c.c2;
+    c.d1x2 = 2.0 * c.d1;
+    // W = H_np / np = u (2 b2 + 2 c2 p2 + 4 c3 np^2 + 2 d2 u)
+    c.b2x2 = 2.0 * c.b2;
+    c.c2x2b = 2.0 * c.c2;
+    c.c3x4 = 4.0 * c.c3;
+    c.d2x2 = 2.0 * c.d2;
+    // dH/du = -1 + p2 (b1 + c1 p2 + c2 np^2) + np^2 (b2 + c3 np^2)
+    //         + u (2 h1 + 2 d1 p2 + 2 d2 np^2 + 3 e1 u)
+    c.h1x2 = 2.0 * c.h1;
+    c.d1x2u = 2.0 * c.d1;
+    c.d2x2u = 2.0 * c.d2;
+    c.e1x3 = 3.0 * c.e1;
+    c.ieta3 = 3.0 * c.ieta;
+    c.q1x6 = 6.0 * c.q1;
+    c.q2x6 = 6.0 * c.q2;
+    c.q1x15 = 15.0 * c.q1;
+    c.q2x15 = 15.0 * c.q2;
+    c.ieta15 = 15.0 * c.ieta;
+    c.q1x3 = 3.0 * c.q1;
+    c.q2x3 = 3.0 * c.q2;
+    return c;
+}
+
+__device__ __forceinline__ double dot3(const double* a, const double* b)
+{
+    return fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
+}
+
+// ------------------------------------------------------- equations of motion
+// dy/dt = (dH/dp, -dH/dr, Omega_1 x S1, Omega_2 x S2)  (Eqs. 6-7, a_2.5PN = 0)
+// With n = u r, np = u (r.p), H_np = np W:
+//   dH/dp = 2 H_p2 p + (np W u) r + u^3 (Seff x r)
+//   dH/dr = u np W p - u^2 (u H_u + np^2 W) r + u^3 (p x Seff) - 3 u^5 (L.Seff) r
+//           + spin-spin / QM parts (see below)
+template <bool QM>
+__device__ __forceinline__ void rhs(const Coef& c, const Vec12& y, Vec12& dy)
+{
+    const double* r = y.r;
+    const double* p = y.p;
+    const double* S1 = y.s1;
+    const double* S2 = y.s2;
+
+    const double rr2 = dot3(r, r);
+    const double u = rsqrt(rr2);
+    const double u2 = u * u;
+    const double u3 = u2 * u;
+    const double u5 = u3 * u2;
+    const double rp = dot3(r, p);
+    const double p2 = dot3(p, p);
+    const double np = rp * u;
+    const double np2 = np * np;
+    const double a1s = dot3(S1, r);     // (S1.n) / u
+    const double a2s = dot3(S2, r);
+    const double S12 = dot3(S1, S2);
+
+    // L = r x p, Seff = g1 S1 + g2 S2
+    const double L0 = fma(r[1], p[2], -r[2] * p[1]);
+    const double L1 = fma(r[2], p[0], -r[0] * p[2]);
+    const double L2 = fma(r[0], p[1], -r[1] * p[0]);
+    const double E0 = fma(c.g1, S1[0], c.g2 * S2[0]);
+    const double E1 = fma(c.g1, S1[1], c.g2 * S2[1]);
+    const double E2 = fma(c.g1, S1[2], c.g2 * S2[2]);
+    const double LSe = fma(L0, E0, fma(L1, E1, L2 * E2));
+
+    // orbital partial derivatives
+    const double tq = fma(c.c2, np2, c.b1);                                 // b1 + c2 np^2
+    const double Hp2x2 = fma(fma(c.a2x6, p2, c.a1x4), p2, 1.0)
+                       + u * fma(c.d1x2, u, fma(c.c1x4, p2, fma(c.c2x2, np2, 2.0 * c.b1)));
+    const double W = u * fma(c.d2x2, u, fma(c.c2x2b, p2, fma(c.c3x4, np2, c.b2x2)));
+    const double Hu = fma(fma(c.c1, p2, tq), p2, -1.0) + np2 * fma(c.c3, np2, c.b2)
+                    + u * fma(c.e1x3, u, fma(c.d1x2u, p2, fma(c.d2x2u, np2, c.h1x2)));
+    const double cr = np * W * u;                                            // H_np u
+
+    // spin-spin and QM scalars
+    double T1 = c.ieta3 * a2s;                                               // 3 ieta a2s + 6 q1 a1s
+    double T2 = c.ieta3 * a1s;                                               // 3 ieta a1s + 6 q2 a2s
+    // 15 u^2 (ieta a1s a2s + q1 a1s^2 + q2 a2s^2) + 3 LSe - 3 ieta S12 - 3 (q1 S11 + q2 S22)
+    double Q = c.ieta15 * (a1s * a2s);
+    double K = fma(-c.ieta3, S12, 3.0 * LSe);
+    if (QM) {
+        T1 = fma(c.q1x6, a1s, T1);
+        T2 = fma(c.q2x6, a2s, T2);
+        Q = fma(c.q1x15 * a1s, a1s, fma(c.q2x15 * a2s, a2s, Q));
+        K = fma(-c.q1x3, dot3(S1, S1), fma(-c.q2x3, dot3(S2, S2), K));
+    }
+    const double V1 = u5 * T1;
+    const double V2 = u5 * T2;
+    const double Ar = u2 * fma(np2, W, u * Hu) + u5 * fma(Q, u2, K);
+
+    // dr/dt = Hp2x2 p + cr r + u^3 (Seff x r)
+    const double X0 = fma(E1, r[2], -E2 * r[1]);
+    const double X1 = fma(E2, r[0], -E0 * r[2]);
+    const double X2 = fma(E0, r[1], -E1 * r[0]);
+    dy.r[0] = fma(Hp2x2, p[0], fma(cr, r[0], u3 * X0));
+    dy.r[1] = fma(Hp2x2, p[1], fma(cr, r[1], u3 * X1));
+    dy.r[2] = fma(Hp2x2, p[2], fma(cr, r[2], u3 * X2));
+
+    // dp/dt = -cr p + Ar r - V1 S1 - V2 S2 - u^3 (p x Seff)
+    const double Y0 = fma(p[1], E2, -p[2] * E1);
+    const double Y1 = fma(p[2], E0, -p[0] * E2);
+    const double Y2 = fma(p[0], E1, -p[1] * E0);
+    dy.p[0] = fma(-cr, p[0], fma(Ar, r[0], fma(-V1, S1[0], fma(-V2, S2[0], -u3 * Y0))));
+    dy.p[1] = fma(-cr, p[1], fma(Ar, r[1], fma(-V1, S1[1], fma(-V2, S2[1], -u3 * Y1))));
+    dy.p[2] = fma(-cr, p[2], fma(Ar, r[2], fma(-V1, S1[2], fma(-V2, S2[2], -u3 * Y2))));
+
+    // dS1/dt = (u^3 g1 L + V1 r - u^3 ieta S2) x S1, and 1 <-> 2 (Eqs. 7-9)
+    const double G1 = u3 * c.g1, G2 = u3 * c.g2, I3 = u3 * c.ieta;
+    const double O10 = fma(G1, L0, fma(V1, r[0], -I3 * S2[0]));
+    const double O11 = fma(G1, L1, fma(V1, r[1], -I3 * S2[1]));
+    const double O12 = fma(G1, L2, fma(V1, r[2], -I3 * S2[2]));
+    dy.s1[0] = fma(O11, S1[2], -O12 * S1[1]);
+    dy.s1[1] = fma(O12, S1[0], -O10 * S1[2]);
+    dy.s1[2] = fma(O10, S1[1], -O11 * S1[0]);
+    const double O20 = fma(G2, L0, fma(V2, r[0], -I3 * S1[0]));
+    const double O21 = fma(G2, L1, fma(V2, r[1], -I3 * S1[1]));
+    const double O22 = fma(G2, L2, fma(V2, r[2], -I3 * S1[2]));
+    dy.s2[0] = fma(O21, S2[2], -O22 * S2[1]);
+    dy.s2[1] = fma(O22, S2[0], -O20 * S2[2]);
+    dy.s2[2] = fma(O20, S2[1], -O21 * S2[0]);
+}
+
+// ------------------------------------------------------------ Hamiltonian
+template <bool QM>
+__device__ __forceinline__ double hamiltonian(const Coef& c, const Vec12& y)
+{
+    const double rr2 = dot3(y.r, y.r);
+    const double u = rsqrt(rr2);
+    const double p2 = dot3(y.p, y.p);
+    const double np = dot3(y.r, y.p) * u;
+    const double np2 = np * np;
+    const double L0 = fma(y.r[1], y.p[2], -y.r[2] * y.p[1]);
+    const double L1 = fma(y.r[2], y.p[0], -y.r[0] * y.p[2]);
+    const double L2 = fma(y.r[0], y.p[1], -y.r[1] * y.p[0]);
+    const double LS1 = fma(L0, y.s1[0], fma(L1, y.s1[1], L2 * y.s1[2]));
+    const double LS2 = fma(L0, y.s2[0], fma(L1, y.s2[1], L2 * y.s2[2]));
+    const double a1 = dot3(y.s1, y.r) * u, a2 = dot3(y.s2, y.r) * u;
+    const double u3 = u * u * u;
+    double Hp = fma(fma(c.a2, p2, c.a1), p2, 0.5) * p2;                         // p2/2 + a1 p2^2 + a2 p2^3
+    double Hu1 = fma(c.b1, p2, c.b2 * np2) + p2 * fma(c.c1, p2, c.c2 * np2) + c.c3 * np2 * np2 - 1.0;
+    double Hu2 = fma(c.d1, p2, fma(c.d2, np2, c.h1));
+    double Hu3 = c.e1 + c.ieta * fma(3.0 * a1, a2, -dot3(y.s1, y.s2));
+    if (QM)
+        Hu3 += c.q1 * fma(3.0 * a1, a1, -dot3(y.s1, y.s1)) + c.q2 * fma(3.0 * a2, a2, -dot3(y.s2, y.s2));
+    const double Hso = u3 * fma(c.g1, LS1, c.g2 * LS2);
+    return Hp + u * fma(u, fma(u, Hu3, Hu2), Hu1) + Hso;
+}
+
+// |J|, J = L + S1 + S2
+__device__ __forceinline__ double jnorm(const Vec12& y)
+{
+    const double J0 = fma(y.r[1], y.p[2], -y.r[2] * y.p[1]) + y.s1[0] + y.s2[0];
+    const double J1 = fma(y.r[2], y.p[0], -y.r[0] * y.p[2]) + y.s1[1] + y.s2[1];
+    const double J2 = fma(y.r[0], y.p[1], -y.r[1] * y.p[0]) + y.s1[2] + y.s2[2];
+    return sqrt(fma(J0, J0, fma(J1, J1, J2 * J2)));
+}
+
+// Reference integrals of one trajectory: E0, J0, |S1|0, |S2|0 (Eq. 12).
+struct Ref {
+    double E, J, S1, S2;
+};
+
+template <bool QM>
+__device__ __forceinline__ Ref integrals(const Coef& c, const Vec12& y)
+{
+    Ref R;
+    R.E = hamiltonian<QM>(c, y);
+    R.J = jnorm(y);
+    R.S1 = sqrt(dot3(y.s1, y.s1));
+    R.S2 = sqrt(dot3(y.s2, y.s2));
+    return R;
+}
+
+// ------------------------------------------------------------------- RK4
+template <bool QM>
+__device__ __forceinline__ void rk4_step(const Coef& c, Vec12& y, double h)
+{
+    const double h2 = 0.5 * h, h3 = h * (1.0 / 3.0), h6 = h * (1.0 / 6.0);
+    Vec12 k, st, acc;
+    double* yv = &y.r[0];
+    double* kv = &k.r[0];
+    double* sv = &st.r[0];
+    double* av = &acc.r[0];
+    rhs<QM>(c, y, k);
+#pragma unroll
+    for (int i = 0; i < 12; i++) {
+        av[i] = fma(h6, kv[i], yv[i]);
+        sv[i] = fma(h2, kv[i], yv[i]);
+    }
+    rhs<QM>(c, st, k);
+#pragma unroll
+    for (int i = 0; i < 12; i++) {
+        av[i] = fma(h3, kv[i], av[i]);
+        sv[i] = fma(h2, kv[i], yv[i]);
+    }
+    rhs<QM>(c, st, k);
+#pragma unroll
+    for (int i = 0; i < 12; i++) {
+        av[i] = fma(h3, kv[i], av[i]);
+        sv[i] = fma(h, kv[i], yv[i]);
+    }
+    rhs<QM>(c, st, k);
+#pragma unroll
+    for (int i = 0; i < 12; i++) yv[i] = fma(h6, kv[i], av[i]);
+}
+
+// ------------------------------------------------------ manifold correction
+enum CorrKind : int { CORR_DUAL = 0, CORR_NONE = 1, CORR_VELOCITY = 2 };
+
+struct NewtonCfg {
+    double tol;       // stop when |d alpha| <= tol and |d beta| <= tol (Sec. 3A: 1e-10)
+    int max_iter;     // iteration cap
+    double det_min;   // relative-determinant guard of the singular scaling
+};
+
+// Eq. 10, then Eqs. 11-13: p = alpha p*, r = beta r* with (alpha, beta) from
+// H(beta r*, alpha p*, S) = E0 and |J(beta r*, alpha p*, S)| = J0 by Newton's
+// method from (1, 1).  Returns the number of Newton iterations; *kind is
+// CORR_DUAL when the dual scaling was applied, CORR_VELOCITY when it was
+// singular (or did not converge) and E was restored by scaling p alone, and
+// CORR_NONE when neither converged.
+//
+// With u = 1/beta, every term of H at the scaled point is a monomial in
+// (alpha, u):  H(alpha, u) = alpha^2 (A2 + alpha^2 (A4 + alpha^2 A6))
+//   + u (B0 + alpha^2 (B2 + alpha^2 B4)) + u^2 (C0 + alpha^2 C2 + alpha E1) + u^3 D0
+// whose coefficients are evaluated once at (r*, p*, S); and
+// |J|^2 = k^2 L*.L* + 2 k L*.S + S.S with k = alpha beta, S = S1 + S2.
+template <bool QM>
+__device__ __forceinline__ int correct(const Coef& c, Vec12& y, const Ref& ref,
+                                       const NewtonCfg& nc, int* kind)
+{
+    // Eq. 10: spin lengths
+    {
+        const double l1 = dot3(y.s1, y.s1), l2 = dot3(y.s2, y.s2);
+        if (ref.S1 > 0.0 && l1 > 0.0) {
+            const double f = ref.S1 * rsqrt(l1);
+            y.s1[0] *= f; y.s1[1] *= f; y.s1[2] *= f;
+        }
+        if (ref.S2 > 0.0 && l2 > 0.0) {
+            const double f = ref.S2 * rsqrt(l2);
+            y.s2[0] *= f; y.s2[1] *= f; y.s2[2] *= f;
+        }
+    }
+    // monomial coefficients at (r*, p*, S)
+    const double R = rsqrt(dot3(y.r, y.r));
+    const double P2 = dot3(y.p, y.p);
+    const double NP = dot3(y.r, y.p) * R;
+    const double NP2 = NP * NP;
+    const double L0 = fma(y.r[1], y.p[2], -y.r[2] * y.p[1]);
+    const double L1 = fma(y.r[2], y.p[0], -y.r[0] * y.p[2]);
+    const double L2 = fma(y.r[0], y.p[1], -y.r[1] * y.p[0]);
+    const double Sx = y.s1[0] + y.s2[0], Sy = y.s1[1] + y.s2[1], Sz = y.s1[2] + y.s2[2];
+    const double LL = fma(L0, L0, fma(L1, L1, L2 * L2));
+    const double LJ = fma(L0, Sx, fma(L1, Sy, L2 * Sz));
+    const double SSq = fma(Sx, Sx, fma(Sy, Sy, Sz * Sz));
+    const double LSe = c.g1 * fma(L0, y.s1[0], fma(L1, y.s1[1], L2 * y.s1[2]))
+                     + c.g2 * fma(L0, y.s2[0], fma(L1, y.s2[1], L2 * y.s2[2]));
+    const double a1 = dot3(y.s1, y.r) * R, a2 = dot3(y.s2, y.r) * R;
+    const double R2 = R * R, R3 = R2 * R;
+    const double A2 = 0.5 * P2;
+    const double A4 = c.a1 * P2 * P2;
+    const double A6 = c.a2 * P2 * P2 * P2;
+    const double B0 = -R;
+    const double B2 = R * fma(c.b1, P2, c.b2 * NP2);
+    const double B4 = R * fma(P2, fma(c.c1, P2, c.c2 * NP2), c.c3 * NP2 * NP2);
+    const double C0 = c.h1 * R2;
+    const double C2 = R2 * fma(c.d1, P2, c.d2 * NP2);
+    const double E1 = R3 * LSe;
+    double Dq = fma(c.ieta, fma(3.0 * a1, a2, -dot3(y.s1, y.s2)), c.e1);
+    if (QM)
+        Dq += c.q1 * fma(3.0 * a1, a1, -dot3(y.s1, y.s1)) + c.q2 * fma(3.0 * a2, a2, -dot3(y.s2, y.s2));
+    const double D0 = R3 * Dq;
+    const double A4x2 = 2.0 * A4, A6x3 = 3.0 * A6, B4x2 = 2.0 * B4, D0x3 = 3.0 * D0, LJx2 = 2.0 * LJ;
+
+    double al = 1.0, be = 1.0;
+    int it = 0;
+    bool conv = false;
+    while (it < nc.max_iter) {
+        ++it;
+        const double u = __drcp_rn(be);
+        const double a2s = al * al;
+        const double Pa = fma(a2s, fma(a2s, A6, A4), A2);
+        const double Pb = fma(a2s, fma(a2s, B4, B2), B0);
+        const double Pc = fma(a2s, C2, fma(al, E1, C0));
+        const double H = fma(a2s, Pa, u * fma(u, fma(u, D0, Pc), Pb));
+        const double Ha = fma(2.0 * al, fma(a2s, fma(a2s, A6x3, A4x2), A2)
+                                        + u * fma(u, C2, fma(a2s, B4x2, B2)), u * u * E1);
+        const double Hu = fma(u, fma(u, D0x3, 2.0 * Pc), Pb);
+        const double Hb = -(u * u) * Hu;
+        const double k = al * be;
+        const double Jn2 = fma(k, fma(k, LL, LJx2), SSq);
+        const double rJ = rsqrt(Jn2);
+        const double dJ = fma(k, LL, LJ) * rJ;
+        const double Ja = be * dJ, Jb = al * dJ;
+        const double F1 = H - ref.E;
+        const double F2 = fma(Jn2, rJ, -ref.J);
+        const double p1 = Ha * Jb, p2 = Hb * Ja;
+        const double det = p1 - p2;
+        if (!(fabs(det) > nc.det_min * (fabs(p1) + fabs(p2)))) break;   // singular (or NaN)
+        const double rd = __drcp_rn(det);
+        const double da = fma(F1, Jb, -Hb * F2) * rd;
+        const double db = fma(Ha, F2, -Ja * F1) * rd;
+        al -= da;
+        be -= db;
+        if (fabs(da) <= nc.tol && fabs(db) <= nc.tol) { conv = true; break; }
+        if (!(fabs(al) < 1e300) || !(fabs(be) < 1e300)) break;
+    }
+    if (conv) {
+        y.r[0] *= be; y.r[1] *= be; y.r[2] *= be;
+        y.p[0] *= al; y.p[1] *= al; y.p[2] *= al;
+        *kind = CORR_DUAL;
+        return it;
+    }
+    // Singular (or non-converged) dual scaling: restore E alone by velocity
+    // scaling, p = a p*, H(r*, a p*, S) = E0 (Newton in a from 1), i.e. the
+    // monomial form at 1/beta = 1.  |J| is left to the next step.
+    double a = 1.0;
+    int k = 0;
+    bool ok = false;
+    const double Bsum = B0 + C0 + D0;
+    while (k < nc.max_iter) {
+        ++k;
+        const double a2s = a * a;
+        const double H = fma(a2s, fma(a2s, fma(a2s, A6, A4), A2) + fma(a2s, B4, B2) + C2, fma(a, E1, Bsum));
+        const double Ha = fma(2.0 * a, fma(a2s, fma(a2s, A6x3, A4x2), A2) + fma(a2s, B4x2, B2) + C2, E1);
+        const double da = (H - ref.E) / Ha;
+        if (!(fabs(da) <= 1.7976931348623157e308)) break;
+        a -= da;
+        if (fabs(da) <= nc.tol) { ok = true; break; }
+    }
+    if (ok) {
+        y.p[0] *= a; y.p[1] *= a; y.p[2] *= a;
+    }
+    *kind = ok ? CORR_VELOCITY : CORR_NONE;
+    return it + k;
+}
+
+}  // namespace pnscan

@@ -1,0 +1,532 @@
+// pn_kernels.cu -- kernels of the batched manifold-corrected PN scan
+// (arXiv:1802.00147, Secs. 2-3).  One orbit per thread; the state of both
+// trajectories lives in registers for a whole run (or a whole chunk of the
+// persistent work-queue kernel) and HBM is touched only at entry and exit.
+#include <cmath>
+
+#include "pn_kernels.cuh"
+
+namespace pnscan {
+
+// --------------------------------------------------------------- helpers
+__device__ __forceinline__ bool finite12(const Vec12& a)
+{
+    const double* v = &a.r[0];
+    int bad = 0;
+#pragma unroll
+    for (int i = 0; i < 12; i++) bad |= ((__double2hiint(v[i]) & 0x7ff00000) == 0x7ff00000);
+    return !bad;
+}
+
+template <bool CG>
+__device__ __forceinline__ double ld(const double* p)
+{
+    if (CG) return __ldcg(p);
+    return *p;
+}
+
+template <bool CG>
+__device__ __forceinline__ int32_t ldi(const int32_t* p)
+{
+    if (CG) return __ldcg(p);
+    return *p;
+}
+
+template <bool CG>
+__device__ __forceinline__ void load12(const double* base, int64_t n, int64_t i, Vec12& v)
+{
+    double* d = &v.r[0];
+#pragma unroll
+    for (int k = 0; k < 12; k++) d[k] = ld<CG>(base + k * n + i);
+}
+
+__device__ __forceinline__ void store12(double* base, int64_t n, int64_t i, const Vec12& v)
+{
+    const double* d = &v.r[0];
+#pragma unroll
+    for (int k = 0; k < 12; k++) base[k * n + i] = d[k];
+}
+
+// Everything one orbit carries between kernel invocations.
+struct Orbit {
+    Vec12 y, ys;
+    Ref ref, refs;
+    double acc, t;
+    int32_t nstep, status, iters, skips, last_kind;
+};
+
+template <bool CG>
+__device__ __forceinline__ void load_orbit(const DevState& S, int64_t i, Orbit& o)
+{
+    const int64_t n = S.ld;
+    load12<CG>(S.y, n, i, o.y);
+    load12<CG>(S.ys, n, i, o.ys);
+    o.ref.E = ld<CG>(S.ref + 0 * n + i);
+    o.ref.J = ld<CG>(S.ref + 1 * n + i);
+    o.ref.S1 = ld<CG>(S.ref + 2 * n + i);
+    o.ref.S2 = ld<CG>(S.ref + 3 * n + i);
+    o.refs.E = ld<CG>(S.ref + 4 * n + i);
+    o.refs.J = ld<CG>(S.ref + 5 * n + i);
+    o.refs.S1 = ld<CG>(S.ref + 6 * n + i);
+    o.refs.S2 = ld<CG>(S.ref + 7 * n + i);
+    o.acc = ld<CG>(S.fli_acc + i);
+    o.t = ld<CG>(S.t + i);
+    o.nstep = ldi<CG>(S.nstep + i);
+    o.iters = ldi<CG>(S.newton_iters + i);
+    o.skips = ldi<CG>(S.n_skip + i);
+    o.last_kind = ldi<CG>(S.last_kind + i);
+}
+
+__device__ __forceinline__ void store_orbit(const DevState& S, int64_t i, const Orbit& o)
+{
+    const int64_t n = S.ld;
+    store12(S.y, n, i, o.y);
+    store12(S.ys, n, i, o.ys);
+    S.ref[4 * n + i] = o.refs.E;
+    S.ref[5 * n + i] = o.refs.J;
+    S.ref[6 * n + i] = o.refs.S1;
+    S.ref[7 * n + i] = o.refs.S2;
+    S.fli_acc[i] = o.acc;
+    S.t[i] = o.t;
+    S.nstep[i] = o.nstep;
+    S.status[i] = o.status;
+    S.newton_iters[i] = o.iters;
+    S.n_skip[i] = o.skips;
+    S.last_kind[i] = o.last_kind;
+}
+
+template <bool CG>
+__device__ __forceinline__ Coef load_coef(const DevState& S, int64_t i, const Flags& f)
+{
+    return make_coef(ld<CG>(S.beta + i), ld<CG>(S.kappa1 + i), ld<CG>(S.kappa2 + i), f);
+}
+
+// Advance one orbit (both trajectories) until nstep == step_end or it stops.
+// One step: RK4 and manifold correction of the main trajectory, the same for
+// the shadow, termination tests, and every `renorm` steps the FLI
+// renormalisation (acc += log10(d/d0), shadow pulled back to distance d0 and
+// given its own reference integrals).
+template <bool QM>
+__device__ __forceinline__ void advance(const RunCfg& rc, const Coef& c, Orbit& o, int32_t step_end)
+{
+    const double t0 = o.t;
+    const int32_t n0 = o.nstep;
+    while (o.nstep < step_end) {
+        rk4_step<QM>(c, o.y, rc.h);
+        if (rc.correct) {
+            int kind;
+            o.iters += correct<QM>(c, o.y, o.ref, rc.newton, &kind);
+            o.skips += kind != CORR_DUAL;
+            o.last_kind = kind;
+        }
+        rk4_step<QM>(c, o.ys, rc.h);
+        if (rc.correct) {
+            int kind;
+            o.iters += correct<QM>(c, o.ys, o.refs, rc.newton, &kind);
+            o.skips += kind != CORR_DUAL;
+        }
+        o.nstep++;
+        if (!finite12(o.y) || !finite12(o.ys)) { o.status = ORBIT_NONFINITE; break; }
+        const double rr2 = dot3(o.y.r, o.y.r);
+        if (rc.rmerge2 > 0.0 && rr2 < rc.rmerge2) { o.status = ORBIT_MERGED; break; }
+        if (rc.rescape2 > 0.0 && rr2 > rc.rescape2) { o.status = ORBIT_ESCAPED; break; }
+        if (rc.renorm > 0 && (o.nstep % rc.renorm) == 0) {
+            double dv[12];
+            const double* a = &o.y.r[0];
+            double* b = &o.ys.r[0];
+            double d2 = 0.0;
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                dv[k] = b[k] - a[k];
+                d2 = fma(dv[k], dv[k], d2);
+            }
+            const double d = sqrt(d2);
+            o.acc += log10(d / rc.d0);
+            const double f = rc.d0 / d;
+#pragma unroll
+            for (int k = 0; k < 12; k++) b[k] = fma(f, dv[k], a[k]);
+            o.refs = integrals<QM>(c, o.ys);
+            if (rc.fli_cap > 0.0 && o.acc >= rc.fli_cap) { o.status = ORBIT_FLI_SATURATED; break; }
+        }
+    }
+    o.t = t0 + (double)(o.nstep - n0) * rc.h;
+}
+
+// ------------------------------------------------------------------ set-up
+// Initial conditions of a scan cell (x0, pfac, theta1, phi1, theta2, phi2,
+// beta, chi1, chi2): r = (x0, 0, 0), p = (0, pfac / sqrt(x0), 0),
+// S_i = chi_i m_i^2 (sin th_i cos ph_i, sin th_i sin ph_i, cos th_i).
+__global__ void k_setup_cells(const double* __restrict__ cells, int64_t n, DevState S)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* c = cells + 9 * i;
+    const double x0 = c[0], beta = c[6];
+    const double m1 = beta / (1.0 + beta), m2 = 1.0 / (1.0 + beta);
+    const double s1 = c[7] * m1 * m1, s2 = c[8] * m2 * m2;
+    double st1, ct1, sp1, cp1, st2, ct2, sp2, cp2;
+    sincos(c[2], &st1, &ct1);
+    sincos(c[3], &sp1, &cp1);
+    sincos(c[4], &st2, &ct2);
+    sincos(c[5], &sp2, &cp2);
+    Vec12 y;
+    y.r[0] = x0; y.r[1] = 0.0; y.r[2] = 0.0;
+    y.p[0] = 0.0; y.p[1] = c[1] / sqrt(x0); y.p[2] = 0.0;
+    y.s1[0] = s1 * st1 * cp1; y.s1[1] = s1 * st1 * sp1; y.s1[2] = s1 * ct1;
+    y.s2[0] = s2 * st2 * cp2; y.s2[1] = s2 * st2 * sp2; y.s2[2] = s2 * ct2;
+    store12(S.y, S.ld, i, y);
+}
+
+__global__ void k_load_states(const double* __restrict__ states, int64_t n, DevState S)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Vec12 y;
+    double* d = &y.r[0];
+#pragma unroll
+    for (int k = 0; k < 12; k++) d[k] = states[12 * i + k];
+    store12(S.y, S.ld, i, y);
+}
+
+// Reference integrals (E0, J0, |S_i|0) of both trajectories; the shadow
+// starts d0 away along x.
+template <bool QM>
+__global__ void k_init(DevState S, RunCfg rc)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= S.n) return;
+    const Coef c = load_coef<false>(S, i, rc.flags);
+    Vec12 y, ys;
+    load12<false>(S.y, S.ld, i, y);
+    ys = y;
+    ys.r[0] = ys.r[0] + rc.d0;
+    const Ref a = integrals<QM>(c, y), b = integrals<QM>(c, ys);
+    store12(S.ys, S.ld, i, ys);
+    const int64_t n = S.ld;
+    S.ref[0 * n + i] = a.E; S.ref[1 * n + i] = a.J; S.ref[2 * n + i] = a.S1; S.ref[3 * n + i] = a.S2;
+    S.ref[4 * n + i] = b.E; S.ref[5 * n + i] = b.J; S.ref[6 * n + i] = b.S1; S.ref[7 * n + i] = b.S2;
+    S.fli_acc[i] = 0.0;
+    S.t[i] = 0.0;
+    S.nstep[i] = 0;
+    S.status[i] = finite12(y) ? ORBIT_RUNNING : ORBIT_NONFINITE;
+    S.newton_iters[i] = 0;
+    S.n_skip[i] = 0;
+    S.last_kind[i] = CORR_DUAL;
+}
+
+// ----------------------------------------------------- static integrator
+// One orbit per thread for the whole run.
+template <bool QM>
+__global__ void __launch_bounds__(128) k_integrate_static(DevState S, RunCfg rc)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= S.n) return;
+    const int32_t st = S.status[i];
+    if (st != ORBIT_RUNNING && st != ORBIT_DONE) return;
+    Orbit o;
+    load_orbit<false>(S, i, o);
+    o.status = ORBIT_RUNNING;
+    const Coef c = load_coef<false>(S, i, rc.flags);
+    const int32_t end = rc.nstep_base + rc.nsteps;
+    advance<QM>(rc, c, o, end);
+    if (o.status == ORBIT_RUNNING && o.nstep == end) o.status = ORBIT_DONE;
+    store_orbit(S, i, o);
+}
+
+// ------------------------------------------- persistent work-queue integrator
+// Tasks are (chunk c, group g): advance the 32 orbits of group g (one warp)
+// through steps [c K, (c+1) K) of the run.  Warps claim tasks in order from
+// one atomic counter; task (c, g) waits for (c-1, g), which was claimed
+// earlier by a running warp, so the oldest unfinished task can always make
+// progress.  Because every group advances chunk by chunk, all SM
+// sub-partitions stay busy until the last chunk, whatever the number of
+// orbits.  Every wait is bounded in time; on expiry the kernel sets the error
+// flag and all warps return.
+__device__ __forceinline__ int ld_acquire(const int* p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v)
+{
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr unsigned long long kQueueWaitLimitNs = 20ull * 1000ull * 1000ull * 1000ull;  // 20 s
+
+template <bool QM>
+__global__ void __launch_bounds__(128) k_integrate_queue(DevState S, RunCfg rc, QueueState q, int chunk)
+{
+    const int lane = threadIdx.x & 31;
+    const long long groups = (S.n + 31) / 32;
+    const long long nchunks = (rc.nsteps + chunk - 1) / chunk;
+    const unsigned long long ntasks = (unsigned long long)(groups * nchunks);
+    const int32_t end_run = rc.nstep_base + rc.nsteps;
+    for (;;) {
+        unsigned long long task = 0;
+        if (lane == 0) task = (*(volatile int*)q.error) ? ntasks : atomicAdd(q.next, 1ull);
+        task = __shfl_sync(0xffffffffu, task, 0);
+        if (task >= ntasks) break;
+        const long long c = (long long)(task / (unsigned long long)groups);
+        const long long g = (long long)(task % (unsigned long long)groups);
+        int ok = 1;
+        if (c > 0 && lane == 0) {
+            const unsigned long long t0 = globaltimer_ns();
+            while (ld_acquire(q.group_done + g) < c) {
+                if (globaltimer_ns() - t0 > kQueueWaitLimitNs) {
+                    atomicExch(q.error, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(200);
+            }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        const int64_t i = g * 32 + lane;
+        if (i < S.n) {
+            const int32_t st = __ldcg(S.status + i);
+            if (st == ORBIT_RUNNING || (c == 0 && st == ORBIT_DONE)) {
+                Orbit o;
+                load_orbit<true>(S, i, o);
+                o.status = ORBIT_RUNNING;
+                const Coef cf = load_coef<true>(S, i, rc.flags);
+                const long long e = (c + 1) * (long long)chunk;
+                const int32_t end = rc.nstep_base + (int32_t)(e < rc.nsteps ? e : rc.nsteps);
+                advance<QM>(rc, cf, o, end);
+                if (o.status == ORBIT_RUNNING && o.nstep == end_run) o.status = ORBIT_DONE;
+                store_orbit(S, i, o);
+            }
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release(q.group_done + g, (int)(c + 1));
+    }
+}
+
+// --------------------------------------------------------------- finalize
+// Integrals of the main trajectory and FLI(t) = acc + log10(d(t)/d0).
+template <bool QM>
+__global__ void k_finalize(DevState S, RunCfg rc)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= S.n) return;
+    const Coef c = load_coef<false>(S, i, rc.flags);
+    Vec12 y, ys;
+    load12<false>(S.y, S.ld, i, y);
+    load12<false>(S.ys, S.ld, i, ys);
+    const Ref I = integrals<QM>(c, y);
+    const double* a = &y.r[0];
+    const double* b = &ys.r[0];
+    double d2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 12; k++) d2 = fma(b[k] - a[k], b[k] - a[k], d2);
+    const int64_t n = S.ld;
+    S.out[0 * n + i] = I.E;
+    S.out[1 * n + i] = I.J;
+    S.out[2 * n + i] = I.S1;
+    S.out[3 * n + i] = I.S2;
+    S.out[4 * n + i] = S.fli_acc[i] + log10(sqrt(d2) / rc.d0);
+}
+
+// ----------------------------------------------------------- scan summary
+__device__ __forceinline__ unsigned long long dbits(double x)
+{
+    return (unsigned long long)__double_as_longlong(x);
+}
+
+__global__ void k_reduce(DevState S, double thr, Summary* out)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    unsigned long long chaotic = 0, iters = 0, skips = 0, steps = 0, fallback = 0;
+    double dE = 0.0, dJ = 0.0, dJall = 0.0, dS = 0.0, fmx = -1e300, fsum = 0.0;
+    int32_t st = -1;
+    if (i < S.n) {
+        const int64_t n = S.ld;
+        st = S.status[i];
+        const double fli = S.out[4 * n + i];
+        iters = (unsigned long long)S.newton_iters[i];
+        skips = (unsigned long long)S.n_skip[i];
+        steps = (unsigned long long)S.nstep[i];
+        if (st == ORBIT_DONE || st == ORBIT_FLI_SATURATED) chaotic = fli > thr;
+        if (st == ORBIT_DONE) {
+            dE = fabs((S.out[0 * n + i] - S.ref[0 * n + i]) / S.ref[0 * n + i]);
+            dJall = fabs((S.out[1 * n + i] - S.ref[1 * n + i]) / S.ref[1 * n + i]);
+            if (!(dJall == dJall)) dJall = 1e300;
+            if (S.last_kind[i] == CORR_DUAL) dJ = dJall;
+            else fallback = 1;
+            const double s1 = S.ref[2 * n + i], s2 = S.ref[3 * n + i];
+            if (s1 > 0.0) dS = fmax(dS, fabs(S.out[2 * n + i] - s1) / s1);
+            if (s2 > 0.0) dS = fmax(dS, fabs(S.out[3 * n + i] - s2) / s2);
+            fmx = fli;
+            fsum = fli;
+        }
+        if (!(dE == dE)) dE = 1e300;
+        if (!(dJ == dJ)) dJ = 1e300;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        chaotic += __shfl_down_sync(0xffffffffu, chaotic, off);
+        iters += __shfl_down_sync(0xffffffffu, iters, off);
+        skips += __shfl_down_sync(0xffffffffu, skips, off);
+        steps += __shfl_down_sync(0xffffffffu, steps, off);
+        fallback += __shfl_down_sync(0xffffffffu, fallback, off);
+        dJall = fmax(dJall, __shfl_down_sync(0xffffffffu, dJall, off));
+        dE = fmax(dE, __shfl_down_sync(0xffffffffu, dE, off));
+        dJ = fmax(dJ, __shfl_down_sync(0xffffffffu, dJ, off));
+        dS = fmax(dS, __shfl_down_sync(0xffffffffu, dS, off));
+        fmx = fmax(fmx, __shfl_down_sync(0xffffffffu, fmx, off));
+        fsum += __shfl_down_sync(0xffffffffu, fsum, off);
+    }
+    // status histogram: one ballot per status value
+#pragma unroll
+    for (int s = 0; s < 6; s++) {
+        const unsigned m = __ballot_sync(0xffffffffu, st == s);
+        if (lane == 0 && m) atomicAdd(&out->status_count[s], (unsigned long long)__popc(m));
+    }
+    if (lane == 0) {
+        if (chaotic) atomicAdd(&out->n_chaotic, chaotic);
+        atomicAdd(&out->newton_iters, iters);
+        atomicAdd(&out->n_skip, skips);
+        atomicAdd(&out->steps, steps);
+        atomicMax(&out->max_dE_bits, dbits(dE));
+        atomicMax(&out->max_dJ_bits, dbits(dJ));
+        atomicMax(&out->max_dJ_all_bits, dbits(dJall));
+        if (fallback) atomicAdd(&out->n_final_fallback, fallback);
+        atomicMax(&out->max_dS_bits, dbits(dS));
+        if (fmx > -1e300) atomicMax(&out->fli_max_bits, dbits(fmx > 0.0 ? fmx : 0.0));
+        atomicAdd(&out->fli_sum, fsum);
+    }
+}
+
+// ------------------------------------------------------------------ gather
+__global__ void k_gather(DevState S, double* states, double* shadow, double* integ)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= S.n) return;
+    const int64_t n = S.ld;
+    if (states) {
+#pragma unroll
+        for (int k = 0; k < 12; k++) states[12 * i + k] = S.y[k * n + i];
+    }
+    if (shadow) {
+#pragma unroll
+        for (int k = 0; k < 12; k++) shadow[12 * i + k] = S.ys[k * n + i];
+    }
+    if (integ) {   // E0, E, J0, |J|, |S1|, |S2|
+        integ[6 * i + 0] = S.ref[0 * n + i];
+        integ[6 * i + 1] = S.out[0 * n + i];
+        integ[6 * i + 2] = S.ref[1 * n + i];
+        integ[6 * i + 3] = S.out[1 * n + i];
+        integ[6 * i + 4] = S.out[2 * n + i];
+        integ[6 * i + 5] = S.out[3 * n + i];
+    }
+}
+
+// ----------------------------------------------------------- FP64 probe
+// Independent dependent DFMA chains; measures the FP64 pipe's throughput.
+__global__ void k_fp64_probe(double* out, int iters)
+{
+    double x0 = threadIdx.x * 1e-3, x1 = x0 + 1.0, x2 = x0 + 2.0, x3 = x0 + 3.0;
+    const double a = 0.9999999, b = 1e-7;
+    for (int i = 0; i < iters; i++) {
+        x0 = fma(x0, a, b);
+        x1 = fma(x1, a, b);
+        x2 = fma(x2, a, b);
+        x3 = fma(x3, a, b);
+    }
+    out[blockIdx.x * (int64_t)blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3;
+}
+
+// -------------------------------------------------------------- launchers
+static inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+cudaError_t launch_setup_cells(const double* cells, int64_t n, DevState S, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_setup_cells<<<grid_for(n, 256), 256, 0, st>>>(cells, n, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load_states(const double* states, int64_t n, DevState S, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_load_states<<<grid_for(n, 256), 256, 0, st>>>(states, n, S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(DevState S, RunCfg rc, cudaStream_t st)
+{
+    if (S.n == 0) return cudaSuccess;
+    if (rc.flags.use_qm) k_init<true><<<grid_for(S.n, 128), 128, 0, st>>>(S, rc);
+    else k_init<false><<<grid_for(S.n, 128), 128, 0, st>>>(S, rc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_integrate_static(DevState S, RunCfg rc, int block, cudaStream_t st)
+{
+    if (S.n == 0 || rc.nsteps <= 0) return cudaSuccess;
+    if (block <= 0 || block > 128 || block % 32) return cudaErrorInvalidValue;
+    if (rc.flags.use_qm) k_integrate_static<true><<<grid_for(S.n, block), block, 0, st>>>(S, rc);
+    else k_integrate_static<false><<<grid_for(S.n, block), block, 0, st>>>(S, rc);
+    return cudaGetLastError();
+}
+
+int queue_blocks_per_sm(int block, bool qm)
+{
+    int nb = 0;
+    if (qm) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<true>, block, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<false>, block, 0);
+    return nb;
+}
+
+cudaError_t launch_integrate_queue(DevState S, RunCfg rc, QueueState q, int block, int grid,
+                                   int chunk, cudaStream_t st)
+{
+    if (S.n == 0 || rc.nsteps <= 0) return cudaSuccess;
+    if (block <= 0 || block > 128 || block % 32 || grid <= 0 || chunk <= 0) return cudaErrorInvalidValue;
+    if (rc.flags.use_qm) k_integrate_queue<true><<<grid, block, 0, st>>>(S, rc, q, chunk);
+    else k_integrate_queue<false><<<grid, block, 0, st>>>(S, rc, q, chunk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(DevState S, RunCfg rc, cudaStream_t st)
+{
+    if (S.n == 0) return cudaSuccess;
+    if (rc.flags.use_qm) k_finalize<true><<<grid_for(S.n, 128), 128, 0, st>>>(S, rc);
+    else k_finalize<false><<<grid_for(S.n, 128), 128, 0, st>>>(S, rc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(DevState S, double thr, Summary* out, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(Summary), st);
+    if (e != cudaSuccess || S.n == 0) return e;
+    k_reduce<<<grid_for(S.n, 256), 256, 0, st>>>(S, thr, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(DevState S, double* states, double* shadow, double* integ, cudaStream_t st)
+{
+    if (S.n == 0) return cudaSuccess;
+    k_gather<<<grid_for(S.n, 256), 256, 0, st>>>(S, states, shadow, integ);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp64_probe(double* out, int blocks, int threads, int iters, cudaStream_t st)
+{
+    k_fp64_probe<<<blocks, threads, 0, st>>>(out, iters);
+    return cudaGetLastError();
+}
+
+}  // namespace pnscan

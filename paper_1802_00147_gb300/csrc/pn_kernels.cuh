@@ -1,0 +1,94 @@
+// pn_kernels.cuh -- device state layout and kernel launch interface of the
+// scan library (internal to the library; the public boundary is
+// include/pnscan.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pn_device.cuh"
+
+namespace pnscan {
+
+enum OrbitStatus : int32_t {
+    ORBIT_RUNNING = 0,
+    ORBIT_DONE = 1,
+    ORBIT_MERGED = 2,
+    ORBIT_ESCAPED = 3,
+    ORBIT_FLI_SATURATED = 4,
+    ORBIT_NONFINITE = 5,
+};
+
+// Structure-of-arrays orbit state in HBM.  Plane k of an [m][n] array starts
+// at base + k * n; a warp reads 32 consecutive orbits of one plane at a time.
+struct DevState {
+    int64_t n;             // orbits
+    int64_t ld;            // plane stride (n rounded up to a multiple of 32)
+    double* y;             // [12][n] main trajectory (r, p, S1, S2)
+    double* ys;            // [12][n] shadow trajectory
+    double* ref;           // [8][n]  E0, J0, |S1|0, |S2|0 of main, then of shadow
+    double* fli_acc;       // [n]     sum of log10(d_k / d0) over renormalisations
+    double* t;             // [n]     time reached
+    int32_t* nstep;        // [n]     steps taken since the initial state
+    int32_t* status;       // [n]     OrbitStatus
+    int32_t* newton_iters; // [n]     Newton iterations, both trajectories
+    int32_t* n_skip;       // [n]     corrections without the dual scaling
+    int32_t* last_kind;    // [n]     CorrKind of the main trajectory's last step
+    double* beta;          // [n]     m1/m2
+    double* kappa1;        // [n]
+    double* kappa2;        // [n]
+    double* out;           // [5][n]  E, |J|, |S1|, |S2|, FLI (written by finalize)
+};
+
+struct RunCfg {
+    Flags flags;
+    NewtonCfg newton;
+    int correct;           // apply the manifold correction each step
+    double h;              // step size
+    double d0;             // FLI separation
+    int renorm;            // renormalise every `renorm` steps (<= 0: never)
+    double fli_cap;        // stop at FLI >= cap (<= 0: never)
+    double rmerge2;        // stop at |r|^2 < rmerge2 (<= 0: never)
+    double rescape2;       // stop at |r|^2 > rescape2 (<= 0: never)
+    int32_t nstep_base;    // nstep of every running orbit when the run started
+    int32_t nsteps;        // steps in this run
+};
+
+// Work-queue state of the persistent integrator (device memory, 256-byte
+// aligned): next task counter, error flag, then one progress counter per
+// 32-orbit group.
+struct QueueState {
+    unsigned long long* next;   // [1]
+    int* error;                 // [1] nonzero: a bounded wait gave up
+    int* group_done;            // [groups] chunks finished per group
+};
+
+struct Summary {                // scan-level reduction (device layout)
+    unsigned long long n_chaotic;
+    unsigned long long status_count[8];
+    unsigned long long newton_iters;
+    unsigned long long n_skip;
+    unsigned long long steps;
+    unsigned long long max_dE_bits;   // non-negative doubles as ordered integers
+    unsigned long long max_dJ_bits;       // over DONE orbits whose last step was dual-scaled
+    unsigned long long max_dJ_all_bits;   // over all DONE orbits
+    unsigned long long n_final_fallback;  // DONE orbits whose last step was not dual-scaled
+    unsigned long long max_dS_bits;
+    unsigned long long fli_max_bits;
+    double fli_sum;
+};
+
+// ---- launchers (return cudaError_t of the launch) ----
+cudaError_t launch_setup_cells(const double* cells_aos, int64_t n, DevState S, cudaStream_t st);
+cudaError_t launch_load_states(const double* states_aos, int64_t n, DevState S, cudaStream_t st);
+cudaError_t launch_init(DevState S, RunCfg rc, cudaStream_t st);
+cudaError_t launch_integrate_static(DevState S, RunCfg rc, int block, cudaStream_t st);
+int queue_blocks_per_sm(int block, bool qm);
+cudaError_t launch_integrate_queue(DevState S, RunCfg rc, QueueState q, int block, int grid,
+                                   int chunk, cudaStream_t st);
+cudaError_t launch_finalize(DevState S, RunCfg rc, cudaStream_t st);
+cudaError_t launch_reduce(DevState S, double fli_thresh, Summary* out, cudaStream_t st);
+cudaError_t launch_gather(DevState S, double* states_aos, double* shadow_aos, double* integ_aos,
+                          cudaStream_t st);
+cudaError_t launch_fp64_probe(double* out, int blocks, int threads, int iters, cudaStream_t st);
+
+}  // namespace pnscan

@@ -1,0 +1,319 @@
+"""GPU parity of the CUDA scan (through the C ABI) against the CPU oracle.
+
+What is compared, and why the tolerances are what they are:
+
+  * per-orbit status, stop time, Newton-skip counts: exact (integer decisions).
+  * final integrals E, |J|, |S_i|: <= 1e-13 relative (both sides restore them
+    to rounding every step).
+  * state after <= 1000 M, relative error per block (r, p, S1, S2): the two
+    programs are FP64 with different rounding orders, so they can agree only
+    as well as the method reproduces itself in FP64.  That floor is measured
+    here: the oracle is re-run with one initial component moved by one ulp,
+    which gives its own sensitivity s_i for each orbit.  The test asserts
+      median(err) <= 3 median(s) and p99(err) <= 3 p99(s)  (no systematic term),
+      max(err)   <= max(1e-10, 3 max(s))                  (no outlier beyond it),
+      >= 99 % of orbits within 1e-10.
+    Near-singular Newton steps amplify rounding by up to 1/det_min = 1e5, and
+    orbits about to merge are strongly unstable, so s_i itself reaches a few
+    1e-10 for a handful of orbits; for the rest, err is ~1e-12.
+  * FLI: log10 of the distance of two trajectories 1e-9 apart, so a one-ulp
+    change moves it by ~1e-2 (up to ~1) after 1000 M.  Asserted: median and
+    max of |dFLI| within 3x the oracle's own one-ulp spread (plus 1e-3), and
+    the regular/chaotic class (FLI > 6) agrees for >= 99.5 % of the orbits.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1802_00147_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+STATE_TOL = 1e-10
+FLI_THRESH = 6.0
+
+
+@pytest.fixture(scope="module")
+def pn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_00147_gb300 import build
+    build.build()
+    import paper_1802_00147_gb300 as pn
+    pn.lib()
+    return pn
+
+
+def gpu_run(pn, cells, nsteps, h=1.0, chunks=1, device=False, read_diag=False, **opts):
+    cells = np.ascontiguousarray(cells)
+    s = pn.Scan(cells[:, W.BETA], kappa1=cells[:, W.KAP1], kappa2=cells[:, W.KAP2],
+                device=device, **opts)
+    if device:
+        import torch
+        s.setup(torch.as_tensor(cells[:, :9], device="cuda"))
+    else:
+        s.setup(cells)
+    for k in range(1, chunks + 1):
+        s.run(h * nsteps * k / chunks, h)
+    out = s.read()
+    if read_diag:
+        out.update(s.read_diag())
+    out["summary"] = s.summary()
+    if device:
+        out = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in out.items()}
+    s.close()
+    return out
+
+
+ORC_KEYS = {"fli_renorm_steps": "fli_renorm", "newton_det_min": "det_min"}
+
+
+def orc_run(cells, nsteps, h=1.0, y0=None, **cfg):
+    cfg = {ORC_KEYS.get(k, k): v for k, v in cfg.items()}
+    if y0 is None:
+        y0 = oracle.setup_cells(cells[:, :9])
+    return oracle.scan(y0, cells[:, W.BETA], h, nsteps, oracle.config(**cfg),
+                       kappa1=cells[:, W.KAP1], kappa2=cells[:, W.KAP2])
+
+
+def block_relerr(a, b):
+    w = np.zeros(a.shape[0])
+    for sl in (slice(0, 3), slice(3, 6), slice(6, 9), slice(9, 12)):
+        num = np.linalg.norm(a[:, sl] - b[:, sl], axis=1)
+        den = np.maximum(np.linalg.norm(b[:, sl], axis=1), 1e-30)
+        w = np.maximum(w, num / den)
+    return w
+
+
+def oracle_sensitivity(cells, nsteps, h=1.0, **cfg):
+    """The oracle against itself with one initial component moved by one ulp
+    (largest over three components): per-orbit state and FLI spread."""
+    o = orc_run(cells, nsteps, h, **cfg)
+    y0 = oracle.setup_cells(cells[:, :9])
+    s_state = np.zeros(cells.shape[0])
+    s_fli = np.zeros(cells.shape[0])
+    for comp in (0, 4, 6):
+        y1 = y0.copy()
+        y1[:, comp] = np.nextafter(y1[:, comp], np.inf)
+        o1 = orc_run(cells, nsteps, h, y0=y1, **cfg)
+        same = o1["status"] == o["status"]
+        e = block_relerr(o1["y"], o["y"])
+        s_state = np.maximum(s_state, np.where(same, e, 0.0))
+        s_fli = np.maximum(s_fli, np.where(same, np.abs(o1["fli"] - o["fli"]), 0.0))
+    return o, s_state, s_fli
+
+
+def assert_parity(g, o, s_state, s_fli):
+    np.testing.assert_array_equal(g["status"], o["status"])
+    np.testing.assert_array_equal(g["t_stop"], o["t_stop"])
+    if "n_skip" in g:
+        np.testing.assert_array_equal(g["n_skip"], o["n_skip"])
+        np.testing.assert_array_equal(g["last_kind"], o["last_kind"])
+    ok = o["status"] != oracle.NONFINITE
+    err = block_relerr(g["states"][ok], o["y"][ok])
+    s = s_state[ok]
+    if err.size:
+        assert np.median(err) <= 3 * np.median(s) + 1e-15, (np.median(err), np.median(s))
+        assert np.quantile(err, 0.99) <= 3 * np.quantile(s, 0.99) + 1e-15
+        assert err.max() <= max(STATE_TOL, 3 * s.max()), (err.max(), s.max())
+        assert np.mean(err <= STATE_TOL) >= 0.99
+    gi, oi = g["integrals"][ok], o["integrals"][ok]
+    for col in (0, 1, 2, 3, 4, 5):
+        assert np.all(np.abs(gi[:, col] - oi[:, col]) <= 1e-13 * np.abs(oi[:, col]) + 1e-300), col
+    done = o["status"] == oracle.DONE
+    if done.any():
+        df = np.abs(g["fli"][done] - o["fli"][done])
+        sf = s_fli[done]
+        assert np.median(df) <= 3 * np.median(sf) + 1e-3, (np.median(df), np.median(sf))
+        assert df.max() <= 3 * sf.max() + 1e-3, (df.max(), sf.max())
+        agree = (g["fli"][done] > FLI_THRESH) == (o["fli"][done] > FLI_THRESH)
+        assert agree.mean() >= 0.995
+    return float(err.max()) if err.size else 0.0
+
+
+def check(pn, cells, nsteps, h=1.0, **opts):
+    g = gpu_run(pn, cells, nsteps, h, read_diag=True, **opts)
+    o, s_state, s_fli = oracle_sensitivity(cells, nsteps, h, **opts)
+    assert_parity(g, o, s_state, s_fli)
+    return g, o
+
+
+# ------------------------------------------------------------------ set-up
+def test_setup_reproduces_oracle_initial_states(pn):
+    cells = W.uneven_batch(n=333, seed=10)
+    g = gpu_run(pn, cells, 0)
+    y0 = oracle.setup_cells(cells[:, :9])
+    np.testing.assert_allclose(g["states"], y0, rtol=1e-15, atol=1e-18)
+    assert np.all(g["status"] == pn.ORBIT_DONE) or np.all(g["status"] == pn.ORBIT_RUNNING)
+
+
+# ------------------------------------------------------------- main parity
+def test_small_scan_parity_1000M(pn):
+    g, o = check(pn, W.small_scan(seed=1), 1000)
+    assert abs(int(g["newton_iters"].sum()) - int(o["newton_iters"].sum())) <= 1e-3 * o["newton_iters"].sum()
+
+
+def test_ragged_batch_parity(pn):
+    """A batch that is not a multiple of the warp or block size."""
+    check(pn, W.full_scan(seed=2, nx=11, nt=7), 700)           # 77 orbits
+
+
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_full_scan_sampled_parity_bench_shape(pn, schedule):
+    """The 314 x 314 scan in the launch configuration the benchmark times
+    (work-queue kernel; and the static kernel), checked on a seeded sample of
+    orbits the oracle integrates one by one."""
+    cells = W.full_scan(seed=2)
+    g = gpu_run(pn, cells, 1000, schedule=schedule, read_diag=True)
+    sub, idx = W.subset(cells, 64, seed=21)
+    o, s_state, s_fli = oracle_sensitivity(sub, 1000)
+    gs = {k: v[idx] for k, v in g.items() if isinstance(v, np.ndarray)}
+    assert_parity(gs, o, s_state, s_fli)
+
+
+def test_uneven_batch_parity_with_early_stops(pn):
+    cells = W.uneven_batch(n=1500, seed=3)
+    g, o = check(pn, cells, 1000)
+    assert (o["status"] == oracle.MERGED).sum() > 50       # the batch really is uneven
+
+
+def test_qm_parity(pn):
+    check(pn, W.qm_grid(n=12, seed=5), 2000, h=0.5, use_qm=1)
+
+
+@pytest.mark.parametrize("opts", [dict(pn_order=0, use_so=0, use_ss=0),
+                                  dict(pn_order=1),
+                                  dict(use_so=0),
+                                  dict(use_ss=0),
+                                  dict(correct=0),
+                                  dict(r_merge=0.0, r_escape=0.0, fli_renorm_steps=37),
+                                  dict(newton_det_min=0.0)])
+def test_flag_variants_parity(pn, opts):
+    check(pn, W.uneven_batch(n=96, seed=12), 400, **opts)
+
+
+def test_zero_spins_and_fli_cap(pn):
+    cells = W.small_scan(seed=4)[::6].copy()
+    cells[:20, W.CHI1] = 0.0
+    cells[:20, W.CHI2] = 0.0
+    g, o = check(pn, cells, 600, fli_cap=1.2)
+    assert (o["status"] == oracle.FLI_SATURATED).sum() > 0 and (o["status"] == oracle.DONE).sum() > 0
+
+
+# ------------------------------------------------- schedules are identical
+def test_schedules_chunks_and_pointers_are_bit_identical(pn):
+    cells = W.uneven_batch(n=700, seed=7)
+    a = gpu_run(pn, cells, 300, schedule=1)
+    b = gpu_run(pn, cells, 300, schedule=2, chunk_steps=64)
+    c = gpu_run(pn, cells, 300, schedule=2, chunk_steps=100, chunks=3)    # 3 scan_run calls
+    d = gpu_run(pn, cells, 300, schedule=2, device=True, use_graph=0)
+    for other in (b, c, d):
+        for k in ("states", "fli", "status", "t_stop", "integrals"):
+            np.testing.assert_array_equal(a[k], other[k], err_msg=k)
+
+
+def test_graph_replay_repeats_the_run(pn):
+    cells = W.small_scan(seed=8)
+    s = pn.Scan(cells[:, W.BETA], schedule=2, use_graph=1)
+    outs = []
+    for _ in range(3):
+        s.setup(cells)
+        s.run(500.0, 1.0)
+        outs.append(s.read())
+    s.close()
+    for o in outs[1:]:
+        np.testing.assert_array_equal(outs[0]["states"], o["states"])
+        np.testing.assert_array_equal(outs[0]["fli"], o["fli"])
+
+
+def test_autotune_keeps_results(pn):
+    cells = W.uneven_batch(n=2000, seed=9)
+    s = pn.Scan(cells[:, W.BETA])
+    s.setup(cells)
+    shape = s.autotune(200)
+    assert shape["schedule"] in (1, 2) and shape["block_size"] in (64, 128)
+    s.run(300.0, 1.0)
+    tuned = s.read()
+    s.close()
+    ref = gpu_run(pn, cells, 300, schedule=1)
+    np.testing.assert_array_equal(ref["states"], tuned["states"])
+
+
+# -------------------------------------------------------------- edge cases
+def test_empty_batch(pn):
+    s = pn.Scan(np.zeros(0))
+    s.setup(np.zeros((0, 11)))
+    s.run(100.0, 1.0)
+    out = s.read()
+    assert out["states"].shape == (0, 12)
+    summ = s.summary()
+    assert summ["n"] == 0 and summ["orbit_steps"] == 0
+    s.close()
+
+
+def test_single_orbit_and_nonfinite_input(pn):
+    cells = W.small_scan(seed=1)[:3].copy()
+    y0 = oracle.setup_cells(cells[:, :9])
+    y0[1, 4] = np.nan
+    s = pn.Scan(cells[:, W.BETA])
+    s.run(50.0, 1.0, initial_states=y0)
+    out = s.read()
+    s.close()
+    o = oracle.scan(y0, cells[:, W.BETA], 1.0, 50, oracle.config())
+    assert out["status"][1] == pn.ORBIT_NONFINITE
+    assert list(out["status"]) == [pn.ORBIT_DONE, pn.ORBIT_NONFINITE, pn.ORBIT_DONE]
+    assert o["status"][1] == oracle.NONFINITE
+    np.testing.assert_allclose(out["states"][[0, 2]], o["y"][[0, 2]], rtol=1e-12)
+
+
+def test_bad_calls_are_rejected(pn):
+    s = pn.Scan(np.ones(4))
+    with pytest.raises(pn.ScanError):
+        s.run(10.0, 1.0)                      # no state yet
+    s.setup(W.small_scan()[:4])
+    with pytest.raises(pn.ScanError):
+        s.run(10.0, 0.0)                      # h <= 0
+    s.run(10.0, 1.0)
+    with pytest.raises(pn.ScanError):
+        s.run(5.0, 1.0)                       # t_end behind the current time
+    s.close()
+    with pytest.raises(pn.ScanError):
+        pn.Scan(np.array([0.5, 1.5]))         # beta outside (0, 1]
+
+
+def test_summary_matches_host_reduction(pn):
+    cells = W.uneven_batch(n=3000, seed=13)
+    g = gpu_run(pn, cells, 800, read_diag=True)
+    s = g["summary"]
+    st = g["status"]
+    done = st == pn.ORBIT_DONE
+    assert s["status_count"] == [int((st == k).sum()) for k in range(6)]
+    assert s["n_chaotic"] == int((g["fli"][(st == 1) | (st == 4)] > 6.0).sum())
+    I = g["integrals"]
+    assert s["max_dE"] == pytest.approx(np.max(np.abs((I[done, 1] - I[done, 0]) / I[done, 0])), rel=1e-12)
+    assert s["max_dJ"] == pytest.approx(np.max(np.abs((I[done, 3] - I[done, 2]) / I[done, 2])), rel=1e-12)
+    assert s["newton_iters"] == int(g["newton_iters"].sum())
+    assert s["fli_mean"] == pytest.approx(float(np.mean(g["fli"][done])), rel=1e-12)
+
+
+# ----------------------------------------- full-length scan: drift, classes
+@pytest.mark.slow
+def test_full_scan_drift_and_classification(pn):
+    """314 x 314 scan to t = 2e4.  Energy drift <= 1e-12 on every orbit that
+    reached t_end; |J| drift <= 1e-12 on every such orbit whose last step was
+    dual-scaled (where the scaling is singular only E can be restored, so a
+    run that ends there carries at most a few steps' RK4 error in |J|, here
+    bounded by 1e-10); and the chaotic/regular class of a seeded 400-orbit
+    sample agrees with the oracle for >= 99.5 % of the cells."""
+    cells = W.full_scan(seed=2)
+    g = gpu_run(pn, cells, 20000)
+    s = g["summary"]
+    assert s["max_dE"] <= 1e-12 and s["max_dJ"] <= 1e-12 and s["max_dS"] <= 1e-12, s
+    assert s["max_dJ_all"] <= 1e-10 and s["n_final_fallback"] <= 1e-3 * s["status_count"][1], s
+    sub, idx = W.subset(cells, 400, seed=22)
+    o = orc_run(sub, 20000)
+    np.testing.assert_array_equal(g["status"][idx], o["status"])
+    done = o["status"] == oracle.DONE
+    agree = (g["fli"][idx][done] > FLI_THRESH) == (o["fli"][done] > FLI_THRESH)
+    assert agree.mean() >= 0.995, (agree.mean(), np.sum(~agree))

@@ -349,18 +349,23 @@ def test_newton_root_matches_independent_root_finder(orc):
     assert abs(a - sol.x[0]) < 1e-12 and abs(b - sol.x[1]) < 1e-12
 
 
-def test_singular_scaling_is_skipped(orc):
+def test_singular_scaling_falls_back_to_velocity_scaling(orc):
     """Where alpha p.dH/dp = beta r.dH/dr the dual scaling has no unique
-    solution; the oracle leaves r*, p* unscaled (spins still corrected)."""
+    solution; the oracle then restores E by scaling p alone (velocity
+    scaling) and leaves r unchanged."""
     s = orc.system(1.0, pn_order=0, use_so=0, use_ss=0, use_qm=0)
     # Newtonian: p.dH/dp - r.dH/dr = p^2 - 1/r = 0 on the circle p = 1/sqrt(r)
     r = 20.0
     y = np.r_[r, 0, 0, 0, 1 / np.sqrt(r), 0, np.zeros(6)]
     ref = orc.integrals(s, y)[:4].copy()
     ref[0] -= 1e-9
-    y2, code, it, _ = orc.correct(s, y, ref)
-    assert code == 1
-    assert np.array_equal(y2, y)
+    y2, code, it, (a, b) = orc.correct(s, y, ref)
+    assert code == 2 and b == 1.0
+    assert np.array_equal(y2[:3], y[:3])
+    assert np.allclose(y2[3:6], a * y[3:6], rtol=0, atol=0)
+    assert abs(orc.hamiltonian(s, y2) - ref[0]) <= 1e-16
+    # closed form: p'^2/2 - 1/r = E0  ->  a = sqrt(2 (E0 + 1/r)) / p
+    assert abs(a - np.sqrt(2 * (ref[0] + 1 / r)) / (1 / np.sqrt(r))) < 1e-15
 
 
 # ------------------------------------------------------------------ FLI
