@@ -104,7 +104,7 @@ def oracle_sensitivity(cells, nsteps, h=1.0, **cfg):
     return o, s_state, s_fli
 
 
-def assert_parity(g, o, s_state, s_fli):
+def assert_parity(g, o, s_state, s_fli, nsteps):
     np.testing.assert_array_equal(g["status"], o["status"])
     np.testing.assert_array_equal(g["t_stop"], o["t_stop"])
     if "n_skip" in g:
@@ -113,9 +113,12 @@ def assert_parity(g, o, s_state, s_fli):
     ok = o["status"] != oracle.NONFINITE
     err = block_relerr(g["states"][ok], o["y"][ok])
     s = s_state[ok]
+    # each step the two programs round differently (about one ulp), which a
+    # non-amplifying run accumulates to at most ~nsteps ulp
+    floor = nsteps * 2.0 ** -52
     if err.size:
-        assert np.median(err) <= 3 * np.median(s) + 1e-15, (np.median(err), np.median(s))
-        assert np.quantile(err, 0.99) <= 3 * np.quantile(s, 0.99) + 1e-15
+        assert np.median(err) <= 3 * np.median(s) + floor, (np.median(err), np.median(s))
+        assert np.quantile(err, 0.99) <= 3 * np.quantile(s, 0.99) + floor
         assert err.max() <= max(STATE_TOL, 3 * s.max()), (err.max(), s.max())
         assert np.mean(err <= STATE_TOL) >= 0.99
     gi, oi = g["integrals"][ok], o["integrals"][ok]
@@ -135,7 +138,7 @@ def assert_parity(g, o, s_state, s_fli):
 def check(pn, cells, nsteps, h=1.0, **opts):
     g = gpu_run(pn, cells, nsteps, h, read_diag=True, **opts)
     o, s_state, s_fli = oracle_sensitivity(cells, nsteps, h, **opts)
-    assert_parity(g, o, s_state, s_fli)
+    assert_parity(g, o, s_state, s_fli, nsteps)
     return g, o
 
 
@@ -169,7 +172,7 @@ def test_full_scan_sampled_parity_bench_shape(pn, schedule):
     sub, idx = W.subset(cells, 64, seed=21)
     o, s_state, s_fli = oracle_sensitivity(sub, 1000)
     gs = {k: v[idx] for k, v in g.items() if isinstance(v, np.ndarray)}
-    assert_parity(gs, o, s_state, s_fli)
+    assert_parity(gs, o, s_state, s_fli, 1000)
 
 
 def test_uneven_batch_parity_with_early_stops(pn):
