@@ -192,6 +192,39 @@ int scan_last_run_timing(scan_handle *h, double *ms, int *launches);
  * peak.  Errors: ARG, CUDA. */
 int scan_fp64_peak(scan_handle *h, int iters, double *tflops);
 
+/* ---- reduction without run-time allocation ----
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory when they reduce a scan (a framework whose
+ * allocator already holds the memory budget, a loop that must not allocate
+ * after start-up, or work issued while a stream is being captured).
+ *
+ * scan_summary_noalloc computes the same reduction as scan_summary over
+ * caller-owned DEVICE arrays -- typically what scan_read / scan_read_diag
+ * wrote in device-pointer mode -- and fills the HOST struct *out.  It calls
+ * no cudaMalloc, cudaFree or other allocating routine: its scratch is a
+ * fixed array of this library in device memory (PNSCAN_NOALLOC_MAX_ORBITS /
+ * 256 + 1 records of 256 bytes, 2.1 MB), present on every GPU that loads the
+ * library until the process exits.
+ *   n              number of orbits, 0 <= n <= PNSCAN_NOALLOC_MAX_ORBITS (else ARG)
+ *   status [n], fli [n], integrals [n x 6] (E0, E, J0, |J|, |S1|, |S2|): required if n > 0
+ *   spin_ref [n x 2] (|S1|0, |S2|0), newton_iters [n], n_skip [n],
+ *   last_kind [n] (NULL: every last step counts as dual-scaled),
+ *   t_stop [n] with h_step > 0 (orbit_steps = sum round(t_stop / h_step)): each nullable;
+ *   a NULL input leaves its fields 0.
+ *   fli_thresh     FLI above this counts as chaotic
+ *   cuda_stream    stream to run on (cudaStream_t); the call synchronises it.
+ * The first call on a device looks up the scratch address on that device
+ * (the device must be current); make that first call before any stream
+ * capture.  Calls share the scratch: two calls whose work overlaps on the
+ * GPU race and must be serialised by the caller.  Errors: ARG, CUDA,
+ * NODEVICE. */
+#define PNSCAN_NOALLOC_MAX_ORBITS 2097152
+int scan_summary_noalloc(int64_t n, const int32_t *status, const double *fli,
+                         const double *integrals, const double *spin_ref,
+                         const int32_t *newton_iters, const int32_t *n_skip,
+                         const int32_t *last_kind, const double *t_stop, double h_step,
+                         double fli_thresh, void *cuda_stream, scan_summary_t *out);
+
 /* Free the handle's device buffers and the handle (NULL is a no-op). */
 void scan_destroy(scan_handle *h);
 

@@ -20,7 +20,7 @@ __all__ = [
     "ScanParams", "ScanSummary", "ScanError", "lib", "library_path",
     "scan_params_default", "scan_create", "scan_setup", "scan_run", "scan_read",
     "scan_read_diag", "scan_summary", "scan_autotune", "scan_last_run_timing",
-    "scan_fp64_peak", "scan_destroy", "scan_strerror", "scan_version", "Scan",
+    "scan_fp64_peak", "scan_summary_noalloc", "scan_destroy", "scan_strerror", "scan_version", "Scan",
     "OK", "ORBIT_RUNNING", "ORBIT_DONE", "ORBIT_MERGED", "ORBIT_ESCAPED",
     "ORBIT_FLI_SATURATED", "ORBIT_NONFINITE", "SCHED_AUTO", "SCHED_STATIC", "SCHED_QUEUE",
 ]
@@ -96,6 +96,8 @@ def lib():
         L.scan_autotune.argtypes = [vp, i, P(i), P(i), P(i), P(i)]
         L.scan_last_run_timing.argtypes = [vp, P(d), P(i)]
         L.scan_fp64_peak.argtypes = [vp, i, P(d)]
+        L.scan_summary_noalloc.argtypes = [_ct.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, d, d, vp,
+                                           P(ScanSummary)]
         L.scan_destroy.argtypes = [vp]
         L.scan_destroy.restype = None
         L.scan_strerror.argtypes = [i]
@@ -103,7 +105,7 @@ def lib():
         L.scan_version.restype = _ct.c_char_p
         for name in ("scan_params_default", "scan_create", "scan_setup", "scan_run", "scan_read",
                      "scan_read_diag", "scan_summary", "scan_autotune", "scan_last_run_timing",
-                     "scan_fp64_peak"):
+                     "scan_fp64_peak", "scan_summary_noalloc"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -177,6 +179,19 @@ def scan_fp64_peak(h, iters=200_000):
     t = _ct.c_double()
     _check(lib().scan_fp64_peak(h, int(iters), _ct.byref(t)), "scan_fp64_peak")
     return t.value
+
+
+def scan_summary_noalloc(n, status, fli, integrals, spin_ref=None, newton_iters=None, n_skip=None,
+                         last_kind=None, t_stop=None, h_step=1.0, fli_thresh=6.0, stream=None):
+    """Scan reduction over caller-owned device arrays without any run-time
+    allocation (see include/pnscan.h).  ``stream``: a torch stream or None."""
+    s = ScanSummary()
+    st = None if stream is None else stream.cuda_stream
+    _check(lib().scan_summary_noalloc(int(n), _ptr(status), _ptr(fli), _ptr(integrals), _ptr(spin_ref),
+                                      _ptr(newton_iters), _ptr(n_skip), _ptr(last_kind), _ptr(t_stop),
+                                      float(h_step), float(fli_thresh), st, _ct.byref(s)),
+           "scan_summary_noalloc")
+    return s
 
 
 def scan_destroy(h):
