@@ -71,7 +71,8 @@ extern "C" {
 /* Per-scan configuration.  scan_params_default() fills the paper's values. */
 typedef struct scan_params {
     int64_t n;               /* number of orbits (>= 0) */
-    const double *beta_m;    /* [n] mass ratio m1/m2 in (0, 1] (Sec. 2); required if n > 0 */
+    const double *beta_m;    /* [n] mass ratio m1/m2 in (0, 1] (Sec. 2); NULL: taken from each cell
+                                by scan_setup (scan_run with initial states is then refused) */
     const double *kappa1;    /* [n] quadrupole-monopole multipliers; NULL = 1 (black holes) */
     const double *kappa2;    /* [n] */
     int pn_order;            /* 0: Newtonian, 1: +1PN, 2: +2PN orbital terms (default 2) */
@@ -224,6 +225,64 @@ int scan_summary_noalloc(int64_t n, const int32_t *status, const double *fli,
                          const int32_t *newton_iters, const int32_t *n_skip,
                          const int32_t *last_kind, const double *t_stop, double h_step,
                          double fli_thresh, void *cuda_stream, scan_summary_t *out);
+
+/* ---- surrogate network (the learned map of the adaptive scan) ----
+ * Not in the paper: an ensemble of `members` networks mapping a cell's
+ * (x0, theta, mass ratio, chi) to its FLI,
+ *   z = (x - center) / scale, h1 = tanh(W1 z + b1), h2 = tanh(W2 h1 + b2),
+ *   FLI ~ w3 . h2 + b3, 64 hidden units per layer,
+ * with BF16 tensor-core operands, FP32 accumulation, FP32 master weights and
+ * Adam moments (beta1 0.9, beta2 0.999, eps 1e-8).  The parameter vector of
+ * a member (MLP_PARAMS floats) is W1 (64 x 4 row-major), b1, W2 (64 x 64,
+ * [out][in]), b2, w3, b3.  All array arguments are DEVICE pointers; the
+ * handle owns its parameters (cudaMalloc'ed at creation).  Calls run on the
+ * handle's stream; mlp_train, mlp_gradient and mlp_get/set_params
+ * synchronise it, mlp_predict does not. */
+#define MLP_INPUTS 4
+#define MLP_HIDDEN 64
+#define MLP_PARAMS 4545
+#define MLP_BATCH 128
+typedef struct mlp_handle mlp_handle;
+
+/* Xavier-uniform weights from seed (SplitMix64), zero biases and moments.
+ * center/scale: host float[4].  members in 1..64.  Errors: ARG, OOM, CUDA, NODEVICE. */
+int mlp_create(int members, uint64_t seed, const float *center, const float *scale, void *cuda_stream,
+               mlp_handle **out);
+/* Copy all members' parameters out / in ([members][MLP_PARAMS] floats);
+ * mlp_set_params also clears the Adam moments. */
+int mlp_get_params(mlp_handle *h, float *params);
+int mlp_set_params(mlp_handle *h, const float *params);
+/* `steps` Adam steps of minibatch MSE training on (X [n][4], y [n]); each
+ * step draws MLP_BATCH rows with replacement from SplitMix64(seed, member,
+ * step, row).  loss_hist [members][steps] (nullable) gets each step's loss. */
+int mlp_train(mlp_handle *h, const float *X, const float *y, int64_t n, int steps, float lr, uint64_t seed,
+              float *loss_hist);
+/* Loss and gradient of every member on exactly MLP_BATCH rows (X [128][4],
+ * y [128]): grad [members][MLP_PARAMS], loss [members].  No update. */
+int mlp_gradient(mlp_handle *h, const float *X, const float *y, float *grad, float *loss);
+/* Ensemble mean and spread (max - min over members) for X [n][4]. */
+int mlp_predict(mlp_handle *h, const float *X, int64_t n, float *mean, float *spread);
+void mlp_destroy(mlp_handle *h);
+
+/* ---- adaptive scan: features, selection and merge ----
+ * Not in the paper.  adaptive_select marks cell i when |mean_i - thr| <= band,
+ * spread_i > spread_max, or mean_i is NaN; writes the marked indices in
+ * ascending order to idx [n], gathers their rows of cells [n][9] (nullable)
+ * into cells_out (nullable), and returns the number marked in *count (host;
+ * synchronises).  workspace: device memory of adaptive_select_workspace(n)
+ * bytes owned by the caller.  n <= 16,777,216.  adaptive_merge writes the
+ * class map cls [n] (1 chaotic, 0 not): marked cells take the integrator's
+ * result (chaotic if status is DONE or FLI_SATURATED and fli_sel > thr),
+ * the others the surrogate's (mean > thr).  adaptive_features writes the
+ * surrogate inputs X [n][4] = (x0, theta1, beta, chi1) of cells [n][9] as
+ * float.  Device pointers throughout. */
+int adaptive_features(const double *cells, int64_t n, float *X, void *cuda_stream);
+size_t adaptive_select_workspace(int64_t n);
+int adaptive_select(const float *mean, const float *spread, int64_t n, float thr, float band, float spread_max,
+                    const double *cells, int32_t *idx, double *cells_out, int64_t *count, void *workspace,
+                    void *cuda_stream);
+int adaptive_merge(const float *mean, int64_t n, float thr, const int32_t *idx, int64_t count,
+                   const double *fli_sel, const int32_t *status_sel, int8_t *cls, void *cuda_stream);
 
 /* Free the handle's device buffers and the handle (NULL is a no-op). */
 void scan_destroy(scan_handle *h);

@@ -23,6 +23,7 @@ __all__ = [
     "scan_fp64_peak", "scan_summary_noalloc", "scan_destroy", "scan_strerror", "scan_version", "Scan",
     "OK", "ORBIT_RUNNING", "ORBIT_DONE", "ORBIT_MERGED", "ORBIT_ESCAPED",
     "ORBIT_FLI_SATURATED", "ORBIT_NONFINITE", "SCHED_AUTO", "SCHED_STATIC", "SCHED_QUEUE",
+    "MLP_PARAMS", "MLP_BATCH", "Surrogate", "adaptive_features", "adaptive_select", "adaptive_merge",
 ]
 
 _HERE = _os.path.dirname(_os.path.abspath(__file__))
@@ -98,6 +99,24 @@ def lib():
         L.scan_fp64_peak.argtypes = [vp, i, P(d)]
         L.scan_summary_noalloc.argtypes = [_ct.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, d, d, vp,
                                            P(ScanSummary)]
+        f, u64, i64 = _ct.c_float, _ct.c_uint64, _ct.c_int64
+        L.mlp_create.argtypes = [i, u64, P(f), P(f), vp, P(vp)]
+        L.mlp_get_params.argtypes = [vp, vp]
+        L.mlp_set_params.argtypes = [vp, vp]
+        L.mlp_train.argtypes = [vp, vp, vp, i64, i, f, u64, vp]
+        L.mlp_gradient.argtypes = [vp, vp, vp, vp, vp]
+        L.mlp_predict.argtypes = [vp, vp, i64, vp, vp]
+        L.mlp_destroy.argtypes = [vp]
+        L.mlp_destroy.restype = None
+        L.adaptive_features.argtypes = [vp, i64, vp, vp]
+        L.adaptive_features.restype = i
+        L.adaptive_select_workspace.argtypes = [i64]
+        L.adaptive_select_workspace.restype = _ct.c_size_t
+        L.adaptive_select.argtypes = [vp, vp, i64, f, f, f, vp, vp, vp, P(i64), vp, vp]
+        L.adaptive_merge.argtypes = [vp, i64, f, vp, i64, vp, vp, vp, vp]
+        for name in ("mlp_create", "mlp_get_params", "mlp_set_params", "mlp_train", "mlp_gradient",
+                     "mlp_predict", "adaptive_select", "adaptive_merge"):
+            getattr(L, name).restype = i
         L.scan_destroy.argtypes = [vp]
         L.scan_destroy.restype = None
         L.scan_strerror.argtypes = [i]
@@ -217,7 +236,8 @@ class Scan:
     torch stream.
     """
 
-    def __init__(self, beta, kappa1=None, kappa2=None, device=False, stream=None, **opts):
+    def __init__(self, beta, kappa1=None, kappa2=None, device=False, stream=None, n=None, **opts):
+        """beta None: mass ratios come from the cells given to setup() (n required)."""
         p = scan_params_default()
         self.device = bool(device)
         self._keep = {}
@@ -225,7 +245,7 @@ class Scan:
             import torch
             self._torch = torch
             dev = torch.device("cuda", torch.cuda.current_device())
-            beta = torch.as_tensor(beta, dtype=torch.float64, device=dev).contiguous()
+            beta = None if beta is None else torch.as_tensor(beta, dtype=torch.float64, device=dev).contiguous()
             kappa1 = None if kappa1 is None else torch.as_tensor(kappa1, dtype=torch.float64, device=dev).contiguous()
             kappa2 = None if kappa2 is None else torch.as_tensor(kappa2, dtype=torch.float64, device=dev).contiguous()
             st = stream if stream is not None else torch.cuda.current_stream()
@@ -244,10 +264,10 @@ class Scan:
             self._cb = (_ALLOC_FN(_alloc), _FREE_FN(_free))
             p.alloc_fn, p.free_fn = self._cb
         else:
-            beta = _np.ascontiguousarray(beta, dtype=_np.float64)
+            beta = None if beta is None else _np.ascontiguousarray(beta, dtype=_np.float64)
             kappa1 = None if kappa1 is None else _np.ascontiguousarray(kappa1, dtype=_np.float64)
             kappa2 = None if kappa2 is None else _np.ascontiguousarray(kappa2, dtype=_np.float64)
-        self.n = int(beta.shape[0])
+        self.n = int(beta.shape[0]) if beta is not None else int(n)
         p.n = self.n
         p.beta_m, p.kappa1, p.kappa2 = _ptr(beta), _ptr(kappa1), _ptr(kappa2)
         for k, v in opts.items():
@@ -327,3 +347,118 @@ class Scan:
 
     def fp64_peak(self, iters=200_000):
         return scan_fp64_peak(self.h, iters)
+
+
+# ----------------------------------------------------- surrogate (mlp_*)
+MLP_PARAMS = 4545
+MLP_BATCH = 128
+
+
+class Surrogate:
+    """Ensemble of small networks mapping (x0, theta, beta, chi) to the FLI
+    (mlp_* of the C ABI).  Arrays are torch CUDA tensors (float32)."""
+
+    def __init__(self, members=5, seed=1, center=(30.0, 1.5707963267948966, 0.5, 0.5),
+                 scale=(20.0, 1.5707963267948966, 0.5, 0.5), stream=None):
+        import torch
+        self._torch = torch
+        self.members = int(members)
+        c = (_ct.c_float * 4)(*center)
+        sc = (_ct.c_float * 4)(*scale)
+        st = (stream or torch.cuda.current_stream()).cuda_stream
+        self.h = _ct.c_void_p()
+        _check(lib().mlp_create(self.members, int(seed), c, sc, st, _ct.byref(self.h)), "mlp_create")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _f32(self, a, shape=None):
+        t = self._torch.as_tensor(a, dtype=self._torch.float32, device="cuda").contiguous()
+        if shape is not None:
+            assert tuple(t.shape) == tuple(shape), (t.shape, shape)
+        return t
+
+    def get_params(self):
+        out = self._torch.empty((self.members, MLP_PARAMS), dtype=self._torch.float32, device="cuda")
+        _check(lib().mlp_get_params(self.h, _ptr(out)), "mlp_get_params")
+        return out
+
+    def set_params(self, params):
+        p = self._f32(params, (self.members, MLP_PARAMS))
+        _check(lib().mlp_set_params(self.h, _ptr(p)), "mlp_set_params")
+
+    def train(self, X, y, steps, lr=1e-3, seed=7, record_loss=True):
+        X = self._f32(X)
+        y = self._f32(y)
+        n = int(X.shape[0])
+        hist = self._torch.empty((self.members, steps), dtype=self._torch.float32,
+                                 device="cuda") if record_loss else None
+        _check(lib().mlp_train(self.h, _ptr(X), _ptr(y), n, int(steps), float(lr), int(seed), _ptr(hist)),
+               "mlp_train")
+        return hist
+
+    def gradient(self, X, y):
+        X = self._f32(X, (MLP_BATCH, 4))
+        y = self._f32(y, (MLP_BATCH,))
+        g = self._torch.empty((self.members, MLP_PARAMS), dtype=self._torch.float32, device="cuda")
+        loss = self._torch.empty(self.members, dtype=self._torch.float32, device="cuda")
+        _check(lib().mlp_gradient(self.h, _ptr(X), _ptr(y), _ptr(g), _ptr(loss)), "mlp_gradient")
+        return g, loss
+
+    def predict(self, X):
+        X = self._f32(X)
+        n = int(X.shape[0])
+        mean = self._torch.empty(n, dtype=self._torch.float32, device="cuda")
+        spread = self._torch.empty(n, dtype=self._torch.float32, device="cuda")
+        _check(lib().mlp_predict(self.h, _ptr(X), n, _ptr(mean), _ptr(spread)), "mlp_predict")
+        return mean, spread
+
+
+def adaptive_features(cells, stream=None):
+    """Surrogate inputs (x0, theta1, beta, chi1) as float32 of cells (n x 9 float64, CUDA)."""
+    import torch
+    cells = cells.contiguous()
+    n = int(cells.shape[0])
+    X = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(lib().adaptive_features(_ptr(cells), n, _ptr(X), st), "adaptive_features")
+    return X
+
+
+def adaptive_select(mean, spread, thr=6.0, band=1.0, spread_max=0.5, cells=None, stream=None):
+    """Indices (ascending, int32) of the cells to integrate, and their gathered
+    scan parameters (n x 9 float64) when cells is given.  Torch CUDA tensors."""
+    import torch
+    n = int(mean.shape[0])
+    ws = torch.empty(max(1, int(lib().adaptive_select_workspace(n))), dtype=torch.uint8, device="cuda")
+    idx = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    cells_out = None
+    if cells is not None:
+        cells = cells.contiguous()
+        cells_out = torch.empty((max(n, 1), 9), dtype=torch.float64, device="cuda")
+    count = _ct.c_int64()
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(lib().adaptive_select(_ptr(mean), _ptr(spread), n, float(thr), float(band), float(spread_max),
+                                 _ptr(cells), _ptr(idx), _ptr(cells_out), _ct.byref(count), _ptr(ws), st),
+           "adaptive_select")
+    k = count.value
+    return idx[:k], (None if cells_out is None else cells_out[:k])
+
+
+def adaptive_merge(mean, thr, idx, fli_sel, status_sel, stream=None):
+    """Class map (int8, 1 chaotic) of all cells: integrator results on idx, surrogate elsewhere."""
+    import torch
+    n = int(mean.shape[0])
+    cls = torch.empty(n, dtype=torch.int8, device="cuda")
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(lib().adaptive_merge(_ptr(mean), n, float(thr), _ptr(idx), int(idx.shape[0]), _ptr(fli_sel),
+                                _ptr(status_sel), _ptr(cls), st), "adaptive_merge")
+    return cls

@@ -1,0 +1,98 @@
+"""Surrogate-adaptive phase-space scan: a driver over the library's C ABI.
+
+The map of a scan grid (chaotic or not, FLI > thr) is produced in five steps,
+each a call into libpnscan:
+
+1. ``adaptive_features``: the surrogate's inputs (x0, theta1, beta, chi1).
+2. ``Surrogate.predict``: ensemble mean and spread of the FLI.
+3. ``adaptive_select``: cells with |mean - thr| <= band or spread > spread_max
+   (ordered compaction, their scan parameters gathered).
+4. ``Scan``: the full FP64 integrator on the selected cells only.
+5. ``adaptive_merge``: integrator result on the selected cells, surrogate
+   class elsewhere.
+
+The surrogate is trained (``Surrogate.train``) on FLI values the integrator
+itself produced for other scans.  PyTorch provides device memory and the
+stream only.
+"""
+import time
+
+import numpy as np
+
+from . import Scan, Surrogate, adaptive_features, adaptive_merge, adaptive_select, ORBIT_DONE, \
+    ORBIT_FLI_SATURATED, ORBIT_NONFINITE
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def integrate_cells(cells_d, t_end, h=1.0, **opts):
+    """Integrate every cell of cells_d (n x >= 9 float64, CUDA) to t_end with the
+    scan integrator; returns the device outputs of scan_read."""
+    torch = _torch()
+    cells9 = cells_d[:, :9].contiguous()
+    n = int(cells9.shape[0])
+    if n == 0:
+        e = torch.empty(0, device="cuda")
+        return dict(fli=e.double(), status=e.int(), states=torch.empty((0, 12), device="cuda").double())
+    with Scan(None, device=True, n=n, **opts) as s:
+        s.setup(cells9)
+        s.run(t_end, h)
+        return s.read()
+
+
+def classes(fli, status, thr):
+    """1 where the orbit reached t_end (or saturated) with FLI > thr."""
+    torch = _torch()
+    ok = (status == ORBIT_DONE) | (status == ORBIT_FLI_SATURATED)
+    return (ok & (fli > thr)).to(torch.int8)
+
+
+def training_set(cell_sets, t_ends, h=1.0):
+    """Surrogate training data from integrator runs: X (m x 4 float32) and the
+    FLI (m float32) of every cell that did not become non-finite."""
+    torch = _torch()
+    Xs, ys = [], []
+    for cells, t_end in zip(cell_sets, t_ends):
+        cd = torch.as_tensor(np.ascontiguousarray(cells[:, :9]), device="cuda")
+        out = integrate_cells(cd, t_end, h)
+        keep = out["status"] != ORBIT_NONFINITE
+        Xs.append(adaptive_features(cd)[keep])
+        ys.append(out["fli"][keep].float())
+    return torch.cat(Xs), torch.cat(ys)
+
+
+def train_surrogate(X, y, members=5, steps=4000, lr=3e-3, seed=1):
+    sur = Surrogate(members=members, seed=seed)
+    hist = sur.train(X, y, steps=steps, lr=lr, seed=seed + 100)
+    return sur, hist
+
+
+def adaptive_map(sur, cells_d, t_end, h=1.0, thr=6.0, band=1.0, spread_max=0.5):
+    """Class map of the grid cells_d (n x 9 float64, CUDA) and its cost."""
+    torch = _torch()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X = adaptive_features(cells_d)
+    mean, spread = sur.predict(X)
+    idx, sel = adaptive_select(mean, spread, thr, band, spread_max, cells=cells_d)
+    t1 = time.perf_counter()
+    out = integrate_cells(sel, t_end, h)
+    cls = adaptive_merge(mean, thr, idx, out["fli"], out["status"])
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return dict(cls=cls, mean=mean, spread=spread, idx=idx, fli_sel=out["fli"], status_sel=out["status"],
+                n_marked=int(idx.shape[0]), seconds=t2 - t0, seconds_surrogate=t1 - t0)
+
+
+def full_map(cells_d, t_end, h=1.0, thr=6.0):
+    """Class map from integrating every cell, and its cost."""
+    torch = _torch()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = integrate_cells(cells_d, t_end, h)
+    cls = classes(out["fli"], out["status"], thr)
+    torch.cuda.synchronize()
+    return dict(cls=cls, fli=out["fli"], status=out["status"], seconds=time.perf_counter() - t0)

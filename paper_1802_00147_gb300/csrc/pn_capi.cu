@@ -31,6 +31,7 @@ struct scan_handle {
     Summary* dsum = nullptr;
     double* staging = nullptr;         // n x 12 device staging for host I/O
     bool loaded = false;
+    bool beta_from_cells = false;      // beta_m was NULL: scan_setup takes beta from the cells
     double t_now = 0.0;
     int32_t nstep_now = 0;
     RunCfg base{};
@@ -250,7 +251,6 @@ int scan_create(const scan_params* p, scan_handle** out)
     if (!out) return PNSCAN_ERR_ARG;
     *out = nullptr;
     if (!p || p->n < 0 || p->n > (int64_t)1 << 31) return PNSCAN_ERR_ARG;
-    if (p->n > 0 && !p->beta_m) return PNSCAN_ERR_ARG;
     if (p->pn_order < 0 || p->pn_order > 2) return PNSCAN_ERR_ARG;
     if (!(p->newton_tol > 0.0) || p->newton_max < 1 || p->newton_max > 1000 || !(p->newton_det_min >= 0.0))
         return PNSCAN_ERR_ARG;
@@ -266,7 +266,7 @@ int scan_create(const scan_params* p, scan_handle** out)
     }
     // beta must lie in (0, 1] (m1 <= m2, Sec. 2)
     const int64_t n = p->n;
-    if (!p->device_ptrs && n > 0) {
+    if (!p->device_ptrs && n > 0 && p->beta_m) {
         for (int64_t i = 0; i < n; i++)
             if (!(p->beta_m[i] > 0.0 && p->beta_m[i] <= 1.0)) return PNSCAN_ERR_ARG;
     }
@@ -274,6 +274,7 @@ int scan_create(const scan_params* p, scan_handle** out)
     scan_handle* h = new (std::nothrow) scan_handle();
     if (!h) return PNSCAN_ERR_OOM;
     h->p = *p;
+    h->beta_from_cells = p->beta_m == nullptr;
     h->p.beta_m = h->p.kappa1 = h->p.kappa2 = nullptr;
     h->stream = (cudaStream_t)p->cuda_stream;
     cudaGetDevice(&h->device);
@@ -310,7 +311,7 @@ int scan_create(const scan_params* p, scan_handle** out)
     // per-orbit physical parameters
     if (n > 0) {
         const cudaMemcpyKind kind = p->device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-        if (cudaMemcpyAsync(h->S.beta, p->beta_m, sizeof(double) * n, kind, h->stream) != cudaSuccess)
+        if (p->beta_m && cudaMemcpyAsync(h->S.beta, p->beta_m, sizeof(double) * n, kind, h->stream) != cudaSuccess)
             return fail(PNSCAN_ERR_CUDA);
         for (int k = 0; k < 2; k++) {
             const double* src = k == 0 ? p->kappa1 : p->kappa2;
@@ -358,7 +359,7 @@ int scan_setup(scan_handle* h, const double* cells)
     if (h->S.n > 0) {
         r = stage_in(h, cells, (size_t)h->S.n * 9, &d);
         if (r != PNSCAN_OK) return r;
-        r = cuda_err(launch_setup_cells(d, h->S.n, h->S, h->stream));
+        r = cuda_err(launch_setup_cells(d, h->S.n, h->S, h->beta_from_cells ? 1 : 0, h->stream));
         if (r != PNSCAN_OK) return r;
     }
     return begin_state(h);
@@ -369,6 +370,7 @@ int scan_run(scan_handle* h, const double* initial_states, double t_end, double 
     if (!h || !(h_step > 0.0) || !std::isfinite(t_end)) return PNSCAN_ERR_ARG;
     int r = PNSCAN_OK;
     if (initial_states) {
+        if (h->beta_from_cells) return PNSCAN_ERR_STATE;   // beta comes only with scan_setup's cells
         if (h->S.n > 0) {
             const double* d = nullptr;
             r = stage_in(h, initial_states, (size_t)h->S.n * 12, &d);

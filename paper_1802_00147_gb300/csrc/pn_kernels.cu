@@ -156,12 +156,13 @@ __device__ __forceinline__ void advance(const RunCfg& rc, const Coef& c, Orbit& 
 // Initial conditions of a scan cell (x0, pfac, theta1, phi1, theta2, phi2,
 // beta, chi1, chi2): r = (x0, 0, 0), p = (0, pfac / sqrt(x0), 0),
 // S_i = chi_i m_i^2 (sin th_i cos ph_i, sin th_i sin ph_i, cos th_i).
-__global__ void k_setup_cells(const double* __restrict__ cells, int64_t n, DevState S)
+__global__ void k_setup_cells(const double* __restrict__ cells, int64_t n, DevState S, int beta_from_cells)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double* c = cells + 9 * i;
     const double x0 = c[0], beta = c[6];
+    if (beta_from_cells) S.beta[i] = beta;
     const double m1 = beta / (1.0 + beta), m2 = 1.0 / (1.0 + beta);
     const double s1 = c[7] * m1 * m1, s2 = c[8] * m2 * m2;
     double st1, ct1, sp1, cp1, st2, ct2, sp2, cp2;
@@ -451,10 +452,10 @@ __global__ void k_fp64_probe(double* out, int iters)
 // -------------------------------------------------------------- launchers
 static inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
-cudaError_t launch_setup_cells(const double* cells, int64_t n, DevState S, cudaStream_t st)
+cudaError_t launch_setup_cells(const double* cells, int64_t n, DevState S, int beta_from_cells, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    k_setup_cells<<<grid_for(n, 256), 256, 0, st>>>(cells, n, S);
+    k_setup_cells<<<grid_for(n, 256), 256, 0, st>>>(cells, n, S, beta_from_cells);
     return cudaGetLastError();
 }
 

@@ -78,7 +78,8 @@ struct Summary {                // scan-level reduction (device layout)
 };
 
 // ---- launchers (return cudaError_t of the launch) ----
-cudaError_t launch_setup_cells(const double* cells_aos, int64_t n, DevState S, cudaStream_t st);
+cudaError_t launch_setup_cells(const double* cells_aos, int64_t n, DevState S, int beta_from_cells,
+                               cudaStream_t st);
 cudaError_t launch_load_states(const double* states_aos, int64_t n, DevState S, cudaStream_t st);
 cudaError_t launch_init(DevState S, RunCfg rc, cudaStream_t st);
 cudaError_t launch_integrate_static(DevState S, RunCfg rc, int block, cudaStream_t st);

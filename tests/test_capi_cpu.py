@@ -66,8 +66,13 @@ def test_bad_arguments_are_rejected_before_any_device_work(pn):
     h = ctypes.c_void_p()
     assert L.scan_create(None, ctypes.byref(h)) == pn.ERR_ARG
     p = pn.scan_params_default()
-    p.n = 4                      # beta_m missing
+    p.n = 4
+    p.newton_tol = 0.0           # Newton tolerance must be positive
     assert L.scan_create(ctypes.byref(p), ctypes.byref(h)) == pn.ERR_ARG
+    p = pn.scan_params_default()
+    p.block_size = 96 + 256      # block size out of range
+    assert L.scan_create(ctypes.byref(p), ctypes.byref(h)) == pn.ERR_ARG
+    p = pn.scan_params_default()
     p.n = -1
     assert L.scan_create(ctypes.byref(p), ctypes.byref(h)) == pn.ERR_ARG
     p.n = 0

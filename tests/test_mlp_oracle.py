@@ -1,0 +1,75 @@
+"""Pins of the FP64 MLP oracle (no GPU): backprop against central finite
+differences, Adam's closed-form first step, ensemble statistics, and that
+training lowers the loss on a smooth target."""
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as M
+
+
+def rand_params(rng, scale=0.5):
+    return rng.normal(size=M.N_PARAMS) * scale
+
+
+def test_layout():
+    assert M.N_PARAMS == 4 * 64 + 64 + 64 * 64 + 64 + 64 + 1
+    p = np.arange(M.N_PARAMS, dtype=float)
+    assert np.array_equal(M.pack(*M.unpack(p)), p)
+
+
+def test_backprop_matches_central_differences():
+    rng = np.random.default_rng(1)
+    p = rand_params(rng, 0.3)
+    z = rng.uniform(-1, 1, size=(16, 4))
+    t = rng.normal(size=16)
+    loss, g = M.loss_and_grad(p, z, t)
+    idx = rng.choice(M.N_PARAMS, 300, replace=False)
+    idx = np.concatenate([idx, [M.OFF_B3, M.OFF_W1, M.OFF_B1, M.OFF_W2 + 5, M.OFF_B2 + 7, M.OFF_W3 + 3]])
+    for i in idx:
+        e = np.zeros(M.N_PARAMS)
+        e[i] = 1e-6
+        fd = (M.loss_and_grad(p + e, z, t)[0] - M.loss_and_grad(p - e, z, t)[0]) / 2e-6
+        assert abs(fd - g[i]) <= 1e-7 * max(1.0, abs(g[i])), (i, fd, g[i])
+
+
+def test_output_bias_gradient_closed_form():
+    """With W2 = 0 and b2 = 0 the hidden layer is 0, y = b3 and
+    dL/db3 = 2 mean(y - t), dL/dw3 = 0."""
+    rng = np.random.default_rng(2)
+    W1, b1, W2, b2, w3, b3 = M.unpack(rand_params(rng))
+    p = M.pack(W1, b1, np.zeros_like(W2), np.zeros_like(b2), w3, 0.7)
+    z = rng.uniform(-1, 1, size=(32, 4))
+    t = rng.normal(size=32)
+    loss, g = M.loss_and_grad(p, z, t)
+    assert loss == pytest.approx(np.mean((0.7 - t) ** 2), rel=1e-14)
+    assert g[M.OFF_B3] == pytest.approx(2 * np.mean(0.7 - t), rel=1e-13)
+    assert np.all(g[M.OFF_W3:M.OFF_B3] == 0.0)
+
+
+def test_adam_first_step_moves_by_lr_sign():
+    rng = np.random.default_rng(3)
+    p = rand_params(rng)
+    g = rng.normal(size=M.N_PARAMS)
+    p1, m, v = M.adam_step(p, g, np.zeros_like(p), np.zeros_like(p), 1, 1e-3)
+    # bias-corrected first moments are g and g^2: the step is lr g / (|g| + eps)
+    np.testing.assert_allclose(p - p1, 1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+    np.testing.assert_allclose(m, 0.1 * g, rtol=1e-14)
+    np.testing.assert_allclose(v, 0.001 * g * g, rtol=1e-14)
+
+
+def test_ensemble_of_identical_members_has_zero_spread():
+    rng = np.random.default_rng(4)
+    p = rand_params(rng)
+    z = rng.uniform(-1, 1, size=(10, 4))
+    mean, spread = M.ensemble_predict(np.stack([p, p, p]), z)
+    np.testing.assert_allclose(mean, M.forward(p, z)[0], rtol=1e-15)
+    assert np.all(spread == 0.0)
+
+
+def test_training_lowers_the_loss():
+    rng = np.random.default_rng(5)
+    z = rng.uniform(-1, 1, size=(2000, 4))
+    t = np.sin(2 * z[:, 0]) + 0.5 * z[:, 1] * z[:, 2] + 2.0
+    p0 = rand_params(rng, 0.2)
+    p, losses = M.train(p0, z, t, 600, 128, 3e-3, rng)
+    assert losses[-50:].mean() < 0.05 * losses[:10].mean()
