@@ -184,6 +184,55 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------- adaptive scan
+ADAPTIVE_N = 1024
+ADAPTIVE_T_END = 1.0e4
+
+
+def run_adaptive(cells_full, cells_full_d, fli_full_d, thr=6.0, band=1.0, spread_max=0.5):
+    """Surrogate-adaptive 1024 x 1024 scan of the small-scan parameters vs
+    integrating every cell: time-to-map and misclassification."""
+    import torch
+    from paper_1802_00147_gb300 import adaptive as A
+    from paper_1802_00147_gb300 import workloads as W
+    import paper_1802_00147_gb300 as pn
+
+    t0 = time.perf_counter()
+    small = W.small_scan(seed=1)
+    Xs, ys = A.training_set([small], [ADAPTIVE_T_END])
+    Xf = pn.adaptive_features(cells_full_d)
+    X = torch.cat([Xs, Xf])
+    y = torch.cat([ys, fli_full_d.float()])
+    sur, hist = A.train_surrogate(X, y, members=5, steps=4000, lr=3e-3, seed=1)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+
+    grid = W.adaptive_grid(ADAPTIVE_N, seed=4)
+    grid_d = torch.as_tensor(np.ascontiguousarray(grid[:, :9]), device="cuda")
+    A.adaptive_map(sur, grid_d[:4096], ADAPTIVE_T_END, thr=thr, band=band, spread_max=spread_max)  # warm-up
+    full = A.full_map(grid_d, ADAPTIVE_T_END, thr=thr)
+    sub, sub_idx = W.subset(grid, 4096, seed=6)
+    sub_idx_d = torch.as_tensor(sub_idx, device="cuda")
+    out = {"grid": "%dx%d" % (ADAPTIVE_N, ADAPTIVE_N), "t_end": ADAPTIVE_T_END, "members": 5,
+           "train_steps": 4000, "train_rows": int(X.shape[0]), "train_s": train_s,
+           "train_loss_first_last": [float(hist[:, :20].mean()), float(hist[:, -200:].mean())],
+           "plain_s": full["seconds"]}
+    for name, th, bd, sp in [("thr6", thr, band, spread_max)]:
+        res = A.adaptive_map(sur, grid_d, ADAPTIVE_T_END, thr=th, band=bd, spread_max=sp)
+        truth = A.classes(full["fli"], full["status"], th)
+        mis_all = float((res["cls"] != truth).float().mean().item())
+        mis_sub = float((res["cls"][sub_idx_d] != truth[sub_idx_d]).float().mean().item())
+        out[name] = {"thr": th, "band": bd, "spread_max": sp, "marked": res["n_marked"],
+                     "marked_frac": res["n_marked"] / grid.shape[0], "adaptive_s": res["seconds"],
+                     "surrogate_s": res["seconds_surrogate"],
+                     "speedup": full["seconds"] / res["seconds"],
+                     "speedup_incl_training": full["seconds"] / (res["seconds"] + train_s),
+                     "misclassification_subset4096": mis_sub, "misclassification_all": mis_all,
+                     "chaotic_frac": float(truth.float().mean().item())}
+    sur.close()
+    return out
+
+
 # -------------------------------------------------------------------- ours
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -283,6 +332,11 @@ def run_ours(args, rank, world, local_rank):
     h2d = cells9.nbytes
     d2h = sum(a.nbytes for a in out.values())
 
+    adaptive = None
+    if args.adaptive and rank == 0:
+        fli_full = scan.read()["fli"]
+        adaptive = run_adaptive(cells_h, cells_d, fli_full)
+
     if rank != 0:
         return
     ms_kernel = float(np.mean(kern_ms))
@@ -306,6 +360,7 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": 5 * args.steps,
         "clocks": clk.summary(),
+        "adaptive": adaptive,
         "scan": {k: summ[k] for k in ("n_chaotic", "status_count", "max_dE", "max_dJ", "max_dJ_all",
                                       "n_final_fallback", "max_dS", "fli_mean", "newton_iters",
                                       "n_skip", "orbit_steps")},
@@ -323,6 +378,8 @@ def main():
     ap.add_argument("--orbits", type=int, default=0,
                     help="seeded subset of the 314x314 scan (0: all 98,596); profiling only")
     ap.add_argument("--t-end", type=float, default=T_END, help="integration time (profiling only)")
+    ap.add_argument("--no-adaptive", dest="adaptive", action="store_false",
+                    help="skip the surrogate-adaptive 1024x1024 scan measurement")
     ap.add_argument("--profile", action="store_true",
                     help="time the device path only (no autotune, e2e or CPU leg) for ncu runs")
     args = ap.parse_args()

@@ -97,8 +97,15 @@ typedef struct scan_params {
     int block_size;          /* threads per block, 32..128, multiple of 32 (0: 128) */
     int chunk_steps;         /* steps per work-queue task (0: 500) */
     int blocks_per_sm;       /* resident blocks per SM for the queue kernel (0: occupancy maximum) */
+    int register_variant;    /* queue kernel compiled for 2 (up to 255 registers/thread) or 3 (168)
+                                resident 128-thread blocks per SM (0: 2, or the autotuned choice) */
     int use_graph;           /* 1: capture the queue run in a CUDA graph and replay it (default 1) */
     double sync_timeout_s;   /* host watchdog for synchronising calls (default 0: wait forever) */
+    int queue_wait_limit_ms; /* bound on a work-queue task's wait for its predecessor; on expiry the
+                                kernel sets an error flag and returns, and the next synchronising
+                                call reports PNSCAN_ERR_KERNEL (default 20000) */
+    int debug_stall_group;   /* test hook, default -1 (off): group g never publishes its first
+                                chunk, so the wait of its second chunk runs out */
     void *(*alloc_fn)(size_t bytes, void *ctx);  /* optional device allocator (e.g. PyTorch's) */
     void (*free_fn)(void *ptr, void *ctx);
     void *alloc_ctx;
@@ -175,13 +182,13 @@ int scan_read_diag(scan_handle *h, double *shadow, int32_t *newton_iters, int32_
  * histogram (synchronises; *out is a host struct).  Errors: ARG, STATE, CUDA. */
 int scan_summary(scan_handle *h, scan_summary_t *out);
 
-/* Pick the integrator schedule, block size, chunk length and blocks per SM
- * by timing candidate launches on a copy of the handle's current state for
+/* Pick the integrator schedule, block size, chunk length, blocks per SM and
+ * register variant by timing candidate launches on a copy of the handle's current state for
  * `steps` steps (the state itself is left unchanged).  The choice is kept in
  * the handle and used by later scan_run calls with schedule AUTO; it is also
  * written to the optional outputs.  Errors: ARG, STATE, CUDA. */
 int scan_autotune(scan_handle *h, int steps, int *schedule, int *block_size, int *chunk_steps,
-                  int *blocks_per_sm);
+                  int *blocks_per_sm, int *register_variant);
 
 /* Device time of the integrator launches of the last scan_run (CUDA events
  * on the handle's stream; synchronises).  *ms and *launches may be NULL. */

@@ -49,7 +49,9 @@ class ScanParams(_ct.Structure):
         ("fli_cap", _ct.c_double), ("r_merge", _ct.c_double), ("r_escape", _ct.c_double),
         ("device_ptrs", _ct.c_int), ("cuda_stream", _ct.c_void_p),
         ("schedule", _ct.c_int), ("block_size", _ct.c_int), ("chunk_steps", _ct.c_int),
-        ("blocks_per_sm", _ct.c_int), ("use_graph", _ct.c_int), ("sync_timeout_s", _ct.c_double),
+        ("blocks_per_sm", _ct.c_int), ("register_variant", _ct.c_int), ("use_graph", _ct.c_int),
+        ("sync_timeout_s", _ct.c_double),
+        ("queue_wait_limit_ms", _ct.c_int), ("debug_stall_group", _ct.c_int),
         ("alloc_fn", _ALLOC_FN), ("free_fn", _FREE_FN), ("alloc_ctx", _ct.c_void_p),
     ]
 
@@ -94,7 +96,7 @@ def lib():
         L.scan_read.argtypes = [vp, vp, vp, vp, vp, vp]
         L.scan_read_diag.argtypes = [vp, vp, vp, vp, vp]
         L.scan_summary.argtypes = [vp, P(ScanSummary)]
-        L.scan_autotune.argtypes = [vp, i, P(i), P(i), P(i), P(i)]
+        L.scan_autotune.argtypes = [vp, i, P(i), P(i), P(i), P(i), P(i)]
         L.scan_last_run_timing.argtypes = [vp, P(d), P(i)]
         L.scan_fp64_peak.argtypes = [vp, i, P(d)]
         L.scan_summary_noalloc.argtypes = [_ct.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, d, d, vp,
@@ -182,10 +184,10 @@ def scan_summary(h):
 
 
 def scan_autotune(h, steps):
-    out = [_ct.c_int() for _ in range(4)]
+    out = [_ct.c_int() for _ in range(5)]
     _check(lib().scan_autotune(h, int(steps), *[_ct.byref(o) for o in out]), "scan_autotune")
     return dict(schedule=out[0].value, block_size=out[1].value, chunk_steps=out[2].value,
-                blocks_per_sm=out[3].value)
+                blocks_per_sm=out[3].value, register_variant=out[4].value)
 
 
 def scan_last_run_timing(h):

@@ -40,6 +40,7 @@ struct scan_handle {
     int block = 128;
     int chunk = 500;
     int bps = 0;
+    int minb = 2;                      // register-budget variant of the queue kernel
     bool tuned = false;
     // timing of the last run
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -48,7 +49,7 @@ struct scan_handle {
     // CUDA graph of the queue run
     cudaGraphExec_t gexec = nullptr;
     RunCfg gcfg{};
-    int gshape[4] = {0, 0, 0, 0};
+    int gshape[5] = {0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -163,22 +164,22 @@ int reset_queue(scan_handle* h, cudaStream_t st)
     return cuda_err(cudaMemsetAsync(h->queue_block, 0, h->queue_bytes, st));
 }
 
-int queue_grid(scan_handle* h, int block, int bps)
+int queue_grid(scan_handle* h, int block, int bps, int minb)
 {
-    int occ = queue_blocks_per_sm(block, h->base.flags.use_qm != 0);
+    int occ = queue_blocks_per_sm(block, h->base.flags.use_qm != 0, minb);
     if (occ <= 0) occ = 1;
     if (bps <= 0 || bps > occ) bps = occ;
     return h->num_sms * bps;
 }
 
 // Launch the integrator for one run on stream st (no timing).
-int launch_run(scan_handle* h, const RunCfg& rc, int sched, int block, int chunk, int bps,
+int launch_run(scan_handle* h, const RunCfg& rc, int sched, int block, int chunk, int bps, int minb,
                const DevState& S, cudaStream_t st)
 {
     if (sched == PNSCAN_SCHED_STATIC) return cuda_err(launch_integrate_static(S, rc, block, st));
     int r = reset_queue(h, st);
     if (r != PNSCAN_OK) return r;
-    return cuda_err(launch_integrate_queue(S, rc, h->q, block, queue_grid(h, block, bps), chunk, st));
+    return cuda_err(launch_integrate_queue(S, rc, h->q, block, queue_grid(h, block, bps, minb), chunk, minb, st));
 }
 
 bool same_run(const RunCfg& a, const RunCfg& b)
@@ -189,12 +190,12 @@ bool same_run(const RunCfg& a, const RunCfg& b)
            a.newton.det_min == b.newton.det_min && a.correct == b.correct && a.h == b.h &&
            a.d0 == b.d0 && a.renorm == b.renorm && a.fli_cap == b.fli_cap &&
            a.rmerge2 == b.rmerge2 && a.rescape2 == b.rescape2 && a.nstep_base == b.nstep_base &&
-           a.nsteps == b.nsteps;
+           a.nsteps == b.nsteps && a.wait_limit_ns == b.wait_limit_ns && a.stall_group == b.stall_group;
 }
 
 int run_graph(scan_handle* h, const RunCfg& rc)
 {
-    const int shape[4] = {h->sched, h->block, h->chunk, h->bps};
+    const int shape[5] = {h->sched, h->block, h->chunk, h->bps, h->minb};
     if (!h->gexec || !same_run(h->gcfg, rc) || std::memcmp(h->gshape, shape, sizeof(shape)) != 0) {
         if (h->gexec) {
             cudaGraphExecDestroy(h->gexec);
@@ -203,7 +204,7 @@ int run_graph(scan_handle* h, const RunCfg& rc)
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_err(e);
-        int r = launch_run(h, rc, h->sched, h->block, h->chunk, h->bps, h->S, h->cap_stream);
+        int r = launch_run(h, rc, h->sched, h->block, h->chunk, h->bps, h->minb, h->S, h->cap_stream);
         e = cudaStreamEndCapture(h->cap_stream, &g);
         if (r != PNSCAN_OK) {
             if (g) cudaGraphDestroy(g);
@@ -243,6 +244,8 @@ int scan_params_default(scan_params* p)
     p->r_escape = 1e3;
     p->schedule = PNSCAN_SCHED_AUTO;
     p->use_graph = 1;
+    p->queue_wait_limit_ms = 20000;
+    p->debug_stall_group = -1;
     return PNSCAN_OK;
 }
 
@@ -256,7 +259,8 @@ int scan_create(const scan_params* p, scan_handle** out)
         return PNSCAN_ERR_ARG;
     if (!(p->fli_d0 > 0.0)) return PNSCAN_ERR_ARG;
     if (p->block_size && (p->block_size < 32 || p->block_size > 128 || p->block_size % 32)) return PNSCAN_ERR_ARG;
-    if (p->chunk_steps < 0 || p->blocks_per_sm < 0) return PNSCAN_ERR_ARG;
+    if (p->chunk_steps < 0 || p->blocks_per_sm < 0 || p->queue_wait_limit_ms < 0) return PNSCAN_ERR_ARG;
+    if (p->register_variant != 0 && p->register_variant != 2 && p->register_variant != 3) return PNSCAN_ERR_ARG;
     if (p->schedule < 0 || p->schedule > 2) return PNSCAN_ERR_ARG;
     if ((p->alloc_fn == nullptr) != (p->free_fn == nullptr)) return PNSCAN_ERR_ARG;
     int ndev = 0;
@@ -342,10 +346,13 @@ int scan_create(const scan_params* p, scan_handle** out)
     b.fli_cap = p->fli_cap;
     b.rmerge2 = p->r_merge > 0.0 ? p->r_merge * p->r_merge : 0.0;
     b.rescape2 = p->r_escape > 0.0 ? p->r_escape * p->r_escape : 0.0;
+    b.wait_limit_ns = (unsigned long long)(p->queue_wait_limit_ms > 0 ? p->queue_wait_limit_ms : 20000) * 1000000ull;
+    b.stall_group = p->debug_stall_group;
     h->sched = p->schedule == PNSCAN_SCHED_STATIC ? PNSCAN_SCHED_STATIC : PNSCAN_SCHED_QUEUE;
     h->block = p->block_size ? p->block_size : 128;
     h->chunk = p->chunk_steps ? p->chunk_steps : 500;
     h->bps = p->blocks_per_sm;
+    h->minb = p->register_variant == 3 ? 3 : 2;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(PNSCAN_ERR_CUDA);
     *out = h;
     return PNSCAN_OK;
@@ -393,7 +400,7 @@ int scan_run(scan_handle* h, const double* initial_states, double t_end, double 
         const RunCfg rc = make_run(h, h_step, nsteps);
         if (cudaEventRecord(h->ev0, h->stream) != cudaSuccess) return PNSCAN_ERR_CUDA;
         if (h->sched == PNSCAN_SCHED_QUEUE && h->p.use_graph) r = run_graph(h, rc);
-        else r = launch_run(h, rc, h->sched, h->block, h->chunk, h->bps, h->S, h->stream);
+        else r = launch_run(h, rc, h->sched, h->block, h->chunk, h->bps, h->minb, h->S, h->stream);
         if (r != PNSCAN_OK) return r;
         if (cudaEventRecord(h->ev1, h->stream) != cudaSuccess) return PNSCAN_ERR_CUDA;
         h->timed = true;
@@ -497,7 +504,8 @@ int scan_summary(scan_handle* h, scan_summary_t* out)
     return PNSCAN_OK;
 }
 
-int scan_autotune(scan_handle* h, int steps, int* schedule, int* block_size, int* chunk_steps, int* blocks_per_sm)
+int scan_autotune(scan_handle* h, int steps, int* schedule, int* block_size, int* chunk_steps, int* blocks_per_sm,
+                  int* register_variant)
 {
     if (!h || steps <= 0) return PNSCAN_ERR_ARG;
     if (!h->loaded) return PNSCAN_ERR_STATE;
@@ -509,15 +517,15 @@ int scan_autotune(scan_handle* h, int steps, int* schedule, int* block_size, int
         void* blk = dev_alloc(h, bytes);
         if (!blk) return PNSCAN_ERR_OOM;
         layout_state(T, (char*)blk, h->S.n);
-        struct Cand { int sched, block, chunk, bps; };
+        struct Cand { int sched, block, chunk, bps, minb; };
         std::vector<Cand> cands;
-        for (int blk_sz : {64, 128}) cands.push_back({PNSCAN_SCHED_STATIC, blk_sz, 0, 0});
-        const int occ128 = queue_blocks_per_sm(128, h->base.flags.use_qm != 0);
-        for (int blk_sz : {64, 128})
+        for (int blk_sz : {64, 128}) cands.push_back({PNSCAN_SCHED_STATIC, blk_sz, 0, 0, 2});
+        for (int minb : {2, 3})
             for (int ch : {steps / 16, steps / 8, steps / 4}) {
                 if (ch < 1) continue;
-                cands.push_back({PNSCAN_SCHED_QUEUE, blk_sz, ch, 0});
-                if (blk_sz == 128 && occ128 > 1) cands.push_back({PNSCAN_SCHED_QUEUE, blk_sz, ch, 1});
+                cands.push_back({PNSCAN_SCHED_QUEUE, 128, ch, 0, minb});
+                if (minb == 2) cands.push_back({PNSCAN_SCHED_QUEUE, 128, ch, 1, minb});
+                if (minb == 3) cands.push_back({PNSCAN_SCHED_QUEUE, 64, ch, 0, minb});
             }
         double best = 1e300;
         Cand bestc = cands[0];
@@ -531,7 +539,7 @@ int scan_autotune(scan_handle* h, int steps, int* schedule, int* block_size, int
                 break;
             }
             cudaEventRecord(e0, h->stream);
-            r = launch_run(h, rc, c.sched, c.block, c.chunk, c.bps, T, h->stream);
+            r = launch_run(h, rc, c.sched, c.block, c.chunk, c.bps, c.minb, T, h->stream);
             cudaEventRecord(e1, h->stream);
             if (r != PNSCAN_OK) break;
             r = sync(h);
@@ -553,12 +561,14 @@ int scan_autotune(scan_handle* h, int steps, int* schedule, int* block_size, int
         // of chunks per run length as a lower bound on the task count
         h->chunk = bestc.sched == PNSCAN_SCHED_QUEUE ? bestc.chunk : h->chunk;
         h->bps = bestc.bps;
+        h->minb = bestc.minb;
         h->tuned = true;
     }
     if (schedule) *schedule = h->sched;
     if (block_size) *block_size = h->block;
     if (chunk_steps) *chunk_steps = h->chunk;
     if (blocks_per_sm) *blocks_per_sm = h->bps;
+    if (register_variant) *register_variant = h->minb;
     return PNSCAN_OK;
 }
 

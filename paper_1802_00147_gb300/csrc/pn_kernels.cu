@@ -241,8 +241,8 @@ __global__ void __launch_bounds__(128) k_integrate_static(DevState S, RunCfg rc)
 // earlier by a running warp, so the oldest unfinished task can always make
 // progress.  Because every group advances chunk by chunk, all SM
 // sub-partitions stay busy until the last chunk, whatever the number of
-// orbits.  Every wait is bounded in time; on expiry the kernel sets the error
-// flag and all warps return.
+// orbits.  Every wait is bounded in time (rc.wait_limit_ns, global timer);
+// on expiry the kernel sets the error flag and all warps return.
 __device__ __forceinline__ int ld_acquire(const int* p)
 {
     int v;
@@ -262,10 +262,8 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
     return t;
 }
 
-constexpr unsigned long long kQueueWaitLimitNs = 20ull * 1000ull * 1000ull * 1000ull;  // 20 s
-
-template <bool QM>
-__global__ void __launch_bounds__(128) k_integrate_queue(DevState S, RunCfg rc, QueueState q, int chunk)
+template <bool QM, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_integrate_queue(DevState S, RunCfg rc, QueueState q, int chunk)
 {
     const int lane = threadIdx.x & 31;
     const long long groups = (S.n + 31) / 32;
@@ -283,7 +281,7 @@ __global__ void __launch_bounds__(128) k_integrate_queue(DevState S, RunCfg rc, 
         if (c > 0 && lane == 0) {
             const unsigned long long t0 = globaltimer_ns();
             while (ld_acquire(q.group_done + g) < c) {
-                if (globaltimer_ns() - t0 > kQueueWaitLimitNs) {
+                if (globaltimer_ns() - t0 > rc.wait_limit_ns) {
                     atomicExch(q.error, 1);
                     ok = 0;
                     break;
@@ -310,7 +308,7 @@ __global__ void __launch_bounds__(128) k_integrate_queue(DevState S, RunCfg rc, 
         }
         __threadfence();
         __syncwarp();
-        if (lane == 0) st_release(q.group_done + g, (int)(c + 1));
+        if (lane == 0 && !(c == 0 && g == rc.stall_group)) st_release(q.group_done + g, (int)(c + 1));
     }
 }
 
@@ -483,21 +481,34 @@ cudaError_t launch_integrate_static(DevState S, RunCfg rc, int block, cudaStream
     return cudaGetLastError();
 }
 
-int queue_blocks_per_sm(int block, bool qm)
+template <int MINB>
+static int occupancy_queue(int block, bool qm)
 {
     int nb = 0;
-    if (qm) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<true>, block, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<false>, block, 0);
+    if (qm) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<true, MINB>, block, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<false, MINB>, block, 0);
     return nb;
 }
 
+int queue_blocks_per_sm(int block, bool qm, int minb)
+{
+    return minb == 3 ? occupancy_queue<3>(block, qm) : occupancy_queue<2>(block, qm);
+}
+
+template <int MINB>
+static void launch_queue(DevState S, RunCfg rc, QueueState q, int block, int grid, int chunk, cudaStream_t st)
+{
+    if (rc.flags.use_qm) k_integrate_queue<true, MINB><<<grid, block, 0, st>>>(S, rc, q, chunk);
+    else k_integrate_queue<false, MINB><<<grid, block, 0, st>>>(S, rc, q, chunk);
+}
+
 cudaError_t launch_integrate_queue(DevState S, RunCfg rc, QueueState q, int block, int grid,
-                                   int chunk, cudaStream_t st)
+                                   int chunk, int minb, cudaStream_t st)
 {
     if (S.n == 0 || rc.nsteps <= 0) return cudaSuccess;
     if (block <= 0 || block > 128 || block % 32 || grid <= 0 || chunk <= 0) return cudaErrorInvalidValue;
-    if (rc.flags.use_qm) k_integrate_queue<true><<<grid, block, 0, st>>>(S, rc, q, chunk);
-    else k_integrate_queue<false><<<grid, block, 0, st>>>(S, rc, q, chunk);
+    if (minb == 3) launch_queue<3>(S, rc, q, block, grid, chunk, st);
+    else launch_queue<2>(S, rc, q, block, grid, chunk, st);
     return cudaGetLastError();
 }
 

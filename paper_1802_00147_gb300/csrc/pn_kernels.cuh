@@ -51,6 +51,8 @@ struct RunCfg {
     double rescape2;       // stop at |r|^2 > rescape2 (<= 0: never)
     int32_t nstep_base;    // nstep of every running orbit when the run started
     int32_t nsteps;        // steps in this run
+    unsigned long long wait_limit_ns;  // bound on a queue task's wait for its predecessor
+    int stall_group;       // test hook: this group never publishes chunk 0 (-1: off)
 };
 
 // Work-queue state of the persistent integrator (device memory, 256-byte
@@ -83,9 +85,11 @@ cudaError_t launch_setup_cells(const double* cells_aos, int64_t n, DevState S, i
 cudaError_t launch_load_states(const double* states_aos, int64_t n, DevState S, cudaStream_t st);
 cudaError_t launch_init(DevState S, RunCfg rc, cudaStream_t st);
 cudaError_t launch_integrate_static(DevState S, RunCfg rc, int block, cudaStream_t st);
-int queue_blocks_per_sm(int block, bool qm);
+// minb: register budget of the queue kernel, 2 (up to 255 registers per
+// thread) or 3 (168 registers) resident 128-thread blocks per SM
+int queue_blocks_per_sm(int block, bool qm, int minb);
 cudaError_t launch_integrate_queue(DevState S, RunCfg rc, QueueState q, int block, int grid,
-                                   int chunk, cudaStream_t st);
+                                   int chunk, int minb, cudaStream_t st);
 cudaError_t launch_finalize(DevState S, RunCfg rc, cudaStream_t st);
 cudaError_t launch_reduce(DevState S, double fli_thresh, Summary* out, cudaStream_t st);
 cudaError_t launch_gather(DevState S, double* states_aos, double* shadow_aos, double* integ_aos,

@@ -211,7 +211,8 @@ def test_schedules_chunks_and_pointers_are_bit_identical(pn):
     b = gpu_run(pn, cells, 300, schedule=2, chunk_steps=64)
     c = gpu_run(pn, cells, 300, schedule=2, chunk_steps=100, chunks=3)    # 3 scan_run calls
     d = gpu_run(pn, cells, 300, schedule=2, device=True, use_graph=0)
-    for other in (b, c, d):
+    e = gpu_run(pn, cells, 300, schedule=2, chunk_steps=75, register_variant=3, block_size=64)
+    for other in (b, c, d, e):
         for k in ("states", "fli", "status", "t_stop", "integrals"):
             np.testing.assert_array_equal(a[k], other[k], err_msg=k)
 
@@ -268,6 +269,28 @@ def test_single_orbit_and_nonfinite_input(pn):
     assert list(out["status"]) == [pn.ORBIT_DONE, pn.ORBIT_NONFINITE, pn.ORBIT_DONE]
     assert o["status"][1] == oracle.NONFINITE
     np.testing.assert_allclose(out["states"][[0, 2]], o["y"][[0, 2]], rtol=1e-12)
+
+
+def test_bounded_queue_wait_reports_an_error_and_the_device_stays_usable(pn):
+    """A work-queue task whose predecessor never reports (test hook: group 0
+    withholds its first chunk) waits at most queue_wait_limit_ms, sets the
+    kernel's error flag and returns; the host reads PNSCAN_ERR_KERNEL and the
+    next run on the same handle works."""
+    import time
+    cells = W.uneven_batch(n=4096, seed=14)
+    s = pn.Scan(cells[:, W.BETA], schedule=2, chunk_steps=50, use_graph=0, queue_wait_limit_ms=300,
+                debug_stall_group=0)
+    s.setup(cells)
+    t0 = time.perf_counter()
+    s.run(150.0, 1.0)
+    with pytest.raises(pn.ScanError) as err:
+        s.read()
+    assert err.value.code == pn.ERR_KERNEL
+    assert time.perf_counter() - t0 < 30.0
+    s.close()
+    ok = gpu_run(pn, cells[:256], 150, schedule=2, chunk_steps=50)
+    ref = gpu_run(pn, cells[:256], 150, schedule=1)
+    np.testing.assert_array_equal(ok["states"], ref["states"])
 
 
 def test_bad_calls_are_rejected(pn):
