@@ -33,11 +33,12 @@ H_STEP = 1.0
 
 # Algorithmic FP64 flops of the kernel's formulation (fma = 2, add/sub/mul = 1,
 # sqrt/rsqrt/reciprocal/division/log10 = 1 each), per trajectory-step:
-#   4 x 226 (RHS) + 171 (RK4 stages) + 138 (correction: spin lengths, Newton
-#   monomial set-up, scaling) = 1213, plus 73 per Newton iteration; per
-#   orbit-step two trajectories, 5 for the termination test and 1.75 for the
-#   FLI renormalisation amortised over 100 steps.
-FLOPS_PER_TRAJ_STEP = 4 * 226 + 171 + 138
+#   4 x 219 (RHS) + 171 (RK4 stages) + 138 (correction: spin lengths, Newton
+#   monomial set-up, scaling) + 43 (first Newton iteration, at alpha = beta = 1)
+#   = 1228, plus 73 per further Newton iteration; per orbit-step two
+#   trajectories, 5 for the termination test and 1.75 for the FLI
+#   renormalisation amortised over 100 steps.
+FLOPS_PER_TRAJ_STEP = 4 * 219 + 171 + 138 + 43
 FLOPS_PER_NEWTON_ITER = 73
 FLOPS_PER_ORBIT_STEP_EXTRA = 5 + 1.75
 # Nominal FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz.
@@ -45,8 +46,9 @@ FP64_PEAK_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def algorithmic_flops(orbit_steps, newton_iters):
+    further = max(0, newton_iters - 2 * orbit_steps)     # iterations beyond each correction's first
     return (orbit_steps * (2 * FLOPS_PER_TRAJ_STEP + FLOPS_PER_ORBIT_STEP_EXTRA)
-            + newton_iters * FLOPS_PER_NEWTON_ITER)
+            + further * FLOPS_PER_NEWTON_ITER)
 
 
 def workload(rank=0, orbits=0):

@@ -34,15 +34,31 @@ struct Vec12 {
 // (Eqs. 8-9); H_S1S2 = ieta u^3 [3 (S1.n)(S2.n) - S1.S2] (Eq. 3 with the 1/eta
 // of Eqs. 8-9); H_QM = u^3 [q1 (3 (S1.n)^2 - S1^2) + q2 (3 (S2.n)^2 - S2^2)],
 // q1 = kappa1/(2 beta eta), q2 = kappa2 beta/(2 eta) (Eqs. 4-5).
-struct Coef {
+enum CoefIdx : int {
     // value of H (integrals, Newton monomials)
-    double a1, b1, b2, h1, a2, c1, c2, c3, d1, d2, e1;
-    double g1, g2, ieta, q1, q2;
+    K_A1, K_B1, K_B2, K_H1, K_A2, K_C1, K_C2, K_C3, K_D1, K_D2, K_E1,
+    K_G1, K_G2, K_IETA, K_Q1, K_Q2,
     // derivative polynomials, pre-multiplied
-    double a1x4, a2x6, c1x4, c2x2, d1x2;        // 2 dH/dp2
-    double b2x2, c2x2b, c3x4, d2x2;             // W = H_np / np
-    double h1x2, d1x2u, d2x2u, e1x3;            // dH/du
-    double ieta3, q1x6, q2x6, q1x15, q2x15, ieta15, q1x3, q2x3;
+    K_A1X4, K_A2X6, K_C1X4, K_C2X2, K_D1X2, K_B1X2,   // 2 dH/dp2
+    K_B2X2, K_C3X4, K_D2X2,                          // W = H_np / np
+    K_H1X2, K_E1X3,                                  // dH/du
+    K_IETA3, K_IETA15, K_Q1X6, K_Q2X6, K_Q1X15, K_Q2X15, K_Q1X3, K_Q2X3,
+    NCOEF
+};
+
+// Per-orbit constants held in registers.
+struct Coef {
+    double v[NCOEF];
+    __host__ __device__ double operator[](int k) const { return v[k]; }
+};
+
+// Per-orbit constants held in shared memory, one plane per constant across
+// the block's threads (consecutive threads, consecutive doubles): read on
+// use, so they cost no registers between uses.
+struct CoefShared {
+    const volatile double* p;   // &plane[0][threadIdx.x]
+    int stride;                 // threads per block
+    __device__ double operator[](int k) const { return p[k * stride]; }
 };
 
 struct Flags {
@@ -53,50 +69,49 @@ struct Flags {
 __host__ __device__ inline Coef make_coef(double beta, double kappa1, double kappa2, Flags f)
 {
     Coef c;
+    double* v = c.v;
     const double eta = beta / ((1.0 + beta) * (1.0 + beta));
     const double pn1 = f.pn_order >= 1 ? 1.0 : 0.0;
     const double pn2 = f.pn_order >= 2 ? 1.0 : 0.0;
-    c.a1 = pn1 * (3.0 * eta - 1.0) / 8.0;
-    c.b1 = pn1 * -(3.0 + eta) / 2.0;
-    c.b2 = pn1 * -eta / 2.0;
-    c.h1 = pn1 * 0.5;
-    c.a2 = pn2 * (1.0 - 5.0 * eta + 5.0 * eta * eta) / 16.0;
-    c.c1 = pn2 * (5.0 - 20.0 * eta - 3.0 * eta * eta) / 8.0;
-    c.c2 = pn2 * -(eta * eta) / 4.0;
-    c.c3 = pn2 * -3.0 * eta * eta / 8.0;
-    c.d1 = pn2 * (5.0 + 8.0 * eta) / 2.0;
-    c.d2 = pn2 * 3.0 * eta / 2.0;
-    c.e1 = pn2 * -(1.0 + 3.0 * eta) / 4.0;
-    c.g1 = f.use_so ? 2.0 + 3.0 / (2.0 * beta) : 0.0;
-    c.g2 = f.use_so ? 2.0 + 1.5 * beta : 0.0;
-    c.ieta = f.use_ss ? 1.0 / eta : 0.0;
-    c.q1 = f.use_qm ? kappa1 / (2.0 * beta * eta) : 0.0;
-    c.q2 = f.use_qm ? kappa2 * beta / (2.0 * eta) : 0.0;
+    v[K_A1] = pn1 * (3.0 * eta - 1.0) / 8.0;
+    v[K_B1] = pn1 * -(3.0 + eta) / 2.0;
+    v[K_B2] = pn1 * -eta / 2.0;
+    v[K_H1] = pn1 * 0.5;
+    v[K_A2] = pn2 * (1.0 - 5.0 * eta + 5.0 * eta * eta) / 16.0;
+    v[K_C1] = pn2 * (5.0 - 20.0 * eta - 3.0 * eta * eta) / 8.0;
+    v[K_C2] = pn2 * -(eta * eta) / 4.0;
+    v[K_C3] = pn2 * -3.0 * eta * eta / 8.0;
+    v[K_D1] = pn2 * (5.0 + 8.0 * eta) / 2.0;
+    v[K_D2] = pn2 * 3.0 * eta / 2.0;
+    v[K_E1] = pn2 * -(1.0 + 3.0 * eta) / 4.0;
+    v[K_G1] = f.use_so ? 2.0 + 3.0 / (2.0 * beta) : 0.0;
+    v[K_G2] = f.use_so ? 2.0 + 1.5 * beta : 0.0;
+    v[K_IETA] = f.use_ss ? 1.0 / eta : 0.0;
+    v[K_Q1] = f.use_qm ? kappa1 / (2.0 * beta * eta) : 0.0;
+    v[K_Q2] = f.use_qm ? kappa2 * beta / (2.0 * eta) : 0.0;
     // 2 dH/dp2 = 1 + 4 a1 p2 + 2 b1 u + 6 a2 p2^2 + u (4 c1 p2 + 2 c2 np^2) + 2 d1 u^2
-    c.a1x4 = 4.0 * c.a1;
-    c.a2x6 = 6.0 * c.a2;
-    c.c1x4 = 4.0 * c.c1;
-    c.c2x2 = 2.0 * c.c2;
-    c.d1x2 = 2.0 * c.d1;
+    v[K_A1X4] = 4.0 * v[K_A1];
+    v[K_A2X6] = 6.0 * v[K_A2];
+    v[K_C1X4] = 4.0 * v[K_C1];
+    v[K_C2X2] = 2.0 * v[K_C2];
+    v[K_D1X2] = 2.0 * v[K_D1];
+    v[K_B1X2] = 2.0 * v[K_B1];
     // W = H_np / np = u (2 b2 + 2 c2 p2 + 4 c3 np^2 + 2 d2 u)
-    c.b2x2 = 2.0 * c.b2;
-    c.c2x2b = 2.0 * c.c2;
-    c.c3x4 = 4.0 * c.c3;
-    c.d2x2 = 2.0 * c.d2;
+    v[K_B2X2] = 2.0 * v[K_B2];
+    v[K_C3X4] = 4.0 * v[K_C3];
+    v[K_D2X2] = 2.0 * v[K_D2];
     // dH/du = -1 + p2 (b1 + c1 p2 + c2 np^2) + np^2 (b2 + c3 np^2)
     //         + u (2 h1 + 2 d1 p2 + 2 d2 np^2 + 3 e1 u)
-    c.h1x2 = 2.0 * c.h1;
-    c.d1x2u = 2.0 * c.d1;
-    c.d2x2u = 2.0 * c.d2;
-    c.e1x3 = 3.0 * c.e1;
-    c.ieta3 = 3.0 * c.ieta;
-    c.q1x6 = 6.0 * c.q1;
-    c.q2x6 = 6.0 * c.q2;
-    c.q1x15 = 15.0 * c.q1;
-    c.q2x15 = 15.0 * c.q2;
-    c.ieta15 = 15.0 * c.ieta;
-    c.q1x3 = 3.0 * c.q1;
-    c.q2x3 = 3.0 * c.q2;
+    v[K_H1X2] = 2.0 * v[K_H1];
+    v[K_E1X3] = 3.0 * v[K_E1];
+    v[K_IETA3] = 3.0 * v[K_IETA];
+    v[K_IETA15] = 15.0 * v[K_IETA];
+    v[K_Q1X6] = 6.0 * v[K_Q1];
+    v[K_Q2X6] = 6.0 * v[K_Q2];
+    v[K_Q1X15] = 15.0 * v[K_Q1];
+    v[K_Q2X15] = 15.0 * v[K_Q2];
+    v[K_Q1X3] = 3.0 * v[K_Q1];
+    v[K_Q2X3] = 3.0 * v[K_Q2];
     return c;
 }
 
@@ -107,12 +122,12 @@ __device__ __forceinline__ double dot3(const double* a, const double* b)
 
 // ------------------------------------------------------- equations of motion
 // dy/dt = (dH/dp, -dH/dr, Omega_1 x S1, Omega_2 x S2)  (Eqs. 6-7, a_2.5PN = 0)
-// With n = u r, np = u (r.p), H_np = np W:
-//   dH/dp = 2 H_p2 p + (np W u) r + u^3 (Seff x r)
-//   dH/dr = u np W p - u^2 (u H_u + np^2 W) r + u^3 (p x Seff) - 3 u^5 (L.Seff) r
+// With n = u r, np = u (r.p), H_np = np W and E = u^3 Seff:
+//   dH/dp = 2 H_p2 p + (np W u) r + E x r
+//   dH/dr = u np W p - u^2 (u H_u + np^2 W) r + p x E - 3 u^2 (L.E) r
 //           + spin-spin / QM parts (see below)
-template <bool QM>
-__device__ __forceinline__ void rhs(const Coef& c, const Vec12& y, Vec12& dy)
+template <bool QM, class C>
+__device__ __forceinline__ void rhs(const C& c, const Vec12& y, Vec12& dy)
 {
     const double* r = y.r;
     const double* p = y.p;
@@ -132,58 +147,60 @@ __device__ __forceinline__ void rhs(const Coef& c, const Vec12& y, Vec12& dy)
     const double a2s = dot3(S2, r);
     const double S12 = dot3(S1, S2);
 
-    // L = r x p, Seff = g1 S1 + g2 S2
+    // L = r x p; E = u^3 Seff = G1 S1 + G2 S2 with G_i = u^3 g_i (Seff = g1 S1 + g2 S2)
     const double L0 = fma(r[1], p[2], -r[2] * p[1]);
     const double L1 = fma(r[2], p[0], -r[0] * p[2]);
     const double L2 = fma(r[0], p[1], -r[1] * p[0]);
-    const double E0 = fma(c.g1, S1[0], c.g2 * S2[0]);
-    const double E1 = fma(c.g1, S1[1], c.g2 * S2[1]);
-    const double E2 = fma(c.g1, S1[2], c.g2 * S2[2]);
-    const double LSe = fma(L0, E0, fma(L1, E1, L2 * E2));
+    const double G1 = u3 * c[K_G1], G2 = u3 * c[K_G2];
+    const double E0 = fma(G1, S1[0], G2 * S2[0]);
+    const double E1 = fma(G1, S1[1], G2 * S2[1]);
+    const double E2 = fma(G1, S1[2], G2 * S2[2]);
+    const double LE = fma(L0, E0, fma(L1, E1, L2 * E2));                     // u^3 L.Seff
 
     // orbital partial derivatives
-    const double tq = fma(c.c2, np2, c.b1);                                 // b1 + c2 np^2
-    const double Hp2x2 = fma(fma(c.a2x6, p2, c.a1x4), p2, 1.0)
-                       + u * fma(c.d1x2, u, fma(c.c1x4, p2, fma(c.c2x2, np2, 2.0 * c.b1)));
-    const double W = u * fma(c.d2x2, u, fma(c.c2x2b, p2, fma(c.c3x4, np2, c.b2x2)));
-    const double Hu = fma(fma(c.c1, p2, tq), p2, -1.0) + np2 * fma(c.c3, np2, c.b2)
-                    + u * fma(c.e1x3, u, fma(c.d1x2u, p2, fma(c.d2x2u, np2, c.h1x2)));
+    const double tq = fma(c[K_C2], np2, c[K_B1]);                                 // b1 + c2 np^2
+    const double Hp2x2 = fma(fma(c[K_A2X6], p2, c[K_A1X4]), p2, 1.0)
+                       + u * fma(c[K_D1X2], u, fma(c[K_C1X4], p2, fma(c[K_C2X2], np2, c[K_B1X2])));
+    const double W = u * fma(c[K_D2X2], u, fma(c[K_C2X2], p2, fma(c[K_C3X4], np2, c[K_B2X2])));
+    const double Hu = fma(fma(c[K_C1], p2, tq), p2, -1.0) + np2 * fma(c[K_C3], np2, c[K_B2])
+                    + u * fma(c[K_E1X3], u, fma(c[K_D1X2], p2, fma(c[K_D2X2], np2, c[K_H1X2])));
     const double cr = np * W * u;                                            // H_np u
 
     // spin-spin and QM scalars
-    double T1 = c.ieta3 * a2s;                                               // 3 ieta a2s + 6 q1 a1s
-    double T2 = c.ieta3 * a1s;                                               // 3 ieta a1s + 6 q2 a2s
-    // 15 u^2 (ieta a1s a2s + q1 a1s^2 + q2 a2s^2) + 3 LSe - 3 ieta S12 - 3 (q1 S11 + q2 S22)
-    double Q = c.ieta15 * (a1s * a2s);
-    double K = fma(-c.ieta3, S12, 3.0 * LSe);
+    double T1 = c[K_IETA3] * a2s;                                               // 3 ieta a2s + 6 q1 a1s
+    double T2 = c[K_IETA3] * a1s;                                               // 3 ieta a1s + 6 q2 a2s
+    // Ar = u^2 (u H_u + np^2 W + 3 u^3 L.Seff)
+    //    + u^5 [15 u^2 (ieta a1s a2s + q1 a1s^2 + q2 a2s^2) - 3 ieta S12 - 3 (q1 S11 + q2 S22)]
+    double Q = c[K_IETA15] * (a1s * a2s);
+    double K = -c[K_IETA3] * S12;
     if (QM) {
-        T1 = fma(c.q1x6, a1s, T1);
-        T2 = fma(c.q2x6, a2s, T2);
-        Q = fma(c.q1x15 * a1s, a1s, fma(c.q2x15 * a2s, a2s, Q));
-        K = fma(-c.q1x3, dot3(S1, S1), fma(-c.q2x3, dot3(S2, S2), K));
+        T1 = fma(c[K_Q1X6], a1s, T1);
+        T2 = fma(c[K_Q2X6], a2s, T2);
+        Q = fma(c[K_Q1X15] * a1s, a1s, fma(c[K_Q2X15] * a2s, a2s, Q));
+        K = fma(-c[K_Q1X3], dot3(S1, S1), fma(-c[K_Q2X3], dot3(S2, S2), K));
     }
     const double V1 = u5 * T1;
     const double V2 = u5 * T2;
-    const double Ar = u2 * fma(np2, W, u * Hu) + u5 * fma(Q, u2, K);
+    const double Ar = fma(u2, fma(3.0, LE, fma(np2, W, u * Hu)), u5 * fma(Q, u2, K));
 
-    // dr/dt = Hp2x2 p + cr r + u^3 (Seff x r)
+    // dr/dt = Hp2x2 p + cr r + E x r
     const double X0 = fma(E1, r[2], -E2 * r[1]);
     const double X1 = fma(E2, r[0], -E0 * r[2]);
     const double X2 = fma(E0, r[1], -E1 * r[0]);
-    dy.r[0] = fma(Hp2x2, p[0], fma(cr, r[0], u3 * X0));
-    dy.r[1] = fma(Hp2x2, p[1], fma(cr, r[1], u3 * X1));
-    dy.r[2] = fma(Hp2x2, p[2], fma(cr, r[2], u3 * X2));
+    dy.r[0] = fma(Hp2x2, p[0], fma(cr, r[0], X0));
+    dy.r[1] = fma(Hp2x2, p[1], fma(cr, r[1], X1));
+    dy.r[2] = fma(Hp2x2, p[2], fma(cr, r[2], X2));
 
-    // dp/dt = -cr p + Ar r - V1 S1 - V2 S2 - u^3 (p x Seff)
+    // dp/dt = -cr p + Ar r - V1 S1 - V2 S2 - p x E
     const double Y0 = fma(p[1], E2, -p[2] * E1);
     const double Y1 = fma(p[2], E0, -p[0] * E2);
     const double Y2 = fma(p[0], E1, -p[1] * E0);
-    dy.p[0] = fma(-cr, p[0], fma(Ar, r[0], fma(-V1, S1[0], fma(-V2, S2[0], -u3 * Y0))));
-    dy.p[1] = fma(-cr, p[1], fma(Ar, r[1], fma(-V1, S1[1], fma(-V2, S2[1], -u3 * Y1))));
-    dy.p[2] = fma(-cr, p[2], fma(Ar, r[2], fma(-V1, S1[2], fma(-V2, S2[2], -u3 * Y2))));
+    dy.p[0] = fma(-cr, p[0], fma(Ar, r[0], fma(-V1, S1[0], fma(-V2, S2[0], -Y0))));
+    dy.p[1] = fma(-cr, p[1], fma(Ar, r[1], fma(-V1, S1[1], fma(-V2, S2[1], -Y1))));
+    dy.p[2] = fma(-cr, p[2], fma(Ar, r[2], fma(-V1, S1[2], fma(-V2, S2[2], -Y2))));
 
     // dS1/dt = (u^3 g1 L + V1 r - u^3 ieta S2) x S1, and 1 <-> 2 (Eqs. 7-9)
-    const double G1 = u3 * c.g1, G2 = u3 * c.g2, I3 = u3 * c.ieta;
+    const double I3 = u3 * c[K_IETA];
     const double O10 = fma(G1, L0, fma(V1, r[0], -I3 * S2[0]));
     const double O11 = fma(G1, L1, fma(V1, r[1], -I3 * S2[1]));
     const double O12 = fma(G1, L2, fma(V1, r[2], -I3 * S2[2]));
@@ -199,8 +216,8 @@ __device__ __forceinline__ void rhs(const Coef& c, const Vec12& y, Vec12& dy)
 }
 
 // ------------------------------------------------------------ Hamiltonian
-template <bool QM>
-__device__ __forceinline__ double hamiltonian(const Coef& c, const Vec12& y)
+template <bool QM, class C>
+__device__ __forceinline__ double hamiltonian(const C& c, const Vec12& y)
 {
     const double rr2 = dot3(y.r, y.r);
     const double u = rsqrt(rr2);
@@ -214,13 +231,13 @@ __device__ __forceinline__ double hamiltonian(const Coef& c, const Vec12& y)
     const double LS2 = fma(L0, y.s2[0], fma(L1, y.s2[1], L2 * y.s2[2]));
     const double a1 = dot3(y.s1, y.r) * u, a2 = dot3(y.s2, y.r) * u;
     const double u3 = u * u * u;
-    double Hp = fma(fma(c.a2, p2, c.a1), p2, 0.5) * p2;                         // p2/2 + a1 p2^2 + a2 p2^3
-    double Hu1 = fma(c.b1, p2, c.b2 * np2) + p2 * fma(c.c1, p2, c.c2 * np2) + c.c3 * np2 * np2 - 1.0;
-    double Hu2 = fma(c.d1, p2, fma(c.d2, np2, c.h1));
-    double Hu3 = c.e1 + c.ieta * fma(3.0 * a1, a2, -dot3(y.s1, y.s2));
+    double Hp = fma(fma(c[K_A2], p2, c[K_A1]), p2, 0.5) * p2;                         // p2/2 + a1 p2^2 + a2 p2^3
+    double Hu1 = fma(c[K_B1], p2, c[K_B2] * np2) + p2 * fma(c[K_C1], p2, c[K_C2] * np2) + c[K_C3] * np2 * np2 - 1.0;
+    double Hu2 = fma(c[K_D1], p2, fma(c[K_D2], np2, c[K_H1]));
+    double Hu3 = c[K_E1] + c[K_IETA] * fma(3.0 * a1, a2, -dot3(y.s1, y.s2));
     if (QM)
-        Hu3 += c.q1 * fma(3.0 * a1, a1, -dot3(y.s1, y.s1)) + c.q2 * fma(3.0 * a2, a2, -dot3(y.s2, y.s2));
-    const double Hso = u3 * fma(c.g1, LS1, c.g2 * LS2);
+        Hu3 += c[K_Q1] * fma(3.0 * a1, a1, -dot3(y.s1, y.s1)) + c[K_Q2] * fma(3.0 * a2, a2, -dot3(y.s2, y.s2));
+    const double Hso = u3 * fma(c[K_G1], LS1, c[K_G2] * LS2);
     return Hp + u * fma(u, fma(u, Hu3, Hu2), Hu1) + Hso;
 }
 
@@ -238,8 +255,8 @@ struct Ref {
     double E, J, S1, S2;
 };
 
-template <bool QM>
-__device__ __forceinline__ Ref integrals(const Coef& c, const Vec12& y)
+template <bool QM, class C>
+__device__ __forceinline__ Ref integrals(const C& c, const Vec12& y)
 {
     Ref R;
     R.E = hamiltonian<QM>(c, y);
@@ -250,8 +267,8 @@ __device__ __forceinline__ Ref integrals(const Coef& c, const Vec12& y)
 }
 
 // ------------------------------------------------------------------- RK4
-template <bool QM>
-__device__ __forceinline__ void rk4_step(const Coef& c, Vec12& y, double h)
+template <bool QM, class C>
+__device__ __forceinline__ void rk4_step(const C& c, Vec12& y, double h)
 {
     const double h2 = 0.5 * h, h3 = h * (1.0 / 3.0), h6 = h * (1.0 / 6.0);
     Vec12 k, st, acc;
@@ -303,8 +320,8 @@ struct NewtonCfg {
 //   + u (B0 + alpha^2 (B2 + alpha^2 B4)) + u^2 (C0 + alpha^2 C2 + alpha E1) + u^3 D0
 // whose coefficients are evaluated once at (r*, p*, S); and
 // |J|^2 = k^2 L*.L* + 2 k L*.S + S.S with k = alpha beta, S = S1 + S2.
-template <bool QM>
-__device__ __forceinline__ int correct(const Coef& c, Vec12& y, const Ref& ref,
+template <bool QM, class C>
+__device__ __forceinline__ int correct(const C& c, Vec12& y, const Ref& ref,
                                        const NewtonCfg& nc, int* kind)
 {
     // Eq. 10: spin lengths
@@ -331,29 +348,57 @@ __device__ __forceinline__ int correct(const Coef& c, Vec12& y, const Ref& ref,
     const double LL = fma(L0, L0, fma(L1, L1, L2 * L2));
     const double LJ = fma(L0, Sx, fma(L1, Sy, L2 * Sz));
     const double SSq = fma(Sx, Sx, fma(Sy, Sy, Sz * Sz));
-    const double LSe = c.g1 * fma(L0, y.s1[0], fma(L1, y.s1[1], L2 * y.s1[2]))
-                     + c.g2 * fma(L0, y.s2[0], fma(L1, y.s2[1], L2 * y.s2[2]));
+    const double LSe = c[K_G1] * fma(L0, y.s1[0], fma(L1, y.s1[1], L2 * y.s1[2]))
+                     + c[K_G2] * fma(L0, y.s2[0], fma(L1, y.s2[1], L2 * y.s2[2]));
     const double a1 = dot3(y.s1, y.r) * R, a2 = dot3(y.s2, y.r) * R;
     const double R2 = R * R, R3 = R2 * R;
     const double A2 = 0.5 * P2;
-    const double A4 = c.a1 * P2 * P2;
-    const double A6 = c.a2 * P2 * P2 * P2;
+    const double A4 = c[K_A1] * P2 * P2;
+    const double A6 = c[K_A2] * P2 * P2 * P2;
     const double B0 = -R;
-    const double B2 = R * fma(c.b1, P2, c.b2 * NP2);
-    const double B4 = R * fma(P2, fma(c.c1, P2, c.c2 * NP2), c.c3 * NP2 * NP2);
-    const double C0 = c.h1 * R2;
-    const double C2 = R2 * fma(c.d1, P2, c.d2 * NP2);
+    const double B2 = R * fma(c[K_B1], P2, c[K_B2] * NP2);
+    const double B4 = R * fma(P2, fma(c[K_C1], P2, c[K_C2] * NP2), c[K_C3] * NP2 * NP2);
+    const double C0 = c[K_H1] * R2;
+    const double C2 = R2 * fma(c[K_D1], P2, c[K_D2] * NP2);
     const double E1 = R3 * LSe;
-    double Dq = fma(c.ieta, fma(3.0 * a1, a2, -dot3(y.s1, y.s2)), c.e1);
+    double Dq = fma(c[K_IETA], fma(3.0 * a1, a2, -dot3(y.s1, y.s2)), c[K_E1]);
     if (QM)
-        Dq += c.q1 * fma(3.0 * a1, a1, -dot3(y.s1, y.s1)) + c.q2 * fma(3.0 * a2, a2, -dot3(y.s2, y.s2));
+        Dq += c[K_Q1] * fma(3.0 * a1, a1, -dot3(y.s1, y.s1)) + c[K_Q2] * fma(3.0 * a2, a2, -dot3(y.s2, y.s2));
     const double D0 = R3 * Dq;
     const double A4x2 = 2.0 * A4, A6x3 = 3.0 * A6, B4x2 = 2.0 * B4, D0x3 = 3.0 * D0, LJx2 = 2.0 * LJ;
 
     double al = 1.0, be = 1.0;
     int it = 0;
-    bool conv = false;
-    while (it < nc.max_iter) {
+    bool conv = false, stop = false;
+    // First iteration at alpha = beta = 1 (u = 1, k = 1): the monomial sums
+    // need no powers and no reciprocal; there dF2/dalpha = dF2/dbeta = dJ and
+    // dH/dbeta = -dH/du, so det = dJ (Ha + Hu).
+    {
+        ++it;
+        const double Pb = B0 + B2 + B4, Pc = C0 + C2 + E1;
+        const double H = (A2 + A4 + A6) + Pb + Pc + D0;
+        const double Ha = fma(2.0, (A2 + A4x2 + A6x3) + (B2 + B4x2) + C2, E1);
+        const double Hu = fma(2.0, Pc, Pb + D0x3);
+        const double Jn2 = LL + LJx2 + SSq;
+        const double rJ = rsqrt(Jn2);
+        const double dJ = (LL + LJ) * rJ;
+        const double F1 = H - ref.E;
+        const double F2 = fma(Jn2, rJ, -ref.J);
+        const double p1 = Ha * dJ, p2 = -Hu * dJ;
+        const double det = p1 - p2;
+        if (fabs(det) > nc.det_min * (fabs(p1) + fabs(p2))) {
+            const double rd = __drcp_rn(det);
+            const double da = fma(F1, dJ, Hu * F2) * rd;
+            const double db = fma(Ha, F2, -dJ * F1) * rd;
+            al -= da;
+            be -= db;
+            if (fabs(da) <= nc.tol && fabs(db) <= nc.tol) conv = true;
+            else if (!(fabs(al) < 1e300) || !(fabs(be) < 1e300)) stop = true;   // diverged
+        } else {
+            stop = true;   // singular: straight to velocity scaling
+        }
+    }
+    while (!conv && !stop && it < nc.max_iter) {
         ++it;
         const double u = __drcp_rn(be);
         const double a2s = al * al;

@@ -106,23 +106,23 @@ __device__ __forceinline__ Coef load_coef(const DevState& S, int64_t i, const Fl
 // the shadow, termination tests, and every `renorm` steps the FLI
 // renormalisation (acc += log10(d/d0), shadow pulled back to distance d0 and
 // given its own reference integrals).
-template <bool QM>
-__device__ __forceinline__ void advance(const RunCfg& rc, const Coef& c, Orbit& o, int32_t step_end)
+template <bool QM, class C>
+__device__ __forceinline__ void advance(const RunCfg& rc, const C& c, Orbit& o, int32_t step_end)
 {
     const double t0 = o.t;
     const int32_t n0 = o.nstep;
     while (o.nstep < step_end) {
-        rk4_step<QM>(c, o.y, rc.h);
+        rk4_step<QM, C>(c, o.y, rc.h);
         if (rc.correct) {
             int kind;
-            o.iters += correct<QM>(c, o.y, o.ref, rc.newton, &kind);
+            o.iters += correct<QM, C>(c, o.y, o.ref, rc.newton, &kind);
             o.skips += kind != CORR_DUAL;
             o.last_kind = kind;
         }
-        rk4_step<QM>(c, o.ys, rc.h);
+        rk4_step<QM, C>(c, o.ys, rc.h);
         if (rc.correct) {
             int kind;
-            o.iters += correct<QM>(c, o.ys, o.refs, rc.newton, &kind);
+            o.iters += correct<QM, C>(c, o.ys, o.refs, rc.newton, &kind);
             o.skips += kind != CORR_DUAL;
         }
         o.nstep++;
@@ -145,7 +145,7 @@ __device__ __forceinline__ void advance(const RunCfg& rc, const Coef& c, Orbit& 
             const double f = rc.d0 / d;
 #pragma unroll
             for (int k = 0; k < 12; k++) b[k] = fma(f, dv[k], a[k]);
-            o.refs = integrals<QM>(c, o.ys);
+            o.refs = integrals<QM, C>(c, o.ys);
             if (rc.fli_cap > 0.0 && o.acc >= rc.fli_cap) { o.status = ORBIT_FLI_SATURATED; break; }
         }
     }
@@ -201,7 +201,7 @@ __global__ void k_init(DevState S, RunCfg rc)
     load12<false>(S.y, S.ld, i, y);
     ys = y;
     ys.r[0] = ys.r[0] + rc.d0;
-    const Ref a = integrals<QM>(c, y), b = integrals<QM>(c, ys);
+    const Ref a = integrals<QM, Coef>(c, y), b = integrals<QM, Coef>(c, ys);
     store12(S.ys, S.ld, i, ys);
     const int64_t n = S.ld;
     S.ref[0 * n + i] = a.E; S.ref[1 * n + i] = a.J; S.ref[2 * n + i] = a.S1; S.ref[3 * n + i] = a.S2;
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(128) k_integrate_static(DevState S, RunCfg rc)
     o.status = ORBIT_RUNNING;
     const Coef c = load_coef<false>(S, i, rc.flags);
     const int32_t end = rc.nstep_base + rc.nsteps;
-    advance<QM>(rc, c, o, end);
+    advance<QM, Coef>(rc, c, o, end);
     if (o.status == ORBIT_RUNNING && o.nstep == end) o.status = ORBIT_DONE;
     store_orbit(S, i, o);
 }
@@ -262,9 +262,12 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
     return t;
 }
 
-template <bool QM, int MINB>
+// SMEM: keep the per-orbit constants in shared memory (one plane per constant)
+// instead of registers, which is what lets MINB = 3 blocks fit without spills.
+template <bool QM, int MINB, bool SMEM>
 __global__ void __launch_bounds__(128, MINB) k_integrate_queue(DevState S, RunCfg rc, QueueState q, int chunk)
 {
+    __shared__ double scoef[SMEM ? NCOEF * 128 : 1];
     const int lane = threadIdx.x & 31;
     const long long groups = (S.n + 31) / 32;
     const long long nchunks = (rc.nsteps + chunk - 1) / chunk;
@@ -298,10 +301,19 @@ __global__ void __launch_bounds__(128, MINB) k_integrate_queue(DevState S, RunCf
                 Orbit o;
                 load_orbit<true>(S, i, o);
                 o.status = ORBIT_RUNNING;
-                const Coef cf = load_coef<true>(S, i, rc.flags);
                 const long long e = (c + 1) * (long long)chunk;
                 const int32_t end = rc.nstep_base + (int32_t)(e < rc.nsteps ? e : rc.nsteps);
-                advance<QM>(rc, cf, o, end);
+                if (SMEM) {
+                    const Coef cf = load_coef<true>(S, i, rc.flags);
+                    volatile double* mine = scoef + threadIdx.x;
+#pragma unroll
+                    for (int k = 0; k < NCOEF; k++) mine[k * (int)blockDim.x] = cf.v[k];
+                    const CoefShared cs{mine, (int)blockDim.x};
+                    advance<QM, CoefShared>(rc, cs, o, end);
+                } else {
+                    const Coef cf = load_coef<true>(S, i, rc.flags);
+                    advance<QM, Coef>(rc, cf, o, end);
+                }
                 if (o.status == ORBIT_RUNNING && o.nstep == end_run) o.status = ORBIT_DONE;
                 store_orbit(S, i, o);
             }
@@ -323,7 +335,7 @@ __global__ void k_finalize(DevState S, RunCfg rc)
     Vec12 y, ys;
     load12<false>(S.y, S.ld, i, y);
     load12<false>(S.ys, S.ld, i, ys);
-    const Ref I = integrals<QM>(c, y);
+    const Ref I = integrals<QM, Coef>(c, y);
     const double* a = &y.r[0];
     const double* b = &ys.r[0];
     double d2 = 0.0;
@@ -481,25 +493,25 @@ cudaError_t launch_integrate_static(DevState S, RunCfg rc, int block, cudaStream
     return cudaGetLastError();
 }
 
-template <int MINB>
+template <int MINB, bool SMEM>
 static int occupancy_queue(int block, bool qm)
 {
     int nb = 0;
-    if (qm) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<true, MINB>, block, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<false, MINB>, block, 0);
+    if (qm) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<true, MINB, SMEM>, block, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<false, MINB, SMEM>, block, 0);
     return nb;
 }
 
 int queue_blocks_per_sm(int block, bool qm, int minb)
 {
-    return minb == 3 ? occupancy_queue<3>(block, qm) : occupancy_queue<2>(block, qm);
+    return minb == 3 ? occupancy_queue<3, true>(block, qm) : occupancy_queue<2, false>(block, qm);
 }
 
-template <int MINB>
+template <int MINB, bool SMEM>
 static void launch_queue(DevState S, RunCfg rc, QueueState q, int block, int grid, int chunk, cudaStream_t st)
 {
-    if (rc.flags.use_qm) k_integrate_queue<true, MINB><<<grid, block, 0, st>>>(S, rc, q, chunk);
-    else k_integrate_queue<false, MINB><<<grid, block, 0, st>>>(S, rc, q, chunk);
+    if (rc.flags.use_qm) k_integrate_queue<true, MINB, SMEM><<<grid, block, 0, st>>>(S, rc, q, chunk);
+    else k_integrate_queue<false, MINB, SMEM><<<grid, block, 0, st>>>(S, rc, q, chunk);
 }
 
 cudaError_t launch_integrate_queue(DevState S, RunCfg rc, QueueState q, int block, int grid,
@@ -507,8 +519,8 @@ cudaError_t launch_integrate_queue(DevState S, RunCfg rc, QueueState q, int bloc
 {
     if (S.n == 0 || rc.nsteps <= 0) return cudaSuccess;
     if (block <= 0 || block > 128 || block % 32 || grid <= 0 || chunk <= 0) return cudaErrorInvalidValue;
-    if (minb == 3) launch_queue<3>(S, rc, q, block, grid, chunk, st);
-    else launch_queue<2>(S, rc, q, block, grid, chunk, st);
+    if (minb == 3) launch_queue<3, true>(S, rc, q, block, grid, chunk, st);
+    else launch_queue<2, false>(S, rc, q, block, grid, chunk, st);
     return cudaGetLastError();
 }
 

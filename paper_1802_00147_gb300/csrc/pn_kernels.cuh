@@ -85,8 +85,9 @@ cudaError_t launch_setup_cells(const double* cells_aos, int64_t n, DevState S, i
 cudaError_t launch_load_states(const double* states_aos, int64_t n, DevState S, cudaStream_t st);
 cudaError_t launch_init(DevState S, RunCfg rc, cudaStream_t st);
 cudaError_t launch_integrate_static(DevState S, RunCfg rc, int block, cudaStream_t st);
-// minb: register budget of the queue kernel, 2 (up to 255 registers per
-// thread) or 3 (168 registers) resident 128-thread blocks per SM
+// minb: variant of the queue kernel: 2 resident 128-thread blocks per SM
+// with the per-orbit constants in registers (up to 255 per thread), or 3
+// with them in shared memory (168 registers)
 int queue_blocks_per_sm(int block, bool qm, int minb);
 cudaError_t launch_integrate_queue(DevState S, RunCfg rc, QueueState q, int block, int grid,
                                    int chunk, int minb, cudaStream_t st);
