@@ -186,6 +186,23 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def aggregate_ranks(elapsed_s, orbit_steps, device=None):
+    """Whole-job timing across ranks: the slowest rank's time and the sum of
+    every rank's orbit-steps (each rank integrates its own batch).  Single
+    process when torch.distributed is not initialised."""
+    import torch
+    import torch.distributed as td
+    if not (td.is_available() and td.is_initialized()) or td.get_world_size() == 1:
+        return float(elapsed_s), float(orbit_steps)
+    t = torch.tensor([float(elapsed_s), float(orbit_steps)], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    mx = t[:1].clone()
+    td.all_reduce(mx, op=td.ReduceOp.MAX)
+    sm = t[1:].clone()
+    td.all_reduce(sm, op=td.ReduceOp.SUM)
+    return float(mx.item()), float(sm.item())
+
+
 # --------------------------------------------------------- adaptive scan
 ADAPTIVE_N = 1024
 ADAPTIVE_T_END = 1.0e4
@@ -291,16 +308,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         if dist:
             td.barrier()
-    elapsed = ev0.elapsed_time(ev1) / 1e3
-    if dist:
-        t = torch.tensor([elapsed], device=dev)
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        elapsed = float(t.item())
-        tot = torch.tensor([float(steps_total)], device=dev)
-        td.all_reduce(tot, op=td.ReduceOp.SUM)
-        steps_all = float(tot.item())
-    else:
-        steps_all = float(steps_total)
+    elapsed, steps_all = aggregate_ranks(ev0.elapsed_time(ev1) / 1e3, steps_total, dev if dist else None)
     value = steps_all / elapsed
     if args.profile:
         if rank == 0:

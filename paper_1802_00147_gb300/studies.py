@@ -1,0 +1,79 @@
+"""Scan studies built on the library's C ABI.
+
+Quadrupole-monopole drift study: the small-scan parameter grid (equal
+masses, chi = 1) with the spin-induced quadrupole-monopole term on and
+kappa_i ~ U[1, 10] (Eqs. 4-5 with kappa multipliers), RK4 at h = 0.5 to
+t_end = 1e5; the drift of E, |J| and the spin lengths over the orbits that
+reach t_end is reported with and without the manifold correction
+(Eqs. 10-13).
+
+    python -m paper_1802_00147_gb300.studies qm [--n 1024] [--subset 65536] [--t-end 1e5]
+"""
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import ORBIT_DONE, Scan
+from . import workloads as W
+
+
+def drift_stats(out, spin_ref):
+    """Relative drift of E, |J| and |S_i| over the orbits that reached t_end."""
+    st = out["status"].cpu().numpy()
+    I = out["integrals"].cpu().numpy()
+    done = st == ORBIT_DONE
+    dE = np.abs((I[done, 1] - I[done, 0]) / I[done, 0])
+    dJ = np.abs((I[done, 3] - I[done, 2]) / I[done, 2])
+    sr = spin_ref[done]
+    dS = np.maximum(np.abs(I[done, 4] - sr[:, 0]) / sr[:, 0], np.abs(I[done, 5] - sr[:, 1]) / sr[:, 1])
+
+    def q(a):
+        return {"max": float(a.max()) if a.size else None, "median": float(np.median(a)) if a.size else None}
+
+    return {"done": int(done.sum()), "status_count": np.bincount(st, minlength=6).tolist(),
+            "dE": q(dE), "dJ": q(dJ), "dS": q(dS)}
+
+
+def qm_drift_study(n=1024, subset=0, t_end=1.0e5, h=0.5, seed=5):
+    import torch
+    cells = W.qm_grid(n, seed=seed)
+    if subset and subset < cells.shape[0]:
+        cells = W.subset(cells, subset, seed=seed + 100)[0]
+    m1 = cells[:, W.BETA] / (1 + cells[:, W.BETA])
+    m2 = 1 / (1 + cells[:, W.BETA])
+    spin_ref = np.stack([cells[:, W.CHI1] * m1 ** 2, cells[:, W.CHI2] * m2 ** 2], axis=1)
+    cd = torch.as_tensor(np.ascontiguousarray(cells[:, :9]), device="cuda")
+    report = {"grid": "%dx%d" % (n, n), "orbits": int(cells.shape[0]), "h": h, "t_end": t_end,
+              "kappa": "U[1,10]", "use_qm": 1}
+    for correct in (1, 0):
+        with Scan(None, kappa1=cells[:, W.KAP1], kappa2=cells[:, W.KAP2], device=True, n=cells.shape[0],
+                  use_qm=1, correct=correct) as s:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.setup(cd)
+            s.run(t_end, h)
+            out = s.read()
+            summ = s.summary()
+            dt = time.perf_counter() - t0
+        r = drift_stats(out, spin_ref)
+        r.update(seconds=dt, orbit_steps=summ["orbit_steps"], rate=summ["orbit_steps"] / dt,
+                 n_chaotic=summ["n_chaotic"], n_final_fallback=summ["n_final_fallback"])
+        report["corrected" if correct else "uncorrected"] = r
+    return report
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("study", choices=["qm"])
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--subset", type=int, default=0)
+    ap.add_argument("--t-end", type=float, default=1.0e5)
+    ap.add_argument("--h", type=float, default=0.5)
+    a = ap.parse_args()
+    print(json.dumps(qm_drift_study(a.n, a.subset, a.t_end, a.h)), flush=True)
+
+
+if __name__ == "__main__":
+    main()
