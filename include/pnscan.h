@@ -67,6 +67,8 @@ extern "C" {
 #define PNSCAN_SCHED_AUTO 0    /* use the autotuned choice (scan_autotune), else QUEUE */
 #define PNSCAN_SCHED_STATIC 1  /* one orbit per thread, one pass over the batch */
 #define PNSCAN_SCHED_QUEUE 2   /* persistent work-queue kernel over (32-orbit group, step chunk) tasks */
+#define PNSCAN_SCHED_COMPACT 3 /* the work queue over epochs of 256, 512, 1024, ... steps, the running
+                                  orbits compacted into a dense list between epochs (uneven batches) */
 
 /* Per-scan configuration.  scan_params_default() fills the paper's values. */
 typedef struct scan_params {
@@ -99,7 +101,7 @@ typedef struct scan_params {
     int blocks_per_sm;       /* resident blocks per SM for the queue kernel (0: occupancy maximum) */
     int register_variant;    /* queue kernel compiled for 2 (up to 255 registers/thread) or 3 (168)
                                 resident 128-thread blocks per SM (0: 2, or the autotuned choice) */
-    int use_graph;           /* 1: capture the queue run in a CUDA graph and replay it (default 1) */
+    int use_graph;           /* 1: capture a queue / compact run in a CUDA graph and replay it (default 1) */
     double sync_timeout_s;   /* host watchdog for synchronising calls (default 0: wait forever) */
     int queue_wait_limit_ms; /* bound on a work-queue task's wait for its predecessor; on expiry the
                                 kernel sets an error flag and returns, and the next synchronising

@@ -4,6 +4,7 @@
 // the launch-shape autotuner, the host watchdog and timing.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -101,6 +102,8 @@ size_t layout_state(DevState& S, char* base, int64_t n)
     S.kappa1 = (double*)take(sizeof(double) * ld);
     S.kappa2 = (double*)take(sizeof(double) * ld);
     S.out = (double*)take(sizeof(double) * 5 * ld);
+    S.order = (int32_t*)take(sizeof(int32_t) * ld);
+    S.order_next = (int32_t*)take(sizeof(int32_t) * ld);
     return off;
 }
 
@@ -133,6 +136,8 @@ RunCfg make_run(const scan_handle* h, double h_step, int32_t nsteps)
     rc.h = h_step;
     rc.nstep_base = h->nstep_now;
     rc.nsteps = nsteps;
+    rc.final_step = h->nstep_now + nsteps;
+    rc.first_epoch = 1;
     return rc;
 }
 
@@ -173,13 +178,55 @@ int queue_grid(scan_handle* h, int block, int bps, int minb)
 }
 
 // Launch the integrator for one run on stream st (no timing).
+// Epoch lengths of the compacting schedule: 256, 512, 1024, ... steps, the
+// last one cut to the run's end, so orbits that stop early leave the dense
+// list soon after they stop.
+std::vector<int32_t> epoch_lengths(int32_t nsteps)
+{
+    std::vector<int32_t> e;
+    int32_t len = 256, done = 0;
+    while (done < nsteps) {
+        const int32_t l = len < nsteps - done ? len : nsteps - done;
+        e.push_back(l);
+        done += l;
+        if (len < (1 << 30) / 2) len *= 2;
+    }
+    return e;
+}
+
 int launch_run(scan_handle* h, const RunCfg& rc, int sched, int block, int chunk, int bps, int minb,
                const DevState& S, cudaStream_t st)
 {
     if (sched == PNSCAN_SCHED_STATIC) return cuda_err(launch_integrate_static(S, rc, block, st));
-    int r = reset_queue(h, st);
-    if (r != PNSCAN_OK) return r;
-    return cuda_err(launch_integrate_queue(S, rc, h->q, block, queue_grid(h, block, bps, minb), chunk, minb, st));
+    const int grid = queue_grid(h, block, bps, minb);
+    if (sched == PNSCAN_SCHED_QUEUE) {
+        int r = reset_queue(h, st);
+        if (r != PNSCAN_OK) return r;
+        return cuda_err(launch_integrate_queue(S, rc, h->q, block, grid, chunk, minb, 0, st));
+    }
+    // PNSCAN_SCHED_COMPACT: epochs over a dense list of the running orbits
+    DevState E = S;
+    int r = cuda_err(launch_compact(E, h->q, 1, 1, st));
+    if (r == PNSCAN_OK) r = cuda_err(cudaMemcpyAsync(h->q.count, h->q.count + 1, sizeof(int), cudaMemcpyDeviceToDevice, st));
+    std::swap(E.order, E.order_next);
+    int32_t offset = 0;
+    const std::vector<int32_t> lens = epoch_lengths(rc.nsteps);
+    for (size_t k = 0; k < lens.size() && r == PNSCAN_OK; k++) {
+        RunCfg erc = rc;
+        erc.nstep_base = rc.nstep_base + offset;
+        erc.nsteps = lens[k];
+        erc.first_epoch = k == 0;
+        r = reset_queue(h, st);
+        if (r == PNSCAN_OK) r = cuda_err(launch_integrate_queue(E, erc, h->q, block, grid, chunk, minb, 1, st));
+        offset += lens[k];
+        if (r == PNSCAN_OK && k + 1 < lens.size()) {
+            r = cuda_err(launch_compact(E, h->q, 0, 0, st));
+            if (r == PNSCAN_OK)
+                r = cuda_err(cudaMemcpyAsync(h->q.count, h->q.count + 1, sizeof(int), cudaMemcpyDeviceToDevice, st));
+            std::swap(E.order, E.order_next);
+        }
+    }
+    return r;
 }
 
 bool same_run(const RunCfg& a, const RunCfg& b)
@@ -190,7 +237,8 @@ bool same_run(const RunCfg& a, const RunCfg& b)
            a.newton.det_min == b.newton.det_min && a.correct == b.correct && a.h == b.h &&
            a.d0 == b.d0 && a.renorm == b.renorm && a.fli_cap == b.fli_cap &&
            a.rmerge2 == b.rmerge2 && a.rescape2 == b.rescape2 && a.nstep_base == b.nstep_base &&
-           a.nsteps == b.nsteps && a.wait_limit_ns == b.wait_limit_ns && a.stall_group == b.stall_group;
+           a.nsteps == b.nsteps && a.wait_limit_ns == b.wait_limit_ns && a.stall_group == b.stall_group &&
+           a.final_step == b.final_step && a.first_epoch == b.first_epoch;
 }
 
 int run_graph(scan_handle* h, const RunCfg& rc)
@@ -261,7 +309,7 @@ int scan_create(const scan_params* p, scan_handle** out)
     if (p->block_size && (p->block_size < 32 || p->block_size > 128 || p->block_size % 32)) return PNSCAN_ERR_ARG;
     if (p->chunk_steps < 0 || p->blocks_per_sm < 0 || p->queue_wait_limit_ms < 0) return PNSCAN_ERR_ARG;
     if (p->register_variant != 0 && p->register_variant != 2 && p->register_variant != 3) return PNSCAN_ERR_ARG;
-    if (p->schedule < 0 || p->schedule > 2) return PNSCAN_ERR_ARG;
+    if (p->schedule < 0 || p->schedule > 3) return PNSCAN_ERR_ARG;
     if ((p->alloc_fn == nullptr) != (p->free_fn == nullptr)) return PNSCAN_ERR_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -293,14 +341,15 @@ int scan_create(const scan_params* p, scan_handle** out)
 
     const int64_t groups = (n + 31) / 32;
     h->queue_bytes = align256(sizeof(unsigned long long)) + align256(sizeof(int)) + align256(sizeof(int) * (groups + 1));
-    h->queue_block = dev_alloc(h, h->queue_bytes + align256(sizeof(Summary)));
+    h->queue_block = dev_alloc(h, h->queue_bytes + align256(2 * sizeof(int)) + align256(sizeof(Summary)));
     if (!h->queue_block) return fail(PNSCAN_ERR_OOM);
     {
         char* b = (char*)h->queue_block;
         h->q.next = (unsigned long long*)b;
         h->q.error = (int*)(b + align256(sizeof(unsigned long long)));
         h->q.group_done = (int*)(b + align256(sizeof(unsigned long long)) + align256(sizeof(int)));
-        h->dsum = (Summary*)(b + h->queue_bytes);
+        h->q.count = (int*)(b + h->queue_bytes);
+        h->dsum = (Summary*)(b + h->queue_bytes + align256(2 * sizeof(int)));
     }
     if (!p->device_ptrs) {
         h->staging = (double*)dev_alloc(h, sizeof(double) * 12 * (size_t)(n > 0 ? n : 1));
@@ -348,7 +397,7 @@ int scan_create(const scan_params* p, scan_handle** out)
     b.rescape2 = p->r_escape > 0.0 ? p->r_escape * p->r_escape : 0.0;
     b.wait_limit_ns = (unsigned long long)(p->queue_wait_limit_ms > 0 ? p->queue_wait_limit_ms : 20000) * 1000000ull;
     b.stall_group = p->debug_stall_group;
-    h->sched = p->schedule == PNSCAN_SCHED_STATIC ? PNSCAN_SCHED_STATIC : PNSCAN_SCHED_QUEUE;
+    h->sched = p->schedule == PNSCAN_SCHED_AUTO ? PNSCAN_SCHED_QUEUE : p->schedule;
     h->block = p->block_size ? p->block_size : 128;
     h->chunk = p->chunk_steps ? p->chunk_steps : 500;
     h->bps = p->blocks_per_sm;
@@ -399,7 +448,7 @@ int scan_run(scan_handle* h, const double* initial_states, double t_end, double 
     if (nsteps > 0 && h->S.n > 0) {
         const RunCfg rc = make_run(h, h_step, nsteps);
         if (cudaEventRecord(h->ev0, h->stream) != cudaSuccess) return PNSCAN_ERR_CUDA;
-        if (h->sched == PNSCAN_SCHED_QUEUE && h->p.use_graph) r = run_graph(h, rc);
+        if (h->sched != PNSCAN_SCHED_STATIC && h->p.use_graph) r = run_graph(h, rc);
         else r = launch_run(h, rc, h->sched, h->block, h->chunk, h->bps, h->minb, h->S, h->stream);
         if (r != PNSCAN_OK) return r;
         if (cudaEventRecord(h->ev1, h->stream) != cudaSuccess) return PNSCAN_ERR_CUDA;
@@ -520,6 +569,8 @@ int scan_autotune(scan_handle* h, int steps, int* schedule, int* block_size, int
         struct Cand { int sched, block, chunk, bps, minb; };
         std::vector<Cand> cands;
         for (int blk_sz : {64, 128}) cands.push_back({PNSCAN_SCHED_STATIC, blk_sz, 0, 0, 2});
+        for (int ch : {steps / 16, steps / 8})
+            if (ch >= 1) cands.push_back({PNSCAN_SCHED_COMPACT, 128, ch, 0, 2});
         for (int minb : {2, 3})
             for (int ch : {steps / 16, steps / 8, steps / 4}) {
                 if (ch < 1) continue;
@@ -559,7 +610,7 @@ int scan_autotune(scan_handle* h, int steps, int* schedule, int* block_size, int
         h->block = bestc.block;
         // a tuned chunk is a fraction of the tuning run; keep the same number
         // of chunks per run length as a lower bound on the task count
-        h->chunk = bestc.sched == PNSCAN_SCHED_QUEUE ? bestc.chunk : h->chunk;
+        h->chunk = bestc.sched != PNSCAN_SCHED_STATIC ? bestc.chunk : h->chunk;
         h->bps = bestc.bps;
         h->minb = bestc.minb;
         h->tuned = true;

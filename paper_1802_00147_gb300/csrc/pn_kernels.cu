@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(128) k_integrate_static(DevState S, RunCfg rc)
     const Coef c = load_coef<false>(S, i, rc.flags);
     const int32_t end = rc.nstep_base + rc.nsteps;
     advance<QM, Coef>(rc, c, o, end);
-    if (o.status == ORBIT_RUNNING && o.nstep == end) o.status = ORBIT_DONE;
+    if (o.status == ORBIT_RUNNING && o.nstep == rc.final_step) o.status = ORBIT_DONE;
     store_orbit(S, i, o);
 }
 
@@ -265,14 +265,17 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
 // SMEM: keep the per-orbit constants in shared memory (one plane per constant)
 // instead of registers, which is what lets MINB = 3 blocks fit without spills.
 template <bool QM, int MINB, bool SMEM>
-__global__ void __launch_bounds__(128, MINB) k_integrate_queue(DevState S, RunCfg rc, QueueState q, int chunk)
+__global__ void __launch_bounds__(128, MINB) k_integrate_queue(DevState S, RunCfg rc, QueueState q, int chunk,
+                                                                int use_order)
 {
     __shared__ double scoef[SMEM ? NCOEF * 128 : 1];
     const int lane = threadIdx.x & 31;
-    const long long groups = (S.n + 31) / 32;
+    // compacting schedule: slot s of the dense list holds orbit order[s]
+    const long long nslots = use_order ? (long long)__ldcg(q.count) : S.n;
+    const long long groups = (nslots + 31) / 32;
     const long long nchunks = (rc.nsteps + chunk - 1) / chunk;
     const unsigned long long ntasks = (unsigned long long)(groups * nchunks);
-    const int32_t end_run = rc.nstep_base + rc.nsteps;
+    const int32_t end_run = rc.final_step;
     for (;;) {
         unsigned long long task = 0;
         if (lane == 0) task = (*(volatile int*)q.error) ? ntasks : atomicAdd(q.next, 1ull);
@@ -294,10 +297,11 @@ __global__ void __launch_bounds__(128, MINB) k_integrate_queue(DevState S, RunCf
         }
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) break;
-        const int64_t i = g * 32 + lane;
-        if (i < S.n) {
+        const int64_t slot = g * 32 + lane;
+        if (slot < nslots) {
+            const int64_t i = use_order ? (int64_t)__ldcg(S.order + slot) : slot;
             const int32_t st = __ldcg(S.status + i);
-            if (st == ORBIT_RUNNING || (c == 0 && st == ORBIT_DONE)) {
+            if (st == ORBIT_RUNNING || (c == 0 && rc.first_epoch && st == ORBIT_DONE)) {
                 Orbit o;
                 load_orbit<true>(S, i, o);
                 o.status = ORBIT_RUNNING;
@@ -322,6 +326,29 @@ __global__ void __launch_bounds__(128, MINB) k_integrate_queue(DevState S, RunCf
         __syncwarp();
         if (lane == 0 && !(c == 0 && g == rc.stall_group)) st_release(q.group_done + g, (int)(c + 1));
     }
+}
+
+// ------------------------------------------------------------- compaction
+// Running orbits of the current list (or of all orbits) appended to the next
+// list with one warp-aggregated atomic per warp; the order within the list
+// does not matter, since an orbit's arithmetic does not depend on its slot.
+__global__ void k_compact(DevState S, QueueState q, int from_all, int first_epoch)
+{
+    const long long nslots = from_all ? S.n : (long long)__ldcg(q.count);
+    const long long slot = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    bool keep = false;
+    int32_t i = 0;
+    if (slot < nslots) {
+        i = from_all ? (int32_t)slot : __ldcg(S.order + slot);
+        const int32_t st = __ldcg(S.status + i);
+        keep = st == ORBIT_RUNNING || (first_epoch && st == ORBIT_DONE);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    int base = 0;
+    if (lane == 0 && m) base = atomicAdd(q.count + 1, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (keep) S.order_next[base + __popc(m & ((1u << lane) - 1u))] = i;
 }
 
 // --------------------------------------------------------------- finalize
@@ -508,19 +535,29 @@ int queue_blocks_per_sm(int block, bool qm, int minb)
 }
 
 template <int MINB, bool SMEM>
-static void launch_queue(DevState S, RunCfg rc, QueueState q, int block, int grid, int chunk, cudaStream_t st)
+static void launch_queue(DevState S, RunCfg rc, QueueState q, int block, int grid, int chunk, int use_order,
+                         cudaStream_t st)
 {
-    if (rc.flags.use_qm) k_integrate_queue<true, MINB, SMEM><<<grid, block, 0, st>>>(S, rc, q, chunk);
-    else k_integrate_queue<false, MINB, SMEM><<<grid, block, 0, st>>>(S, rc, q, chunk);
+    if (rc.flags.use_qm) k_integrate_queue<true, MINB, SMEM><<<grid, block, 0, st>>>(S, rc, q, chunk, use_order);
+    else k_integrate_queue<false, MINB, SMEM><<<grid, block, 0, st>>>(S, rc, q, chunk, use_order);
 }
 
 cudaError_t launch_integrate_queue(DevState S, RunCfg rc, QueueState q, int block, int grid,
-                                   int chunk, int minb, cudaStream_t st)
+                                   int chunk, int minb, int use_order, cudaStream_t st)
 {
     if (S.n == 0 || rc.nsteps <= 0) return cudaSuccess;
     if (block <= 0 || block > 128 || block % 32 || grid <= 0 || chunk <= 0) return cudaErrorInvalidValue;
-    if (minb == 3) launch_queue<3, true>(S, rc, q, block, grid, chunk, st);
-    else launch_queue<2, false>(S, rc, q, block, grid, chunk, st);
+    if (minb == 3) launch_queue<3, true>(S, rc, q, block, grid, chunk, use_order, st);
+    else launch_queue<2, false>(S, rc, q, block, grid, chunk, use_order, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact(DevState S, QueueState q, int from_all, int first_epoch, cudaStream_t st)
+{
+    if (S.n == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(q.count + 1, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_compact<<<grid_for(S.n, 256), 256, 0, st>>>(S, q, from_all, first_epoch);
     return cudaGetLastError();
 }
 

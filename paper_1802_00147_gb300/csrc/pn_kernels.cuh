@@ -37,6 +37,8 @@ struct DevState {
     double* kappa1;        // [n]
     double* kappa2;        // [n]
     double* out;           // [5][n]  E, |J|, |S1|, |S2|, FLI (written by finalize)
+    int32_t* order;        // [n]     compacting schedule: running orbits, densely
+    int32_t* order_next;   // [n]     the next epoch's list
 };
 
 struct RunCfg {
@@ -49,8 +51,10 @@ struct RunCfg {
     double fli_cap;        // stop at FLI >= cap (<= 0: never)
     double rmerge2;        // stop at |r|^2 < rmerge2 (<= 0: never)
     double rescape2;       // stop at |r|^2 > rescape2 (<= 0: never)
-    int32_t nstep_base;    // nstep of every running orbit when the run started
-    int32_t nsteps;        // steps in this run
+    int32_t nstep_base;    // nstep of every running orbit when the run (or epoch) started
+    int32_t nsteps;        // steps in this run (or epoch)
+    int32_t final_step;    // nstep at which an orbit is DONE (end of the whole run)
+    int first_epoch;       // 1: orbits left DONE by an earlier run may continue
     unsigned long long wait_limit_ns;  // bound on a queue task's wait for its predecessor
     int stall_group;       // test hook: this group never publishes chunk 0 (-1: off)
 };
@@ -62,6 +66,7 @@ struct QueueState {
     unsigned long long* next;   // [1]
     int* error;                 // [1] nonzero: a bounded wait gave up
     int* group_done;            // [groups] chunks finished per group
+    int* count;                 // [2] compacting schedule: orbits in order / order_next
 };
 
 struct Summary {                // scan-level reduction (device layout)
@@ -90,7 +95,10 @@ cudaError_t launch_integrate_static(DevState S, RunCfg rc, int block, cudaStream
 // with them in shared memory (168 registers)
 int queue_blocks_per_sm(int block, bool qm, int minb);
 cudaError_t launch_integrate_queue(DevState S, RunCfg rc, QueueState q, int block, int grid,
-                                   int chunk, int minb, cudaStream_t st);
+                                   int chunk, int minb, int use_order, cudaStream_t st);
+// Compacting schedule: order_next <- running orbits of order (or of all
+// orbits when from_all), count[1] <- their number; then swap is up to the caller.
+cudaError_t launch_compact(DevState S, QueueState q, int from_all, int first_epoch, cudaStream_t st);
 cudaError_t launch_finalize(DevState S, RunCfg rc, cudaStream_t st);
 cudaError_t launch_reduce(DevState S, double fli_thresh, Summary* out, cudaStream_t st);
 cudaError_t launch_gather(DevState S, double* states_aos, double* shadow_aos, double* integ_aos,

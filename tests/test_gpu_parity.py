@@ -135,9 +135,13 @@ def assert_parity(g, o, s_state, s_fli, nsteps):
     return float(err.max()) if err.size else 0.0
 
 
+GPU_ONLY = ("schedule", "chunk_steps", "block_size", "blocks_per_sm", "register_variant", "use_graph")
+
+
 def check(pn, cells, nsteps, h=1.0, **opts):
     g = gpu_run(pn, cells, nsteps, h, read_diag=True, **opts)
-    o, s_state, s_fli = oracle_sensitivity(cells, nsteps, h, **opts)
+    physics = {k: v for k, v in opts.items() if k not in GPU_ONLY}
+    o, s_state, s_fli = oracle_sensitivity(cells, nsteps, h, **physics)
     assert_parity(g, o, s_state, s_fli, nsteps)
     return g, o
 
@@ -175,9 +179,10 @@ def test_full_scan_sampled_parity_bench_shape(pn, schedule):
     assert_parity(gs, o, s_state, s_fli, 1000)
 
 
-def test_uneven_batch_parity_with_early_stops(pn):
+@pytest.mark.parametrize("schedule", [2, 3])
+def test_uneven_batch_parity_with_early_stops(pn, schedule):
     cells = W.uneven_batch(n=1500, seed=3)
-    g, o = check(pn, cells, 1000)
+    g, o = check(pn, cells, 1000, schedule=schedule)
     assert (o["status"] == oracle.MERGED).sum() > 50       # the batch really is uneven
 
 
@@ -211,7 +216,9 @@ def test_schedules_chunks_and_pointers_are_bit_identical(pn):
     b = gpu_run(pn, cells, 300, schedule=2, chunk_steps=64)
     c = gpu_run(pn, cells, 300, schedule=2, chunk_steps=100, chunks=3)    # 3 scan_run calls
     d = gpu_run(pn, cells, 300, schedule=2, device=True, use_graph=0)
-    for other in (b, c, d):
+    f = gpu_run(pn, cells, 300, schedule=3, chunk_steps=64)                # compacting epochs
+    g = gpu_run(pn, cells, 300, schedule=3, chunk_steps=100, chunks=3, use_graph=0)
+    for other in (b, c, d, f, g):
         for k in ("states", "fli", "status", "t_stop", "integrals"):
             np.testing.assert_array_equal(a[k], other[k], err_msg=k)
     # the shared-memory-constants variant is compiled separately: the same
