@@ -222,6 +222,9 @@ def run_adaptive(cells_full, cells_full_d, fli_full_d, thr=6.0, band=1.0, spread
     Xf = pn.adaptive_features(cells_full_d)
     X = torch.cat([Xs, Xf])
     y = torch.cat([ys, fli_full_d.float()])
+    torch.cuda.synchronize()
+    data_s = time.perf_counter() - t0          # integrating the small scan (the full one is reused)
+    t0 = time.perf_counter()
     sur, hist = A.train_surrogate(X, y, members=5, steps=4000, lr=3e-3, seed=1)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
@@ -234,6 +237,7 @@ def run_adaptive(cells_full, cells_full_d, fli_full_d, thr=6.0, band=1.0, spread
     sub_idx_d = torch.as_tensor(sub_idx, device="cuda")
     out = {"grid": "%dx%d" % (ADAPTIVE_N, ADAPTIVE_N), "t_end": ADAPTIVE_T_END, "members": 5,
            "train_steps": 4000, "train_rows": int(X.shape[0]), "train_s": train_s,
+           "training_data_s": data_s,
            "train_loss_first_last": [float(hist[:, :20].mean()), float(hist[:, -200:].mean())],
            "plain_s": full["seconds"]}
     for name, th, bd, sp in [("thr6", thr, band, spread_max)]:
@@ -250,6 +254,31 @@ def run_adaptive(cells_full, cells_full_d, fli_full_d, thr=6.0, band=1.0, spread
                      "chaotic_frac": float(truth.float().mean().item())}
     sur.close()
     return out
+
+
+# ----------------------------------------------------------- uneven batch
+def run_uneven(n=100_000, t_end=2.0e4):
+    """The uneven batch (mass ratio 0.1-1, isotropic spins, p_y 50-100% of
+    circular; merger / escape / FLI-saturation cut-offs), autotuned schedule,
+    one timed run through the CUDA graph."""
+    import torch
+    import paper_1802_00147_gb300 as pn
+    from paper_1802_00147_gb300 import workloads as W
+    cells = W.uneven_batch(n, seed=3)
+    cd = torch.as_tensor(np.ascontiguousarray(cells[:, :9]), device="cuda")
+    with pn.Scan(None, device=True, n=n, fli_cap=12.0) as s:
+        s.setup(cd)
+        shape = s.autotune(2000)
+        for _ in range(2):                      # warm-up (and graph capture), then timed
+            s.setup(cd)
+            s.run(t_end, H_STEP)
+            summ = s.summary()
+        ms, _ = s.last_run_timing()
+    return {"workload": "uneven batch: 1e5 orbits, beta~U[0.1,1], chi~U[0,1], isotropic spins, "
+                        "x0~U[10,50], p_y 50-100% of circular; stops at r<6, r>1e3, FLI>=12; t_end 2e4",
+            "schedule": shape, "kernel_ms": ms, "orbit_steps": summ["orbit_steps"],
+            "value": summ["orbit_steps"] / (ms * 1e-3), "unit": UNIT,
+            "status_count": summ["status_count"]}
 
 
 # -------------------------------------------------------------------- ours
@@ -342,6 +371,7 @@ def run_ours(args, rank, world, local_rank):
     h2d = cells9.nbytes
     d2h = sum(a.nbytes for a in out.values())
 
+    uneven = run_uneven() if (rank == 0 and args.adaptive) else None
     adaptive = None
     if args.adaptive and rank == 0:
         fli_full = scan.read()["fli"]
@@ -371,6 +401,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": 5 * args.steps,
         "clocks": clk.summary(),
         "adaptive": adaptive,
+        "uneven": uneven,
         "scan": {k: summ[k] for k in ("n_chaotic", "status_count", "max_dE", "max_dJ", "max_dJ_all",
                                       "n_final_fallback", "max_dS", "fli_mean", "newton_iters",
                                       "n_skip", "orbit_steps")},
@@ -389,7 +420,7 @@ def main():
                     help="seeded subset of the 314x314 scan (0: all 98,596); profiling only")
     ap.add_argument("--t-end", type=float, default=T_END, help="integration time (profiling only)")
     ap.add_argument("--no-adaptive", dest="adaptive", action="store_false",
-                    help="skip the surrogate-adaptive 1024x1024 scan measurement")
+                    help="skip the uneven-batch and surrogate-adaptive 1024x1024 measurements")
     ap.add_argument("--profile", action="store_true",
                     help="time the device path only (no autotune, e2e or CPU leg) for ncu runs")
     args = ap.parse_args()
