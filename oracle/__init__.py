@@ -23,7 +23,7 @@ class Config(_ct.Structure):
         ("correct", _ct.c_int),
         ("newton_tol", _ct.c_double), ("newton_max", _ct.c_int), ("det_min", _ct.c_double),
         ("fli_d0", _ct.c_double), ("fli_renorm", _ct.c_int), ("fli_cap", _ct.c_double),
-        ("r_merge", _ct.c_double), ("r_escape", _ct.c_double),
+        ("r_merge", _ct.c_double), ("r_escape", _ct.c_double), ("rk_order", _ct.c_int),
     ]
 
 
@@ -37,9 +37,9 @@ class Sys(_ct.Structure):
 
 def config(pn_order=2, use_so=1, use_ss=1, use_qm=0, correct=1, newton_tol=1e-10,
            newton_max=50, det_min=1e-5, fli_d0=1e-9, fli_renorm=100, fli_cap=0.0,
-           r_merge=6.0, r_escape=1e3):
+           r_merge=6.0, r_escape=1e3, rk_order=4):
     return Config(pn_order, use_so, use_ss, use_qm, correct, newton_tol, newton_max,
-                  det_min, fli_d0, fli_renorm, fli_cap, r_merge, r_escape)
+                  det_min, fli_d0, fli_renorm, fli_cap, r_merge, r_escape, rk_order)
 
 
 def lib():
@@ -58,6 +58,7 @@ def lib():
         L.orc_gradient.argtypes = [P(Sys), dp, dp]
         L.orc_rhs.argtypes = [P(Sys), dp, dp]
         L.orc_rk4_step.argtypes = [P(Sys), dp, d]
+        L.orc_rk5_step.argtypes = [P(Sys), dp, d]
         L.orc_integrals.argtypes = [P(Sys), dp, dp]
         L.orc_correct.argtypes = [P(Sys), dp, dp, d, i, d, P(i), dp]
         L.orc_correct.restype = i
@@ -111,6 +112,12 @@ def rhs(s, y):
 def rk4_step(s, y, h):
     y = _vec(y).copy()
     lib().orc_rk4_step(_ct.byref(s), _dp(y), float(h))
+    return y
+
+
+def rk5_step(s, y, h):
+    y = _vec(y).copy()
+    lib().orc_rk5_step(_ct.byref(s), _dp(y), float(h))
     return y
 
 

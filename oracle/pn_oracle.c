@@ -247,6 +247,37 @@ void orc_rk4_step(const orc_sys *s, double y[12], double h)
     for (i = 0; i < 12; i++) y[i] = y[i] + h * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]) / 6.0;
 }
 
+/* Fifth-order explicit Runge-Kutta step with the tableau of Dormand & Prince
+ * (1980), fifth-order weights, fixed step (the paper's RK5 is not named). */
+void orc_rk5_step(const orc_sys *s, double y[12], double h)
+{
+    static const double a21 = 1.0 / 5.0;
+    static const double a31 = 3.0 / 40.0, a32 = 9.0 / 40.0;
+    static const double a41 = 44.0 / 45.0, a42 = -56.0 / 15.0, a43 = 32.0 / 9.0;
+    static const double a51 = 19372.0 / 6561.0, a52 = -25360.0 / 2187.0, a53 = 64448.0 / 6561.0,
+                        a54 = -212.0 / 729.0;
+    static const double a61 = 9017.0 / 3168.0, a62 = -355.0 / 33.0, a63 = 46732.0 / 5247.0,
+                        a64 = 49.0 / 176.0, a65 = -5103.0 / 18656.0;
+    static const double b1 = 35.0 / 384.0, b3 = 500.0 / 1113.0, b4 = 125.0 / 192.0,
+                        b5 = -2187.0 / 6784.0, b6 = 11.0 / 84.0;
+    double k1[12], k2[12], k3[12], k4[12], k5[12], k6[12], t[12];
+    int i;
+    orc_rhs(s, y, k1);
+    for (i = 0; i < 12; i++) t[i] = y[i] + h * (a21 * k1[i]);
+    orc_rhs(s, t, k2);
+    for (i = 0; i < 12; i++) t[i] = y[i] + h * (a31 * k1[i] + a32 * k2[i]);
+    orc_rhs(s, t, k3);
+    for (i = 0; i < 12; i++) t[i] = y[i] + h * (a41 * k1[i] + a42 * k2[i] + a43 * k3[i]);
+    orc_rhs(s, t, k4);
+    for (i = 0; i < 12; i++) t[i] = y[i] + h * (a51 * k1[i] + a52 * k2[i] + a53 * k3[i] + a54 * k4[i]);
+    orc_rhs(s, t, k5);
+    for (i = 0; i < 12; i++)
+        t[i] = y[i] + h * (a61 * k1[i] + a62 * k2[i] + a63 * k3[i] + a64 * k4[i] + a65 * k5[i]);
+    orc_rhs(s, t, k6);
+    for (i = 0; i < 12; i++)
+        y[i] = y[i] + h * (b1 * k1[i] + b3 * k3[i] + b4 * k4[i] + b5 * k5[i] + b6 * k6[i]);
+}
+
 /* --------------------------------------------------------------- integrals */
 void orc_integrals(const orc_sys *s, const double y[12], double out[7])
 {
@@ -437,13 +468,15 @@ static void integrate_one(const orc_config *cfg, const orc_sys *s, const double 
 
     for (k = 1; k <= nsteps; k++) {
         int it = 0;
-        orc_rk4_step(s, y, h);
+        if (cfg->rk_order == 5) orc_rk5_step(s, y, h);
+        else orc_rk4_step(s, y, h);
         if (cfg->correct) {
             last_kind = orc_correct(s, y, ref, cfg->newton_tol, cfg->newton_max, cfg->det_min, &it, 0);
             if (last_kind != ORC_CORR_OK) skips++;
             iters += it;
         }
-        orc_rk4_step(s, ys, h);
+        if (cfg->rk_order == 5) orc_rk5_step(s, ys, h);
+        else orc_rk4_step(s, ys, h);
         if (cfg->correct) {
             if (orc_correct(s, ys, refs, cfg->newton_tol, cfg->newton_max, cfg->det_min, &it, 0))
                 skips++;
@@ -524,7 +557,8 @@ int orc_trace(const double y0[12], double beta, double kappa1, double kappa2,
     reference_integrals(&s, y, ref);
     for (k = 1; k <= nsteps; k++) {
         int it;
-        orc_rk4_step(&s, y, h);
+        if (cfg->rk_order == 5) orc_rk5_step(&s, y, h);
+        else orc_rk4_step(&s, y, h);
         if (cfg->correct) orc_correct(&s, y, ref, cfg->newton_tol, cfg->newton_max, cfg->det_min, &it, 0);
         if (k % every == 0) {
             memcpy(trace + 12 * m, y, sizeof(y));

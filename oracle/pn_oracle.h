@@ -44,6 +44,7 @@ typedef struct {
     double fli_cap;       /* stop when the FLI reaches this value (<= 0: never) */
     double r_merge;       /* stop when |r| < r_merge (<= 0: never) */
     double r_escape;      /* stop when |r| > r_escape (<= 0: never) */
+    int rk_order;         /* 4: classical RK4; 5: Dormand-Prince fifth-order weights */
 } orc_config;
 
 /* Per-orbit final status (oracle's own numbering). */
@@ -76,6 +77,10 @@ void orc_rhs(const orc_sys *s, const double y[12], double dy[12]);
 
 /* One classical RK4 step of size h, in place. */
 void orc_rk4_step(const orc_sys *s, double y[12], double h);
+
+/* One fifth-order Runge-Kutta step (Dormand-Prince 1980 tableau, fifth-order
+ * weights, fixed step), in place. */
+void orc_rk5_step(const orc_sys *s, double y[12], double h);
 
 /* Integrals: out = (E, |J|, |S1|, |S2|, Jx, Jy, Jz). */
 void orc_integrals(const orc_sys *s, const double y[12], double out[7]);

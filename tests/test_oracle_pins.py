@@ -290,6 +290,34 @@ def test_rk4_energy_error_is_fourth_order(orc):
     assert 10 < err[0] / err[1] < 24
 
 
+def test_rk5_energy_error_is_fifth_order(orc):
+    """The fifth-order Dormand-Prince weights: halving h shrinks the global
+    energy error ~32x (a wrong tableau entry drops the order)."""
+    beta, y0 = paper_orbit("case_II_orbit_1")
+    s = orc.system(beta)
+    E0 = orc.hamiltonian(s, y0)
+    err = []
+    for h in (2.0, 1.0):
+        y = y0.copy()
+        for _ in range(int(round(400 / h))):
+            y = orc.rk5_step(s, y, h)
+        err.append(abs(orc.hamiltonian(s, y) - E0))
+    assert 22 < err[0] / err[1] < 45, err
+
+
+def test_rk5_kepler_closure(orc):
+    s = kepler_system(orc)
+    y0 = np.r_[10.0, 0, 0, 0, 0.28, 0, np.zeros(6)]
+    T = 2 * np.pi * (-1 / (2 * orc.hamiltonian(s, y0))) ** 1.5
+    errs = []
+    for N in (500, 1000):
+        y = y0.copy()
+        for _ in range(N):
+            y = orc.rk5_step(s, y, T / N)
+        errs.append(np.linalg.norm(y[:3] - y0[:3]) / 10.0)
+    assert errs[1] < 1e-9 and 22 < errs[0] / errs[1] < 45, errs
+
+
 # ------------------------------------------------------ manifold correction
 def test_correction_restores_all_six_integrals(orc):
     rng = np.random.default_rng(21)
