@@ -7,7 +7,7 @@
  * (arXiv:1802.00147):
  *   - H = H_N + H_1PN + H_2PN + H_SO(1.5PN) + H_S1S2(2PN) [+ H_QM]      Sec. 2, Eqs. 1-5
  *   - Hamilton's equations and spin precession                          Eqs. 6-9
- *   - a fixed-step explicit Runge-Kutta step (classical RK4)            Sec. 3A
+ *   - a fixed-step explicit Runge-Kutta step (RK4, or RK5)              Sec. 3A
  *   - manifold correction after every step: spin lengths (Eq. 10), then
  *     dual scaling p = alpha p*, r = beta r* with (alpha, beta) from E and
  *     |J| by Newton's method                                            Eqs. 11-13, Sec. 3A
@@ -82,6 +82,8 @@ typedef struct scan_params {
     int use_ss;              /* 2PN S1-S2 spin-spin, Eq. 3 (default 1) */
     int use_qm;              /* spin-induced quadrupole-monopole, Eqs. 4-5 (default 0) */
     int correct;             /* manifold correction after every step (default 1) */
+    int rk_order;            /* base integrator: 4 classical RK4 (default), 5 fifth-order Runge-Kutta
+                                with the Dormand-Prince (1980) weights (the paper's RK5, Sec. 3A) */
     double newton_tol;       /* Newton stop: |d alpha|, |d beta| <= tol (default 1e-10, Sec. 3A) */
     int newton_max;          /* Newton iteration cap (default 50) */
     double newton_det_min;   /* a step whose dual-scaling Jacobian has |det| <= det_min

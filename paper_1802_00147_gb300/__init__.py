@@ -43,7 +43,7 @@ class ScanParams(_ct.Structure):
         ("n", _ct.c_int64),
         ("beta_m", _ct.c_void_p), ("kappa1", _ct.c_void_p), ("kappa2", _ct.c_void_p),
         ("pn_order", _ct.c_int), ("use_so", _ct.c_int), ("use_ss", _ct.c_int), ("use_qm", _ct.c_int),
-        ("correct", _ct.c_int),
+        ("correct", _ct.c_int), ("rk_order", _ct.c_int),
         ("newton_tol", _ct.c_double), ("newton_max", _ct.c_int), ("newton_det_min", _ct.c_double),
         ("fli_d0", _ct.c_double), ("fli_renorm_steps", _ct.c_int), ("fli_thresh", _ct.c_double),
         ("fli_cap", _ct.c_double), ("r_merge", _ct.c_double), ("r_escape", _ct.c_double),

@@ -171,7 +171,7 @@ int reset_queue(scan_handle* h, cudaStream_t st)
 
 int queue_grid(scan_handle* h, int block, int bps, int minb)
 {
-    int occ = queue_blocks_per_sm(block, h->base.flags.use_qm != 0, minb);
+    int occ = queue_blocks_per_sm(block, h->base.flags.use_qm != 0, minb, h->base.rk_order);
     if (occ <= 0) occ = 1;
     if (bps <= 0 || bps > occ) bps = occ;
     return h->num_sms * bps;
@@ -234,7 +234,7 @@ bool same_run(const RunCfg& a, const RunCfg& b)
     return a.flags.pn_order == b.flags.pn_order && a.flags.use_so == b.flags.use_so &&
            a.flags.use_ss == b.flags.use_ss && a.flags.use_qm == b.flags.use_qm &&
            a.newton.tol == b.newton.tol && a.newton.max_iter == b.newton.max_iter &&
-           a.newton.det_min == b.newton.det_min && a.correct == b.correct && a.h == b.h &&
+           a.newton.det_min == b.newton.det_min && a.correct == b.correct && a.rk_order == b.rk_order && a.h == b.h &&
            a.d0 == b.d0 && a.renorm == b.renorm && a.fli_cap == b.fli_cap &&
            a.rmerge2 == b.rmerge2 && a.rescape2 == b.rescape2 && a.nstep_base == b.nstep_base &&
            a.nsteps == b.nsteps && a.wait_limit_ns == b.wait_limit_ns && a.stall_group == b.stall_group &&
@@ -281,6 +281,7 @@ int scan_params_default(scan_params* p)
     p->use_ss = 1;
     p->use_qm = 0;
     p->correct = 1;
+    p->rk_order = 4;
     p->newton_tol = 1e-10;
     p->newton_max = 50;
     p->newton_det_min = 1e-5;
@@ -309,6 +310,7 @@ int scan_create(const scan_params* p, scan_handle** out)
     if (p->block_size && (p->block_size < 32 || p->block_size > 128 || p->block_size % 32)) return PNSCAN_ERR_ARG;
     if (p->chunk_steps < 0 || p->blocks_per_sm < 0 || p->queue_wait_limit_ms < 0) return PNSCAN_ERR_ARG;
     if (p->register_variant != 0 && p->register_variant != 2 && p->register_variant != 3) return PNSCAN_ERR_ARG;
+    if (p->rk_order != 0 && p->rk_order != 4 && p->rk_order != 5) return PNSCAN_ERR_ARG;
     if (p->schedule < 0 || p->schedule > 3) return PNSCAN_ERR_ARG;
     if ((p->alloc_fn == nullptr) != (p->free_fn == nullptr)) return PNSCAN_ERR_ARG;
     int ndev = 0;
@@ -390,6 +392,7 @@ int scan_create(const scan_params* p, scan_handle** out)
     b.newton.max_iter = p->newton_max;
     b.newton.det_min = p->newton_det_min;
     b.correct = p->correct != 0;
+    b.rk_order = p->rk_order == 5 ? 5 : 4;
     b.d0 = p->fli_d0;
     b.renorm = p->fli_renorm_steps;
     b.fli_cap = p->fli_cap;

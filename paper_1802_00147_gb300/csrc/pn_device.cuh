@@ -299,6 +299,60 @@ __device__ __forceinline__ void rk4_step(const C& c, Vec12& y, double h)
     for (int i = 0; i < 12; i++) yv[i] = fma(h6, kv[i], av[i]);
 }
 
+// Fifth-order Runge-Kutta step, Dormand & Prince (1980) tableau with the
+// fifth-order weights (b7 = 0, so six derivative evaluations).  The stage
+// derivatives go to shared memory (kst: 6 x 12 planes of `stride` doubles,
+// this thread's column) so the registers hold only y and the stage state.
+template <bool QM, class C>
+__device__ __forceinline__ void rk5_step(const C& c, Vec12& y, double h, double* kst, int stride)
+{
+    const double a21 = 1.0 / 5.0;
+    const double a31 = 3.0 / 40.0, a32 = 9.0 / 40.0;
+    const double a41 = 44.0 / 45.0, a42 = -56.0 / 15.0, a43 = 32.0 / 9.0;
+    const double a51 = 19372.0 / 6561.0, a52 = -25360.0 / 2187.0, a53 = 64448.0 / 6561.0, a54 = -212.0 / 729.0;
+    const double a61 = 9017.0 / 3168.0, a62 = -355.0 / 33.0, a63 = 46732.0 / 5247.0, a64 = 49.0 / 176.0,
+                 a65 = -5103.0 / 18656.0;
+    const double b1 = 35.0 / 384.0, b3 = 500.0 / 1113.0, b4 = 125.0 / 192.0, b5 = -2187.0 / 6784.0,
+                 b6 = 11.0 / 84.0;
+    const double A[6][5] = {{0, 0, 0, 0, 0},
+                            {a21, 0, 0, 0, 0},
+                            {a31, a32, 0, 0, 0},
+                            {a41, a42, a43, 0, 0},
+                            {a51, a52, a53, a54, 0},
+                            {a61, a62, a63, a64, a65}};
+    const double B[6] = {b1, 0.0, b3, b4, b5, b6};
+    double* yv = &y.r[0];
+    Vec12 st, k;
+    double* sv = &st.r[0];
+    double* kv = &k.r[0];
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+        if (j == 0) {
+            rhs<QM, C>(c, y, k);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 12; i++) {
+                double acc = yv[i];
+#pragma unroll
+                for (int m = 0; m < 5; m++)
+                    if (m < j && A[j][m] != 0.0) acc = fma(h * A[j][m], kst[(m * 12 + i) * stride], acc);
+                sv[i] = acc;
+            }
+            rhs<QM, C>(c, st, k);
+        }
+#pragma unroll
+        for (int i = 0; i < 12; i++) kst[(j * 12 + i) * stride] = kv[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 12; i++) {
+        double acc = yv[i];
+#pragma unroll
+        for (int m = 0; m < 6; m++)
+            if (B[m] != 0.0) acc = fma(h * B[m], kst[(m * 12 + i) * stride], acc);
+        yv[i] = acc;
+    }
+}
+
 // ------------------------------------------------------ manifold correction
 enum CorrKind : int { CORR_DUAL = 0, CORR_NONE = 1, CORR_VELOCITY = 2 };
 

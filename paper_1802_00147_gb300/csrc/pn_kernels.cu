@@ -106,20 +106,25 @@ __device__ __forceinline__ Coef load_coef(const DevState& S, int64_t i, const Fl
 // the shadow, termination tests, and every `renorm` steps the FLI
 // renormalisation (acc += log10(d/d0), shadow pulled back to distance d0 and
 // given its own reference integrals).
-template <bool QM, class C>
+template <bool QM, int RK, class C>
 __device__ __forceinline__ void advance(const RunCfg& rc, const C& c, Orbit& o, int32_t step_end)
 {
+    extern __shared__ double kst_dyn[];      // RK5 stage derivatives (rk_order 5 only)
+    double* kst = kst_dyn + threadIdx.x;
+    const int kstride = (int)blockDim.x;
     const double t0 = o.t;
     const int32_t n0 = o.nstep;
     while (o.nstep < step_end) {
-        rk4_step<QM, C>(c, o.y, rc.h);
+        if (RK == 5) rk5_step<QM, C>(c, o.y, rc.h, kst, kstride);
+        else rk4_step<QM, C>(c, o.y, rc.h);
         if (rc.correct) {
             int kind;
             o.iters += correct<QM, C>(c, o.y, o.ref, rc.newton, &kind);
             o.skips += kind != CORR_DUAL;
             o.last_kind = kind;
         }
-        rk4_step<QM, C>(c, o.ys, rc.h);
+        if (RK == 5) rk5_step<QM, C>(c, o.ys, rc.h, kst, kstride);
+        else rk4_step<QM, C>(c, o.ys, rc.h);
         if (rc.correct) {
             int kind;
             o.iters += correct<QM, C>(c, o.ys, o.refs, rc.newton, &kind);
@@ -217,7 +222,7 @@ __global__ void k_init(DevState S, RunCfg rc)
 
 // ----------------------------------------------------- static integrator
 // One orbit per thread for the whole run.
-template <bool QM>
+template <bool QM, int RK>
 __global__ void __launch_bounds__(128) k_integrate_static(DevState S, RunCfg rc)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -229,7 +234,7 @@ __global__ void __launch_bounds__(128) k_integrate_static(DevState S, RunCfg rc)
     o.status = ORBIT_RUNNING;
     const Coef c = load_coef<false>(S, i, rc.flags);
     const int32_t end = rc.nstep_base + rc.nsteps;
-    advance<QM, Coef>(rc, c, o, end);
+    advance<QM, RK, Coef>(rc, c, o, end);
     if (o.status == ORBIT_RUNNING && o.nstep == rc.final_step) o.status = ORBIT_DONE;
     store_orbit(S, i, o);
 }
@@ -264,7 +269,7 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
 
 // SMEM: keep the per-orbit constants in shared memory (one plane per constant)
 // instead of registers, which is what lets MINB = 3 blocks fit without spills.
-template <bool QM, int MINB, bool SMEM>
+template <bool QM, int MINB, bool SMEM, int RK>
 __global__ void __launch_bounds__(128, MINB) k_integrate_queue(DevState S, RunCfg rc, QueueState q, int chunk,
                                                                 int use_order)
 {
@@ -313,10 +318,10 @@ __global__ void __launch_bounds__(128, MINB) k_integrate_queue(DevState S, RunCf
 #pragma unroll
                     for (int k = 0; k < NCOEF; k++) mine[k * (int)blockDim.x] = cf.v[k];
                     const CoefShared cs{mine, (int)blockDim.x};
-                    advance<QM, CoefShared>(rc, cs, o, end);
+                    advance<QM, RK, CoefShared>(rc, cs, o, end);
                 } else {
                     const Coef cf = load_coef<true>(S, i, rc.flags);
-                    advance<QM, Coef>(rc, cf, o, end);
+                    advance<QM, RK, Coef>(rc, cf, o, end);
                 }
                 if (o.status == ORBIT_RUNNING && o.nstep == end_run) o.status = ORBIT_DONE;
                 store_orbit(S, i, o);
@@ -511,35 +516,56 @@ cudaError_t launch_init(DevState S, RunCfg rc, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <int RK>
+static void launch_static(DevState S, RunCfg rc, int block, cudaStream_t st)
+{
+    const size_t sm = RK == 5 ? rk5_smem_bytes(block) : 0;
+    if (sm > 48 * 1024) {
+        cudaFuncSetAttribute(k_integrate_static<true, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_integrate_static<false, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    }
+    if (rc.flags.use_qm) k_integrate_static<true, RK><<<grid_for(S.n, block), block, sm, st>>>(S, rc);
+    else k_integrate_static<false, RK><<<grid_for(S.n, block), block, sm, st>>>(S, rc);
+}
+
 cudaError_t launch_integrate_static(DevState S, RunCfg rc, int block, cudaStream_t st)
 {
     if (S.n == 0 || rc.nsteps <= 0) return cudaSuccess;
     if (block <= 0 || block > 128 || block % 32) return cudaErrorInvalidValue;
-    if (rc.flags.use_qm) k_integrate_static<true><<<grid_for(S.n, block), block, 0, st>>>(S, rc);
-    else k_integrate_static<false><<<grid_for(S.n, block), block, 0, st>>>(S, rc);
+    if (rc.rk_order == 5) launch_static<5>(S, rc, block, st);
+    else launch_static<4>(S, rc, block, st);
     return cudaGetLastError();
 }
 
-template <int MINB, bool SMEM>
+template <int MINB, bool SMEM, int RK>
 static int occupancy_queue(int block, bool qm)
 {
+    const size_t sm = RK == 5 ? rk5_smem_bytes(block) : 0;
     int nb = 0;
-    if (qm) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<true, MINB, SMEM>, block, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<false, MINB, SMEM>, block, 0);
+    if (sm > 48 * 1024) {
+        cudaFuncSetAttribute(k_integrate_queue<true, MINB, SMEM, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_integrate_queue<false, MINB, SMEM, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    }
+    if (qm) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<true, MINB, SMEM, RK>, block, sm);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<false, MINB, SMEM, RK>, block, sm);
     return nb;
 }
 
-int queue_blocks_per_sm(int block, bool qm, int minb)
+// Compiled variants: RK4 with the per-orbit constants in registers (2 blocks
+// per SM) or in shared memory (3 blocks per SM); RK5 with them in registers.
+int queue_blocks_per_sm(int block, bool qm, int minb, int rk_order)
 {
-    return minb == 3 ? occupancy_queue<3, true>(block, qm) : occupancy_queue<2, false>(block, qm);
+    if (rk_order == 5) return occupancy_queue<2, false, 5>(block, qm);
+    return minb == 3 ? occupancy_queue<3, true, 4>(block, qm) : occupancy_queue<2, false, 4>(block, qm);
 }
 
-template <int MINB, bool SMEM>
+template <int MINB, bool SMEM, int RK>
 static void launch_queue(DevState S, RunCfg rc, QueueState q, int block, int grid, int chunk, int use_order,
                          cudaStream_t st)
 {
-    if (rc.flags.use_qm) k_integrate_queue<true, MINB, SMEM><<<grid, block, 0, st>>>(S, rc, q, chunk, use_order);
-    else k_integrate_queue<false, MINB, SMEM><<<grid, block, 0, st>>>(S, rc, q, chunk, use_order);
+    const size_t sm = RK == 5 ? rk5_smem_bytes(block) : 0;
+    if (rc.flags.use_qm) k_integrate_queue<true, MINB, SMEM, RK><<<grid, block, sm, st>>>(S, rc, q, chunk, use_order);
+    else k_integrate_queue<false, MINB, SMEM, RK><<<grid, block, sm, st>>>(S, rc, q, chunk, use_order);
 }
 
 cudaError_t launch_integrate_queue(DevState S, RunCfg rc, QueueState q, int block, int grid,
@@ -547,8 +573,9 @@ cudaError_t launch_integrate_queue(DevState S, RunCfg rc, QueueState q, int bloc
 {
     if (S.n == 0 || rc.nsteps <= 0) return cudaSuccess;
     if (block <= 0 || block > 128 || block % 32 || grid <= 0 || chunk <= 0) return cudaErrorInvalidValue;
-    if (minb == 3) launch_queue<3, true>(S, rc, q, block, grid, chunk, use_order, st);
-    else launch_queue<2, false>(S, rc, q, block, grid, chunk, use_order, st);
+    if (rc.rk_order == 5) launch_queue<2, false, 5>(S, rc, q, block, grid, chunk, use_order, st);
+    else if (minb == 3) launch_queue<3, true, 4>(S, rc, q, block, grid, chunk, use_order, st);
+    else launch_queue<2, false, 4>(S, rc, q, block, grid, chunk, use_order, st);
     return cudaGetLastError();
 }
 

@@ -45,6 +45,7 @@ struct RunCfg {
     Flags flags;
     NewtonCfg newton;
     int correct;           // apply the manifold correction each step
+    int rk_order;          // 4: classical RK4; 5: Dormand-Prince fifth order
     double h;              // step size
     double d0;             // FLI separation
     int renorm;            // renormalise every `renorm` steps (<= 0: never)
@@ -68,6 +69,10 @@ struct QueueState {
     int* group_done;            // [groups] chunks finished per group
     int* count;                 // [2] compacting schedule: orbits in order / order_next
 };
+
+// Dynamic shared memory of the integrators for the RK5 stage derivatives
+// (6 x 12 doubles per thread).
+inline size_t rk5_smem_bytes(int block) { return (size_t)6 * 12 * block * sizeof(double); }
 
 struct Summary {                // scan-level reduction (device layout)
     unsigned long long n_chaotic;
@@ -93,7 +98,7 @@ cudaError_t launch_integrate_static(DevState S, RunCfg rc, int block, cudaStream
 // minb: variant of the queue kernel: 2 resident 128-thread blocks per SM
 // with the per-orbit constants in registers (up to 255 per thread), or 3
 // with them in shared memory (168 registers)
-int queue_blocks_per_sm(int block, bool qm, int minb);
+int queue_blocks_per_sm(int block, bool qm, int minb, int rk_order);
 cudaError_t launch_integrate_queue(DevState S, RunCfg rc, QueueState q, int block, int grid,
                                    int chunk, int minb, int use_order, cudaStream_t st);
 // Compacting schedule: order_next <- running orbits of order (or of all

@@ -8,6 +8,12 @@ reach t_end is reported with and without the manifold correction
 (Eqs. 10-13).
 
     python -m paper_1802_00147_gb300.studies qm [--n 1024] [--subset 65536] [--t-end 1e5]
+
+The paper's own scans (Sec. 3C, Figs. 6-7), with the fifth-order base
+integrator and the paper's FLI threshold 5.8; the FLI maps are written as
+.npy files (no graphics):
+
+    python -m paper_1802_00147_gb300.studies paper [--t-end 1e5] [--out DIR]
 """
 import argparse
 import json
@@ -64,15 +70,50 @@ def qm_drift_study(n=1024, subset=0, t_end=1.0e5, h=0.5, seed=5):
     return report
 
 
+def paper_scans(t_end=1.0e5, h=1.0, thr=5.8, out_dir=None, n=314):
+    """Fig. 6 (theta2 scans at theta1 = pi/2 and 0) and Fig. 7 (theta1-theta2
+    plane) with RK5; no merger / escape cut-off (the paper integrates every
+    orbit to t_end and discards unbound ones afterwards)."""
+    import os
+    import torch
+    runs = {"fig6a_theta1_pi2": W.paper_theta2_scan(np.pi / 2, n), "fig6b_theta1_0": W.paper_theta2_scan(0.0, n),
+            "fig7_theta1_theta2": W.paper_theta12_scan(n)}
+    report = {"t_end": t_end, "h": h, "rk_order": 5, "fli_threshold": thr}
+    for name, cells in runs.items():
+        cd = torch.as_tensor(np.ascontiguousarray(cells[:, :9]), device="cuda")
+        with Scan(None, device=True, n=cells.shape[0], rk_order=5, r_merge=0.0, r_escape=0.0) as s:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.setup(cd)
+            s.run(t_end, h)
+            out = s.read()
+            dt = time.perf_counter() - t0
+        fli = out["fli"].cpu().numpy()
+        r = np.linalg.norm(out["states"].cpu().numpy()[:, :3], axis=1)
+        bound = r < 100.0
+        if out_dir:
+            os.makedirs(out_dir, exist_ok=True)
+            np.save(os.path.join(out_dir, name + "_fli.npy"), fli.reshape(-1, n) if fli.size > n else fli)
+            np.save(os.path.join(out_dir, name + "_r_end.npy"), r)
+        report[name] = {"orbits": int(fli.size), "seconds": dt, "bound_frac": float(bound.mean()),
+                        "chaotic_frac_bound": float((fli[bound] > thr).mean()) if bound.any() else None,
+                        "fli_median_bound": float(np.median(fli[bound])) if bound.any() else None}
+    return report
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["qm"])
+    ap.add_argument("study", choices=["qm", "paper"])
+    ap.add_argument("--out", default=None)
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--subset", type=int, default=0)
     ap.add_argument("--t-end", type=float, default=1.0e5)
     ap.add_argument("--h", type=float, default=0.5)
     a = ap.parse_args()
-    print(json.dumps(qm_drift_study(a.n, a.subset, a.t_end, a.h)), flush=True)
+    if a.study == "qm":
+        print(json.dumps(qm_drift_study(a.n, a.subset, a.t_end, a.h)), flush=True)
+    else:
+        print(json.dumps(paper_scans(a.t_end, 1.0, out_dir=a.out)), flush=True)
 
 
 if __name__ == "__main__":

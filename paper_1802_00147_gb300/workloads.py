@@ -109,3 +109,35 @@ def subset(cells, m, seed=6):
     rng = np.random.Generator(np.random.PCG64(seed))
     idx = np.sort(rng.choice(cells.shape[0], size=min(m, cells.shape[0]), replace=False))
     return cells[idx], idx
+
+
+def paper_cells(x0, p_y, beta, theta1, theta2, chi=1.0):
+    """Cells of the paper's own scans: r = (x0, 0, 0), p = (0, p_y, 0), both
+    spins in the x-z plane at polar angles theta1, theta2 (arrays), chi_i = chi."""
+    theta1 = np.asarray(theta1, dtype=np.float64)
+    theta2 = np.asarray(theta2, dtype=np.float64)
+    theta1, theta2 = np.broadcast_arrays(theta1, theta2)
+    n = theta1.size
+    c = np.zeros((n, NFIELDS))
+    c[:, X0] = x0
+    c[:, PFAC] = p_y * np.sqrt(x0)
+    c[:, TH1] = theta1.ravel()
+    c[:, TH2] = theta2.ravel()
+    c[:, BETA] = beta
+    c[:, CHI1] = c[:, CHI2] = chi
+    c[:, KAP1] = c[:, KAP2] = 1.0
+    return c
+
+
+def paper_theta2_scan(theta1, n=314):
+    """Sec. 3C, Fig. 6: theta2 from 0 in steps of 0.01 (314 orbits), theta1
+    fixed, (beta, r, p) = (1/3, 5.65, 0.765)."""
+    return paper_cells(5.65, 0.765, 1.0 / 3.0, theta1, 0.01 * np.arange(n))
+
+
+def paper_theta12_scan(n=314):
+    """Sec. 3C, Fig. 7: the (theta1, theta2) plane, both from 0 in steps of 0.01
+    (314 x 314 orbits), (beta, r, p) = (1, 10.14, 0.365), chi = 1."""
+    t = 0.01 * np.arange(n)
+    T1, T2 = np.meshgrid(t, t, indexing="ij")
+    return paper_cells(10.14, 0.365, 1.0, T1.ravel(), T2.ravel())

@@ -196,7 +196,9 @@ def test_qm_parity(pn):
                                   dict(use_ss=0),
                                   dict(correct=0),
                                   dict(r_merge=0.0, r_escape=0.0, fli_renorm_steps=37),
-                                  dict(newton_det_min=0.0)])
+                                  dict(newton_det_min=0.0),
+                                  dict(rk_order=5),
+                                  dict(rk_order=5, schedule=1)])
 def test_flag_variants_parity(pn, opts):
     check(pn, W.uneven_batch(n=96, seed=12), 400, **opts)
 
