@@ -89,6 +89,9 @@ typedef struct scan_params {
     double newton_det_min;   /* a step whose dual-scaling Jacobian has |det| <= det_min
                                 (|J11 J22| + |J12 J21|) restores E by scaling p alone
                                 (default 1e-5) */
+    int newton_apply_small;  /* 1: apply a Newton step, then stop if it was within newton_tol (default);
+                                0: stop before applying a step already within newton_tol (the rule
+                                under which Fig. 4's tolerance dependence appears) */
     double fli_d0;           /* separation of the two trajectories (default 1e-9) */
     int fli_renorm_steps;    /* renormalise every this many steps (default 100; <= 0: never) */
     double fli_thresh;       /* FLI above this is chaotic (default 6) */

@@ -24,6 +24,7 @@ class Config(_ct.Structure):
         ("newton_tol", _ct.c_double), ("newton_max", _ct.c_int), ("det_min", _ct.c_double),
         ("fli_d0", _ct.c_double), ("fli_renorm", _ct.c_int), ("fli_cap", _ct.c_double),
         ("r_merge", _ct.c_double), ("r_escape", _ct.c_double), ("rk_order", _ct.c_int),
+        ("newton_apply_small", _ct.c_int),
     ]
 
 
@@ -37,9 +38,9 @@ class Sys(_ct.Structure):
 
 def config(pn_order=2, use_so=1, use_ss=1, use_qm=0, correct=1, newton_tol=1e-10,
            newton_max=50, det_min=1e-5, fli_d0=1e-9, fli_renorm=100, fli_cap=0.0,
-           r_merge=6.0, r_escape=1e3, rk_order=4):
+           r_merge=6.0, r_escape=1e3, rk_order=4, newton_apply_small=1):
     return Config(pn_order, use_so, use_ss, use_qm, correct, newton_tol, newton_max,
-                  det_min, fli_d0, fli_renorm, fli_cap, r_merge, r_escape, rk_order)
+                  det_min, fli_d0, fli_renorm, fli_cap, r_merge, r_escape, rk_order, newton_apply_small)
 
 
 def lib():

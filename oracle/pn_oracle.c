@@ -299,6 +299,13 @@ int orc_correct(const orc_sys *s, double y[12], const double ref[4],
                 double newton_tol, int newton_max, double det_min,
                 int *iters, double alpha_beta[2])
 {
+    return orc_correct_rule(s, y, ref, newton_tol, newton_max, det_min, 1, iters, alpha_beta);
+}
+
+int orc_correct_rule(const orc_sys *s, double y[12], const double ref[4],
+                     double newton_tol, int newton_max, double det_min, int apply_small,
+                     int *iters, double alpha_beta[2])
+{
     double rs[3], ps[3], yb[12], g[12];
     double alpha = 1.0, beta = 1.0;
     int it, i, converged = 0;
@@ -347,6 +354,12 @@ int orc_correct(const orc_sys *s, double y[12], const double ref[4],
         if (!(fabs(det) > det_min * (fabs(A * D) + fabs(B * C))) || !isfinite(det)) break;
         da = (F1 * D - B * F2) / det;
         db = (A * F2 - C * F1) / det;
+        /* stopping rule: apply the step and then test it (default), or stop
+         * before applying a step already within the tolerance */
+        if (!apply_small && fabs(da) <= newton_tol && fabs(db) <= newton_tol) {
+            converged = 1;
+            break;
+        }
         alpha = alpha - da;
         beta = beta - db;
         if (!isfinite(alpha) || !isfinite(beta)) break;
@@ -384,6 +397,10 @@ int orc_correct(const orc_sys *s, double y[12], const double ref[4],
             A = dot3(g2 + 3, ps);             /* dH/da = dH/dp . p* */
             da = F / A;
             if (!isfinite(da)) break;
+            if (!apply_small && fabs(da) <= newton_tol) {
+                ok = 1;
+                break;
+            }
             a = a - da;
             if (fabs(da) <= newton_tol) {
                 ok = 1;
@@ -471,14 +488,16 @@ static void integrate_one(const orc_config *cfg, const orc_sys *s, const double 
         if (cfg->rk_order == 5) orc_rk5_step(s, y, h);
         else orc_rk4_step(s, y, h);
         if (cfg->correct) {
-            last_kind = orc_correct(s, y, ref, cfg->newton_tol, cfg->newton_max, cfg->det_min, &it, 0);
+            last_kind = orc_correct_rule(s, y, ref, cfg->newton_tol, cfg->newton_max, cfg->det_min,
+                                         cfg->newton_apply_small, &it, 0);
             if (last_kind != ORC_CORR_OK) skips++;
             iters += it;
         }
         if (cfg->rk_order == 5) orc_rk5_step(s, ys, h);
         else orc_rk4_step(s, ys, h);
         if (cfg->correct) {
-            if (orc_correct(s, ys, refs, cfg->newton_tol, cfg->newton_max, cfg->det_min, &it, 0))
+            if (orc_correct_rule(s, ys, refs, cfg->newton_tol, cfg->newton_max, cfg->det_min,
+                                 cfg->newton_apply_small, &it, 0))
                 skips++;
             iters += it;
         }
@@ -559,7 +578,9 @@ int orc_trace(const double y0[12], double beta, double kappa1, double kappa2,
         int it;
         if (cfg->rk_order == 5) orc_rk5_step(&s, y, h);
         else orc_rk4_step(&s, y, h);
-        if (cfg->correct) orc_correct(&s, y, ref, cfg->newton_tol, cfg->newton_max, cfg->det_min, &it, 0);
+        if (cfg->correct)
+            orc_correct_rule(&s, y, ref, cfg->newton_tol, cfg->newton_max, cfg->det_min,
+                             cfg->newton_apply_small, &it, 0);
         if (k % every == 0) {
             memcpy(trace + 12 * m, y, sizeof(y));
             m++;

@@ -45,6 +45,8 @@ typedef struct {
     double r_merge;       /* stop when |r| < r_merge (<= 0: never) */
     double r_escape;      /* stop when |r| > r_escape (<= 0: never) */
     int rk_order;         /* 4: classical RK4; 5: Dormand-Prince fifth-order weights */
+    int newton_apply_small; /* 1: apply a Newton step, then stop if it was within newton_tol;
+                               0: stop before applying a step already within newton_tol */
 } orc_config;
 
 /* Per-orbit final status (oracle's own numbering). */
@@ -94,6 +96,10 @@ void orc_integrals(const orc_sys *s, const double y[12], double out[7]);
 int orc_correct(const orc_sys *s, double y[12], const double ref[4],
                 double newton_tol, int newton_max, double det_min,
                 int *iters, double alpha_beta[2]);
+/* The same with the stopping rule as a parameter (apply_small as in orc_config). */
+int orc_correct_rule(const orc_sys *s, double y[12], const double ref[4],
+                     double newton_tol, int newton_max, double det_min, int apply_small,
+                     int *iters, double alpha_beta[2]);
 
 /* Initial conditions of a scan cell: cell = (x0, pfac, theta1, phi1,
  * theta2, phi2, beta, chi1, chi2).  r = (x0,0,0), p = (0, pfac/sqrt(x0), 0),

@@ -45,6 +45,7 @@ class ScanParams(_ct.Structure):
         ("pn_order", _ct.c_int), ("use_so", _ct.c_int), ("use_ss", _ct.c_int), ("use_qm", _ct.c_int),
         ("correct", _ct.c_int), ("rk_order", _ct.c_int),
         ("newton_tol", _ct.c_double), ("newton_max", _ct.c_int), ("newton_det_min", _ct.c_double),
+        ("newton_apply_small", _ct.c_int),
         ("fli_d0", _ct.c_double), ("fli_renorm_steps", _ct.c_int), ("fli_thresh", _ct.c_double),
         ("fli_cap", _ct.c_double), ("r_merge", _ct.c_double), ("r_escape", _ct.c_double),
         ("device_ptrs", _ct.c_int), ("cuda_stream", _ct.c_void_p),

@@ -234,7 +234,8 @@ bool same_run(const RunCfg& a, const RunCfg& b)
     return a.flags.pn_order == b.flags.pn_order && a.flags.use_so == b.flags.use_so &&
            a.flags.use_ss == b.flags.use_ss && a.flags.use_qm == b.flags.use_qm &&
            a.newton.tol == b.newton.tol && a.newton.max_iter == b.newton.max_iter &&
-           a.newton.det_min == b.newton.det_min && a.correct == b.correct && a.rk_order == b.rk_order && a.h == b.h &&
+           a.newton.det_min == b.newton.det_min && a.newton.apply_small == b.newton.apply_small &&
+           a.correct == b.correct && a.rk_order == b.rk_order && a.h == b.h &&
            a.d0 == b.d0 && a.renorm == b.renorm && a.fli_cap == b.fli_cap &&
            a.rmerge2 == b.rmerge2 && a.rescape2 == b.rescape2 && a.nstep_base == b.nstep_base &&
            a.nsteps == b.nsteps && a.wait_limit_ns == b.wait_limit_ns && a.stall_group == b.stall_group &&
@@ -285,6 +286,7 @@ int scan_params_default(scan_params* p)
     p->newton_tol = 1e-10;
     p->newton_max = 50;
     p->newton_det_min = 1e-5;
+    p->newton_apply_small = 1;
     p->fli_d0 = 1e-9;
     p->fli_renorm_steps = 100;
     p->fli_thresh = 6.0;
@@ -391,6 +393,7 @@ int scan_create(const scan_params* p, scan_handle** out)
     b.newton.tol = p->newton_tol;
     b.newton.max_iter = p->newton_max;
     b.newton.det_min = p->newton_det_min;
+    b.newton.apply_small = p->newton_apply_small != 0;
     b.correct = p->correct != 0;
     b.rk_order = p->rk_order == 5 ? 5 : 4;
     b.d0 = p->fli_d0;

@@ -360,6 +360,7 @@ struct NewtonCfg {
     double tol;       // stop when |d alpha| <= tol and |d beta| <= tol (Sec. 3A: 1e-10)
     int max_iter;     // iteration cap
     double det_min;   // relative-determinant guard of the singular scaling
+    int apply_small;  // 1: apply a step, then stop if it was within tol; 0: stop before applying it
 };
 
 // Eq. 10, then Eqs. 11-13: p = alpha p*, r = beta r* with (alpha, beta) from
@@ -444,10 +445,15 @@ __device__ __forceinline__ int correct(const C& c, Vec12& y, const Ref& ref,
             const double rd = __drcp_rn(det);
             const double da = fma(F1, dJ, Hu * F2) * rd;
             const double db = fma(Ha, F2, -dJ * F1) * rd;
-            al -= da;
-            be -= db;
-            if (fabs(da) <= nc.tol && fabs(db) <= nc.tol) conv = true;
-            else if (!(fabs(al) < 1e300) || !(fabs(be) < 1e300)) stop = true;   // diverged
+            const bool small = fabs(da) <= nc.tol && fabs(db) <= nc.tol;
+            if (small && !nc.apply_small) {
+                conv = true;
+            } else {
+                al -= da;
+                be -= db;
+                if (small) conv = true;
+                else if (!(fabs(al) < 1e300) || !(fabs(be) < 1e300)) stop = true;   // diverged
+            }
         } else {
             stop = true;   // singular: straight to velocity scaling
         }
@@ -477,9 +483,11 @@ __device__ __forceinline__ int correct(const C& c, Vec12& y, const Ref& ref,
         const double rd = __drcp_rn(det);
         const double da = fma(F1, Jb, -Hb * F2) * rd;
         const double db = fma(Ha, F2, -Ja * F1) * rd;
+        const bool small = fabs(da) <= nc.tol && fabs(db) <= nc.tol;
+        if (small && !nc.apply_small) { conv = true; break; }
         al -= da;
         be -= db;
-        if (fabs(da) <= nc.tol && fabs(db) <= nc.tol) { conv = true; break; }
+        if (small) { conv = true; break; }
         if (!(fabs(al) < 1e300) || !(fabs(be) < 1e300)) break;
     }
     if (conv) {
@@ -502,6 +510,7 @@ __device__ __forceinline__ int correct(const C& c, Vec12& y, const Ref& ref,
         const double Ha = fma(2.0 * a, fma(a2s, fma(a2s, A6x3, A4x2), A2) + fma(a2s, B4x2, B2) + C2, E1);
         const double da = (H - ref.E) / Ha;
         if (!(fabs(da) <= 1.7976931348623157e308)) break;
+        if (!nc.apply_small && fabs(da) <= nc.tol) { ok = true; break; }
         a -= da;
         if (fabs(da) <= nc.tol) { ok = true; break; }
     }

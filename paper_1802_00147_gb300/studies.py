@@ -14,6 +14,13 @@ integrator and the paper's FLI threshold 5.8; the FLI maps are written as
 .npy files (no graphics):
 
     python -m paper_1802_00147_gb300.studies paper [--t-end 1e5] [--out DIR]
+
+Newton-tolerance ablation (Sec. 3A, Fig. 4) over a scan grid: the energy
+drift at t_end for eps = 1e-6, 1e-8, 1e-10 under both Newton stopping rules
+(apply a step and then test it; stop before applying a step within eps),
+RK5 at h = 1:
+
+    python -m paper_1802_00147_gb300.studies newton [--n 64] [--t-end 1e4]
 """
 import argparse
 import json
@@ -101,9 +108,33 @@ def paper_scans(t_end=1.0e5, h=1.0, thr=5.8, out_dir=None, n=314):
     return report
 
 
+def newton_tolerance_study(n=64, t_end=1.0e4, h=1.0, eps_list=(1e-6, 1e-8, 1e-10), seed=1):
+    """Energy, |J| and spin-length drift at t_end on an n x n grid of the
+    small-scan family (x0 in [15, 40], theta in [0, pi], m1 = m2, chi = 1)
+    for each Newton tolerance and stopping rule."""
+    import torch
+    cells = W.grid_cells(n, n, 15.0, 40.0, seed)
+    m1 = cells[:, W.BETA] / (1 + cells[:, W.BETA])
+    m2 = 1 / (1 + cells[:, W.BETA])
+    spin_ref = np.stack([cells[:, W.CHI1] * m1 ** 2, cells[:, W.CHI2] * m2 ** 2], axis=1)
+    cd = torch.as_tensor(np.ascontiguousarray(cells[:, :9]), device="cuda")
+    report = {"grid": "%dx%d" % (n, n), "orbits": int(cells.shape[0]), "h": h, "t_end": t_end, "rk_order": 5}
+    for apply_small in (1, 0):
+        rule = "apply_then_test" if apply_small else "stop_before_applying"
+        report[rule] = {}
+        for eps in eps_list:
+            with Scan(None, device=True, n=cells.shape[0], rk_order=5, newton_tol=eps,
+                      newton_apply_small=apply_small) as s:
+                s.setup(cd)
+                s.run(t_end, h)
+                out = s.read()
+            report[rule]["%g" % eps] = drift_stats(out, spin_ref)
+    return report
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["qm", "paper"])
+    ap.add_argument("study", choices=["qm", "paper", "newton"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--subset", type=int, default=0)
@@ -112,6 +143,8 @@ def main():
     a = ap.parse_args()
     if a.study == "qm":
         print(json.dumps(qm_drift_study(a.n, a.subset, a.t_end, a.h)), flush=True)
+    elif a.study == "newton":
+        print(json.dumps(newton_tolerance_study(a.n, a.t_end)), flush=True)
     else:
         print(json.dumps(paper_scans(a.t_end, 1.0, out_dir=a.out)), flush=True)
 

@@ -198,6 +198,7 @@ def test_qm_parity(pn):
                                   dict(r_merge=0.0, r_escape=0.0, fli_renorm_steps=37),
                                   dict(newton_det_min=0.0),
                                   dict(rk_order=5),
+                                  dict(newton_apply_small=0, newton_tol=1e-8),
                                   dict(rk_order=5, schedule=1)])
 def test_flag_variants_parity(pn, opts):
     check(pn, W.uneven_batch(n=96, seed=12), 400, **opts)

@@ -14,6 +14,8 @@ a wrong sign or coefficient, a transposed operand -- fails one of them:
 * the Newton root of Eq. 13 vs an independent 2-D root finder
 * FLI of an integrable orbit grows as a power law; the paper's case II
   orbits 1 / 2 are regular / chaotic (Sec. 3B, Fig. 3)
+* the Newton tolerance matters only under the stop-before-applying rule,
+  and then sets the energy error's size (Fig. 4)
 """
 import json
 import os
@@ -439,6 +441,32 @@ def test_uncorrected_rk4_drifts(orc):
         I = orc.scan(y0[None], beta, 1.0, T, cfg)["integrals"][0]
         e.append(abs(I[1] - I[0]) / abs(I[0]))
     assert e[0] > 1e-11 and e[1] > 2 * e[0]
+
+
+def test_newton_tolerance_ablation_fig_4(orc):
+    """Fig. 4 / Sec. 3A: the energy error depends on the Newton tolerance eps
+    of the scale factors only under the rule that stops BEFORE applying a
+    step already within eps.  Then the error follows the uncorrected drift
+    until the pending step exceeds eps, so its size is set by eps (~7 eps
+    here, a sawtooth whose first tooth is the linear growth of Fig. 4);
+    under the default rule (apply the step, then test it) the error left is
+    quadratic in eps (round-off from eps = 1e-8 down).  Orbit 4, corrected RK5, h = 1, 2e4 steps."""
+    beta, y0 = paper_orbit("orbit_4")
+    s = orc.system(beta, pn_order=2, use_so=1, use_ss=1)
+    E0 = orc.hamiltonian(s, y0)
+    worst = {}
+    for apply_small in (1, 0):
+        for eps in (1e-6, 1e-8, 1e-10):
+            cfg = orc.config(newton_tol=eps, newton_apply_small=apply_small, rk_order=5,
+                             r_merge=0, r_escape=0)
+            tr = orc.trace(y0, beta, 1.0, 20_000, 1, cfg)
+            worst[apply_small, eps] = max(abs(orc.hamiltonian(s, y) - E0) for y in tr) / abs(E0)
+    for eps in (1e-6, 1e-8, 1e-10):
+        # after an applied step Newton's remaining error is quadratic in it
+        assert worst[1, eps] <= max(1e-13, 100 * eps * eps), (eps, worst[1, eps])
+        assert worst[1, eps] <= 1e-4 * worst[0, eps]
+        assert 0.1 * eps <= worst[0, eps] <= 100 * eps, (eps, worst[0, eps])
+    assert worst[0, 1e-6] > 10 * worst[0, 1e-8] > 100 * worst[0, 1e-10]
 
 
 # ---------------------------------------------------- set-up and statuses

@@ -21,3 +21,26 @@ def test_qm_drift_with_and_without_correction():
     assert c["dJ"]["median"] <= 1e-14
     assert u["dE"]["median"] > 1e3 * c["dE"]["median"]
     assert u["dJ"]["median"] > 1e2 * c["dJ"]["median"]
+
+
+def test_newton_tolerance_ablation_over_a_grid():
+    """Fig. 4 over a 24 x 24 grid to t = 3000: under the stop-before-applying
+    rule the Newton steps at eps = 1e-6 and 1e-8 are rarely applied, so the
+    energy drift follows the uncorrected growth (the oracle gives medians
+    8.9e-12 / 1.7e-12), while eps = 1e-10 holds it ~100x lower (6.3e-14);
+    under the default rule every eps leaves round-off (oracle: max 1.6e-15)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_00147_gb300 import build
+    build.build()
+    from paper_1802_00147_gb300 import studies
+    r = studies.newton_tolerance_study(n=24, t_end=3000.0)
+    a, b = r["apply_then_test"], r["stop_before_applying"]
+    med = {eps: b[eps]["dE"]["median"] for eps in ("1e-06", "1e-08", "1e-10")}
+    for eps in med:
+        assert a[eps]["done"] > 400 and b[eps]["done"] > 400
+        assert a[eps]["dE"]["max"] <= 1e-12
+        assert med[eps] <= 100 * float(eps)
+    assert med["1e-06"] >= med["1e-08"] > 10 * med["1e-10"]
+    assert med["1e-06"] > 1e3 * a["1e-06"]["dE"]["median"]
