@@ -104,8 +104,11 @@ typedef struct scan_params {
     int block_size;          /* threads per block, 32..128, multiple of 32 (0: 128) */
     int chunk_steps;         /* steps per work-queue task (0: 500) */
     int blocks_per_sm;       /* resident blocks per SM for the queue kernel (0: occupancy maximum) */
-    int register_variant;    /* queue kernel compiled for 2 (up to 255 registers/thread) or 3 (168)
-                                resident 128-thread blocks per SM (0: 2, or the autotuned choice) */
+    int register_variant;    /* RK4 queue kernel variant: 2 -- up to 255 registers/thread, 2 resident
+                                128-thread blocks per SM; 3 -- 168 registers, 3 blocks, per-orbit
+                                constants in shared memory; 4 -- as 2 with the RK stage and trajectory
+                                loops not unrolled (smaller code, bit-identical results)
+                                (0: 4, or the autotuned choice) */
     int use_graph;           /* 1: capture a queue / compact run in a CUDA graph and replay it (default 1) */
     double sync_timeout_s;   /* host watchdog for synchronising calls (default 0: wait forever) */
     int queue_wait_limit_ms; /* bound on a work-queue task's wait for its predecessor; on expiry the

@@ -311,7 +311,7 @@ int scan_create(const scan_params* p, scan_handle** out)
     if (!(p->fli_d0 > 0.0)) return PNSCAN_ERR_ARG;
     if (p->block_size && (p->block_size < 32 || p->block_size > 128 || p->block_size % 32)) return PNSCAN_ERR_ARG;
     if (p->chunk_steps < 0 || p->blocks_per_sm < 0 || p->queue_wait_limit_ms < 0) return PNSCAN_ERR_ARG;
-    if (p->register_variant != 0 && p->register_variant != 2 && p->register_variant != 3) return PNSCAN_ERR_ARG;
+    if (p->register_variant != 0 && (p->register_variant < 2 || p->register_variant > 4)) return PNSCAN_ERR_ARG;
     if (p->rk_order != 0 && p->rk_order != 4 && p->rk_order != 5) return PNSCAN_ERR_ARG;
     if (p->schedule < 0 || p->schedule > 3) return PNSCAN_ERR_ARG;
     if ((p->alloc_fn == nullptr) != (p->free_fn == nullptr)) return PNSCAN_ERR_ARG;
@@ -407,7 +407,7 @@ int scan_create(const scan_params* p, scan_handle** out)
     h->block = p->block_size ? p->block_size : 128;
     h->chunk = p->chunk_steps ? p->chunk_steps : 500;
     h->bps = p->blocks_per_sm;
-    h->minb = p->register_variant == 3 ? 3 : 2;
+    h->minb = p->register_variant >= 2 ? p->register_variant : 4;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return fail(PNSCAN_ERR_CUDA);
     *out = h;
     return PNSCAN_OK;
@@ -577,7 +577,7 @@ int scan_autotune(scan_handle* h, int steps, int* schedule, int* block_size, int
         for (int blk_sz : {64, 128}) cands.push_back({PNSCAN_SCHED_STATIC, blk_sz, 0, 0, 2});
         for (int ch : {steps / 16, steps / 8})
             if (ch >= 1) cands.push_back({PNSCAN_SCHED_COMPACT, 128, ch, 0, 2});
-        for (int minb : {2, 3})
+        for (int minb : {2, 3, 4})
             for (int ch : {steps / 16, steps / 8, steps / 4}) {
                 if (ch < 1) continue;
                 cands.push_back({PNSCAN_SCHED_QUEUE, 128, ch, 0, minb});

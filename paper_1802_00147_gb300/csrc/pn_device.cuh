@@ -299,6 +299,34 @@ __device__ __forceinline__ void rk4_step(const C& c, Vec12& y, double h)
     for (int i = 0; i < 12; i++) yv[i] = fma(h6, kv[i], av[i]);
 }
 
+// The same RK4 step with the four stages in a loop that is not unrolled, so
+// the equations of motion are compiled once instead of four times (smaller
+// code, same arithmetic in the same order: results are bit-identical).
+template <bool QM, class C>
+__device__ __forceinline__ void rk4_step_rolled(const C& c, Vec12& y, double h)
+{
+    const double h2 = 0.5 * h, h3 = h * (1.0 / 3.0), h6 = h * (1.0 / 6.0);
+    Vec12 k, st = y, acc = y;
+    const double* yv = &y.r[0];
+    const double* kv = &k.r[0];
+    double* sv = &st.r[0];
+    double* av = &acc.r[0];
+#pragma unroll 1
+    for (int j = 0; j < 4; j++) {
+        rhs<QM>(c, st, k);
+        const double w = (j == 0 || j == 3) ? h6 : h3;
+        // stage 0: acc = y + h/6 k1 (acc starts as y)
+#pragma unroll
+        for (int i = 0; i < 12; i++) av[i] = fma(w, kv[i], av[i]);
+        if (j < 3) {
+            const double a = j == 2 ? h : h2;
+#pragma unroll
+            for (int i = 0; i < 12; i++) sv[i] = fma(a, kv[i], yv[i]);
+        }
+    }
+    y = acc;
+}
+
 // Fifth-order Runge-Kutta step, Dormand & Prince (1980) tableau with the
 // fifth-order weights (b7 = 0, so six derivative evaluations).  The stage
 // derivatives go to shared memory (kst: 6 x 12 planes of `stride` doubles,
@@ -350,6 +378,59 @@ __device__ __forceinline__ void rk5_step(const C& c, Vec12& y, double h, double*
         for (int m = 0; m < 6; m++)
             if (B[m] != 0.0) acc = fma(h * B[m], kst[(m * 12 + i) * stride], acc);
         yv[i] = acc;
+    }
+}
+
+// Tableau of rk5_step scaled by the step: hab[5 j + m] = h a_{j+1, m+1}
+// (j = 1..5, m < j) and hab[30 + m] = h b_{m+1}.
+__device__ __forceinline__ void rk5_scaled_tableau(double h, double* hab)
+{
+    const double A[6][5] = {{0, 0, 0, 0, 0},
+                            {1.0 / 5.0, 0, 0, 0, 0},
+                            {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0},
+                            {44.0 / 45.0, -56.0 / 15.0, 32.0 / 9.0, 0, 0},
+                            {19372.0 / 6561.0, -25360.0 / 2187.0, 64448.0 / 6561.0, -212.0 / 729.0, 0},
+                            {9017.0 / 3168.0, -355.0 / 33.0, 46732.0 / 5247.0, 49.0 / 176.0, -5103.0 / 18656.0}};
+    const double B[6] = {35.0 / 384.0, 0.0, 500.0 / 1113.0, 125.0 / 192.0, -2187.0 / 6784.0, 11.0 / 84.0};
+#pragma unroll
+    for (int j = 0; j < 6; j++)
+#pragma unroll
+        for (int m = 0; m < 5; m++) hab[5 * j + m] = h * A[j][m];
+#pragma unroll
+    for (int m = 0; m < 6; m++) hab[30 + m] = h * B[m];
+}
+
+// rk5_step with the stage loops not unrolled (one compiled copy of the
+// equations of motion); hab from rk5_scaled_tableau.  Same products and
+// sums in the same order as rk5_step: bit-identical results.
+template <bool QM, class C>
+__device__ __forceinline__ void rk5_step_rolled(const C& c, Vec12& y, const double* hab, double* kst, int stride)
+{
+    double* yv = &y.r[0];
+    Vec12 st = y, k;
+    double* sv = &st.r[0];
+    const double* kv = &k.r[0];
+#pragma unroll 1
+    for (int j = 0; j < 6; j++) {
+        if (j > 0) {
+            st = y;
+#pragma unroll 1
+            for (int m = 0; m < j; m++) {
+                const double a = hab[5 * j + m];
+#pragma unroll
+                for (int i = 0; i < 12; i++) sv[i] = fma(a, kst[(m * 12 + i) * stride], sv[i]);
+            }
+        }
+        rhs<QM, C>(c, st, k);
+#pragma unroll
+        for (int i = 0; i < 12; i++) kst[(j * 12 + i) * stride] = kv[i];
+    }
+#pragma unroll 1
+    for (int m = 0; m < 6; m++) {
+        if (m == 1) continue;                        // b2 = 0
+        const double b = hab[30 + m];
+#pragma unroll
+        for (int i = 0; i < 12; i++) yv[i] = fma(b, kst[(m * 12 + i) * stride], yv[i]);
     }
 }
 

@@ -106,8 +106,23 @@ __device__ __forceinline__ Coef load_coef(const DevState& S, int64_t i, const Fl
 // the shadow, termination tests, and every `renorm` steps the FLI
 // renormalisation (acc += log10(d/d0), shadow pulled back to distance d0 and
 // given its own reference integrals).
-template <bool QM, int RK, class C>
-__device__ __forceinline__ void advance(const RunCfg& rc, const C& c, Orbit& o, int32_t step_end)
+//
+// ROLLED: the two trajectories and the RK stages run in loops that are not
+// unrolled -- one compiled copy of the equations of motion and of the
+// correction instead of eight (RK4) or twelve (RK5) and two; the trajectories
+// are swapped in registers between the passes.  Same operations in the same
+// order.  hab: the step-scaled RK5 tableau (RK5 only).
+template <class T>
+__device__ __forceinline__ void swap_regs(T& a, T& b)
+{
+    const T t = a;
+    a = b;
+    b = t;
+}
+
+template <bool QM, int RK, class C, bool ROLLED = false>
+__device__ __forceinline__ void advance(const RunCfg& rc, const C& c, Orbit& o, int32_t step_end,
+                                        const double* hab = nullptr)
 {
     extern __shared__ double kst_dyn[];      // RK5 stage derivatives (rk_order 5 only)
     double* kst = kst_dyn + threadIdx.x;
@@ -115,6 +130,21 @@ __device__ __forceinline__ void advance(const RunCfg& rc, const C& c, Orbit& o, 
     const double t0 = o.t;
     const int32_t n0 = o.nstep;
     while (o.nstep < step_end) {
+        if (ROLLED) {
+#pragma unroll 1
+            for (int tr = 0; tr < 2; tr++) {
+                if (RK == 5) rk5_step_rolled<QM, C>(c, o.y, hab, kst, kstride);
+                else rk4_step_rolled<QM, C>(c, o.y, rc.h);
+                if (rc.correct) {
+                    int kind;
+                    o.iters += correct<QM, C>(c, o.y, o.ref, rc.newton, &kind);
+                    o.skips += kind != CORR_DUAL;
+                    if (tr == 0) o.last_kind = kind;
+                }
+                swap_regs(o.y, o.ys);
+                swap_regs(o.ref, o.refs);
+            }
+        } else {
         if (RK == 5) rk5_step<QM, C>(c, o.y, rc.h, kst, kstride);
         else rk4_step<QM, C>(c, o.y, rc.h);
         if (rc.correct) {
@@ -129,6 +159,7 @@ __device__ __forceinline__ void advance(const RunCfg& rc, const C& c, Orbit& o, 
             int kind;
             o.iters += correct<QM, C>(c, o.ys, o.refs, rc.newton, &kind);
             o.skips += kind != CORR_DUAL;
+        }
         }
         o.nstep++;
         if (!finite12(o.y) || !finite12(o.ys)) { o.status = ORBIT_NONFINITE; break; }
@@ -269,11 +300,16 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
 
 // SMEM: keep the per-orbit constants in shared memory (one plane per constant)
 // instead of registers, which is what lets MINB = 3 blocks fit without spills.
-template <bool QM, int MINB, bool SMEM, int RK>
+template <bool QM, int MINB, bool SMEM, int RK, bool ROLLED = false>
 __global__ void __launch_bounds__(128, MINB) k_integrate_queue(DevState S, RunCfg rc, QueueState q, int chunk,
                                                                 int use_order)
 {
     __shared__ double scoef[SMEM ? NCOEF * 128 : 1];
+    __shared__ double hab[(RK == 5 && ROLLED) ? 36 : 1];
+    if (RK == 5 && ROLLED) {
+        if (threadIdx.x == 0) rk5_scaled_tableau(rc.h, hab);
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31;
     // compacting schedule: slot s of the dense list holds orbit order[s]
     const long long nslots = use_order ? (long long)__ldcg(q.count) : S.n;
@@ -318,10 +354,10 @@ __global__ void __launch_bounds__(128, MINB) k_integrate_queue(DevState S, RunCf
 #pragma unroll
                     for (int k = 0; k < NCOEF; k++) mine[k * (int)blockDim.x] = cf.v[k];
                     const CoefShared cs{mine, (int)blockDim.x};
-                    advance<QM, RK, CoefShared>(rc, cs, o, end);
+                    advance<QM, RK, CoefShared, ROLLED>(rc, cs, o, end, hab);
                 } else {
                     const Coef cf = load_coef<true>(S, i, rc.flags);
-                    advance<QM, RK, Coef>(rc, cf, o, end);
+                    advance<QM, RK, Coef, ROLLED>(rc, cf, o, end, hab);
                 }
                 if (o.status == ORBIT_RUNNING && o.nstep == end_run) o.status = ORBIT_DONE;
                 store_orbit(S, i, o);
@@ -537,35 +573,44 @@ cudaError_t launch_integrate_static(DevState S, RunCfg rc, int block, cudaStream
     return cudaGetLastError();
 }
 
-template <int MINB, bool SMEM, int RK>
+template <int MINB, bool SMEM, int RK, bool ROLLED = false>
 static int occupancy_queue(int block, bool qm)
 {
     const size_t sm = RK == 5 ? rk5_smem_bytes(block) : 0;
     int nb = 0;
     if (sm > 48 * 1024) {
-        cudaFuncSetAttribute(k_integrate_queue<true, MINB, SMEM, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_integrate_queue<false, MINB, SMEM, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_integrate_queue<true, MINB, SMEM, RK, ROLLED>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_integrate_queue<false, MINB, SMEM, RK, ROLLED>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     }
-    if (qm) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<true, MINB, SMEM, RK>, block, sm);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<false, MINB, SMEM, RK>, block, sm);
+    if (qm) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<true, MINB, SMEM, RK, ROLLED>, block, sm);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<false, MINB, SMEM, RK, ROLLED>, block, sm);
     return nb;
 }
 
-// Compiled variants: RK4 with the per-orbit constants in registers (2 blocks
-// per SM) or in shared memory (3 blocks per SM); RK5 with them in registers.
+// Compiled variants (the `minb` code): RK4 with the per-orbit constants in
+// registers, 2 blocks per SM (2); in shared memory, 3 blocks per SM (3); in
+// registers with the stage and trajectory loops rolled (4).  RK5 with the
+// constants in registers, loops unrolled (2, 3) or rolled (4).
 int queue_blocks_per_sm(int block, bool qm, int minb, int rk_order)
 {
-    if (rk_order == 5) return occupancy_queue<2, false, 5>(block, qm);
-    return minb == 3 ? occupancy_queue<3, true, 4>(block, qm) : occupancy_queue<2, false, 4>(block, qm);
+    if (rk_order == 5)
+        return minb == 4 ? occupancy_queue<2, false, 5, true>(block, qm) : occupancy_queue<2, false, 5>(block, qm);
+    if (minb == 3) return occupancy_queue<3, true, 4>(block, qm);
+    if (minb == 4) return occupancy_queue<2, false, 4, true>(block, qm);
+    return occupancy_queue<2, false, 4>(block, qm);
 }
 
-template <int MINB, bool SMEM, int RK>
+template <int MINB, bool SMEM, int RK, bool ROLLED = false>
 static void launch_queue(DevState S, RunCfg rc, QueueState q, int block, int grid, int chunk, int use_order,
                          cudaStream_t st)
 {
     const size_t sm = RK == 5 ? rk5_smem_bytes(block) : 0;
-    if (rc.flags.use_qm) k_integrate_queue<true, MINB, SMEM, RK><<<grid, block, sm, st>>>(S, rc, q, chunk, use_order);
-    else k_integrate_queue<false, MINB, SMEM, RK><<<grid, block, sm, st>>>(S, rc, q, chunk, use_order);
+    if (rc.flags.use_qm)
+        k_integrate_queue<true, MINB, SMEM, RK, ROLLED><<<grid, block, sm, st>>>(S, rc, q, chunk, use_order);
+    else
+        k_integrate_queue<false, MINB, SMEM, RK, ROLLED><<<grid, block, sm, st>>>(S, rc, q, chunk, use_order);
 }
 
 cudaError_t launch_integrate_queue(DevState S, RunCfg rc, QueueState q, int block, int grid,
@@ -573,8 +618,10 @@ cudaError_t launch_integrate_queue(DevState S, RunCfg rc, QueueState q, int bloc
 {
     if (S.n == 0 || rc.nsteps <= 0) return cudaSuccess;
     if (block <= 0 || block > 128 || block % 32 || grid <= 0 || chunk <= 0) return cudaErrorInvalidValue;
-    if (rc.rk_order == 5) launch_queue<2, false, 5>(S, rc, q, block, grid, chunk, use_order, st);
+    if (rc.rk_order == 5 && minb == 4) launch_queue<2, false, 5, true>(S, rc, q, block, grid, chunk, use_order, st);
+    else if (rc.rk_order == 5) launch_queue<2, false, 5>(S, rc, q, block, grid, chunk, use_order, st);
     else if (minb == 3) launch_queue<3, true, 4>(S, rc, q, block, grid, chunk, use_order, st);
+    else if (minb == 4) launch_queue<2, false, 4, true>(S, rc, q, block, grid, chunk, use_order, st);
     else launch_queue<2, false, 4>(S, rc, q, block, grid, chunk, use_order, st);
     return cudaGetLastError();
 }

@@ -221,9 +221,18 @@ def test_schedules_chunks_and_pointers_are_bit_identical(pn):
     d = gpu_run(pn, cells, 300, schedule=2, device=True, use_graph=0)
     f = gpu_run(pn, cells, 300, schedule=3, chunk_steps=64)                # compacting epochs
     g = gpu_run(pn, cells, 300, schedule=3, chunk_steps=100, chunks=3, use_graph=0)
-    for other in (b, c, d, f, g):
+    # queue kernel with the stage / trajectory loops unrolled (2) and rolled (4)
+    r2 = gpu_run(pn, cells, 300, schedule=2, chunk_steps=64, register_variant=2)
+    r4 = gpu_run(pn, cells, 300, schedule=3, chunk_steps=64, register_variant=4)
+    for other in (b, c, d, f, g, r2, r4):
         for k in ("states", "fli", "status", "t_stop", "integrals"):
             np.testing.assert_array_equal(a[k], other[k], err_msg=k)
+    # RK5: static kernel, queue kernel unrolled (2) and rolled (4)
+    a5 = gpu_run(pn, cells, 200, schedule=1, rk_order=5)
+    for rv in (2, 4):
+        o5 = gpu_run(pn, cells, 200, schedule=2, chunk_steps=64, rk_order=5, register_variant=rv)
+        for k in ("states", "fli", "status", "t_stop", "integrals"):
+            np.testing.assert_array_equal(a5[k], o5[k], err_msg="rk5 variant %d %s" % (rv, k))
     # the shared-memory-constants variant is compiled separately: the same
     # arithmetic up to the compiler's rounding choices, so equal statuses and
     # states within rounding (amplified near merger)
