@@ -81,7 +81,9 @@ typedef struct scan_params {
     int use_so;              /* 1.5PN spin-orbit (default 1) */
     int use_ss;              /* 2PN S1-S2 spin-spin, Eq. 3 (default 1) */
     int use_qm;              /* spin-induced quadrupole-monopole, Eqs. 4-5 (default 0) */
-    int correct;             /* manifold correction after every step (default 1) */
+    int correct;             /* correction after every step: 0 none; 1 spin lengths (Eq. 10) and dual
+                                scaling (Eqs. 11-13) (default); ablations: 2 spin lengths only;
+                                3 spin lengths and velocity scaling p = a p* to E0 (Sec. 1) */
     int rk_order;            /* base integrator: 4 classical RK4 (default), 5 fifth-order Runge-Kutta
                                 with the Dormand-Prince (1980) weights (the paper's RK5, Sec. 3A) */
     double newton_tol;       /* Newton stop: |d alpha|, |d beta| <= tol (default 1e-10, Sec. 3A) */

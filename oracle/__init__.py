@@ -63,6 +63,8 @@ def lib():
         L.orc_integrals.argtypes = [P(Sys), dp, dp]
         L.orc_correct.argtypes = [P(Sys), dp, dp, d, i, d, P(i), dp]
         L.orc_correct.restype = i
+        L.orc_correct_rule.argtypes = [P(Sys), dp, dp, d, i, d, i, i, P(i), dp]
+        L.orc_correct_rule.restype = i
         L.orc_setup_cell.argtypes = [dp, dp]
         L.orc_scan.argtypes = [i64, dp, dp, dp, dp, P(Config), d, i64, dp, dp, dp, dp,
                                P(_ct.c_int32), dp, P(i64), P(_ct.c_int32), P(_ct.c_int32), i]
@@ -130,15 +132,19 @@ def integrals(s, y):
     return out
 
 
-def correct(s, y, ref, newton_tol=1e-10, newton_max=50, det_min=1e-5):
+MODE_DUAL, MODE_SPINS, MODE_VELOCITY = 1, 2, 3
+
+
+def correct(s, y, ref, newton_tol=1e-10, newton_max=50, det_min=1e-5, mode=MODE_DUAL, apply_small=1):
     """Returns (y_corrected, code, iters, (alpha, beta)); code 0 dual scaling,
-    2 velocity scaling (singular dual scaling), 1 nothing applied."""
+    2 velocity scaling (singular dual scaling, or mode MODE_VELOCITY), 1 nothing
+    applied beyond the spin lengths."""
     y = _vec(y).copy()
     ref = _vec(ref)
     it = _ct.c_int(0)
     ab = _np.zeros(2)
-    code = lib().orc_correct(_ct.byref(s), _dp(y), _dp(ref), newton_tol, newton_max,
-                             det_min, _ct.byref(it), _dp(ab))
+    code = lib().orc_correct_rule(_ct.byref(s), _dp(y), _dp(ref), newton_tol, newton_max,
+                                  det_min, int(apply_small), int(mode), _ct.byref(it), _dp(ab))
     return y, code, it.value, (ab[0], ab[1])
 
 

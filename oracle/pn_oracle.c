@@ -299,16 +299,16 @@ int orc_correct(const orc_sys *s, double y[12], const double ref[4],
                 double newton_tol, int newton_max, double det_min,
                 int *iters, double alpha_beta[2])
 {
-    return orc_correct_rule(s, y, ref, newton_tol, newton_max, det_min, 1, iters, alpha_beta);
+    return orc_correct_rule(s, y, ref, newton_tol, newton_max, det_min, 1, ORC_MODE_DUAL, iters, alpha_beta);
 }
 
 int orc_correct_rule(const orc_sys *s, double y[12], const double ref[4],
-                     double newton_tol, int newton_max, double det_min, int apply_small,
+                     double newton_tol, int newton_max, double det_min, int apply_small, int mode,
                      int *iters, double alpha_beta[2])
 {
     double rs[3], ps[3], yb[12], g[12];
     double alpha = 1.0, beta = 1.0;
-    int it, i, converged = 0;
+    int it = 0, i, converged = 0;
 
     /* Eq. 10: restore both spin lengths (skipped for a zero-length spin). */
     for (i = 0; i < 2; i++) {
@@ -320,6 +320,15 @@ int orc_correct_rule(const orc_sys *s, double y[12], const double ref[4],
         }
     }
 
+    if (mode == ORC_MODE_SPINS) {          /* ablation: Eq. 10 alone */
+        if (iters) *iters = 0;
+        if (alpha_beta) {
+            alpha_beta[0] = 1.0;
+            alpha_beta[1] = 1.0;
+        }
+        return ORC_CORR_SKIPPED;
+    }
+
     /* Eqs. 11-13: p = alpha p*, r = beta r*; the two conditions
      * H(beta r*, alpha p*, S) = E0 and |J(beta r*, alpha p*, S)| = J0 make the
      * least-squares function of Eq. 12 vanish; Newton from (1, 1). */
@@ -328,7 +337,9 @@ int orc_correct_rule(const orc_sys *s, double y[12], const double ref[4],
         ps[i] = y[3 + i];
     }
     memcpy(yb, y, sizeof(yb));
-    for (it = 1; it <= newton_max; it++) {
+    /* mode ORC_MODE_VELOCITY (ablation): no dual scaling, straight to the
+     * velocity scaling below */
+    for (it = 1; mode == ORC_MODE_DUAL && it <= newton_max; it++) {
         double J[3], rxp[3], rsxp[3], rxps[3], Jn, F1, F2, A, B, C, D, det, da, db;
         for (i = 0; i < 3; i++) {
             yb[i] = beta * rs[i];
@@ -368,6 +379,7 @@ int orc_correct_rule(const orc_sys *s, double y[12], const double ref[4],
             break;
         }
     }
+    if (mode != ORC_MODE_DUAL) it = 0;
     if (it > newton_max) it = newton_max;
     if (converged) {
         for (i = 0; i < 3; i++) {
@@ -489,7 +501,7 @@ static void integrate_one(const orc_config *cfg, const orc_sys *s, const double 
         else orc_rk4_step(s, y, h);
         if (cfg->correct) {
             last_kind = orc_correct_rule(s, y, ref, cfg->newton_tol, cfg->newton_max, cfg->det_min,
-                                         cfg->newton_apply_small, &it, 0);
+                                         cfg->newton_apply_small, cfg->correct, &it, 0);
             if (last_kind != ORC_CORR_OK) skips++;
             iters += it;
         }
@@ -497,7 +509,7 @@ static void integrate_one(const orc_config *cfg, const orc_sys *s, const double 
         else orc_rk4_step(s, ys, h);
         if (cfg->correct) {
             if (orc_correct_rule(s, ys, refs, cfg->newton_tol, cfg->newton_max, cfg->det_min,
-                                 cfg->newton_apply_small, &it, 0))
+                                 cfg->newton_apply_small, cfg->correct, &it, 0))
                 skips++;
             iters += it;
         }
@@ -580,7 +592,7 @@ int orc_trace(const double y0[12], double beta, double kappa1, double kappa2,
         else orc_rk4_step(&s, y, h);
         if (cfg->correct)
             orc_correct_rule(&s, y, ref, cfg->newton_tol, cfg->newton_max, cfg->det_min,
-                             cfg->newton_apply_small, &it, 0);
+                             cfg->newton_apply_small, cfg->correct, &it, 0);
         if (k % every == 0) {
             memcpy(trace + 12 * m, y, sizeof(y));
             m++;

@@ -35,7 +35,9 @@ typedef struct {
 /* Integration / correction / FLI configuration (one per scan). */
 typedef struct {
     int pn_order, use_so, use_ss, use_qm;
-    int correct;          /* 1: manifold correction (Eqs. 10-13) after every step */
+    int correct;          /* correction after every step: 0 none; 1 spin lengths (Eq. 10) and dual
+                             scaling (Eqs. 11-13); ablations: 2 spin lengths only; 3 spin lengths and
+                             velocity scaling p = a p* to E0 (Sec. 1, Wu et al. 2007) */
     double newton_tol;    /* stop when max(|d alpha|, |d beta|) <= tol (Sec. 3A: 1e-10) */
     int newton_max;       /* iteration cap (50) */
     double det_min;       /* skip the scaling when |det| <= det_min (|J11 J22| + |J12 J21|) */
@@ -96,9 +98,11 @@ void orc_integrals(const orc_sys *s, const double y[12], double out[7]);
 int orc_correct(const orc_sys *s, double y[12], const double ref[4],
                 double newton_tol, int newton_max, double det_min,
                 int *iters, double alpha_beta[2]);
-/* The same with the stopping rule as a parameter (apply_small as in orc_config). */
+/* The same with the stopping rule (apply_small as in orc_config) and the
+ * correction mode (orc_config.correct: ORC_MODE_*) as parameters. */
+enum { ORC_MODE_DUAL = 1, ORC_MODE_SPINS = 2, ORC_MODE_VELOCITY = 3 };
 int orc_correct_rule(const orc_sys *s, double y[12], const double ref[4],
-                     double newton_tol, int newton_max, double det_min, int apply_small,
+                     double newton_tol, int newton_max, double det_min, int apply_small, int mode,
                      int *iters, double alpha_beta[2]);
 
 /* Initial conditions of a scan cell: cell = (x0, pfac, theta1, phi1,

@@ -235,6 +235,7 @@ bool same_run(const RunCfg& a, const RunCfg& b)
            a.flags.use_ss == b.flags.use_ss && a.flags.use_qm == b.flags.use_qm &&
            a.newton.tol == b.newton.tol && a.newton.max_iter == b.newton.max_iter &&
            a.newton.det_min == b.newton.det_min && a.newton.apply_small == b.newton.apply_small &&
+           a.newton.mode == b.newton.mode &&
            a.correct == b.correct && a.rk_order == b.rk_order && a.h == b.h &&
            a.d0 == b.d0 && a.renorm == b.renorm && a.fli_cap == b.fli_cap &&
            a.rmerge2 == b.rmerge2 && a.rescape2 == b.rescape2 && a.nstep_base == b.nstep_base &&
@@ -314,6 +315,7 @@ int scan_create(const scan_params* p, scan_handle** out)
     if (p->register_variant != 0 && (p->register_variant < 2 || p->register_variant > 4)) return PNSCAN_ERR_ARG;
     if (p->rk_order != 0 && p->rk_order != 4 && p->rk_order != 5) return PNSCAN_ERR_ARG;
     if (p->schedule < 0 || p->schedule > 3) return PNSCAN_ERR_ARG;
+    if (p->correct < 0 || p->correct > 3) return PNSCAN_ERR_ARG;
     if ((p->alloc_fn == nullptr) != (p->free_fn == nullptr)) return PNSCAN_ERR_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -394,6 +396,7 @@ int scan_create(const scan_params* p, scan_handle** out)
     b.newton.max_iter = p->newton_max;
     b.newton.det_min = p->newton_det_min;
     b.newton.apply_small = p->newton_apply_small != 0;
+    b.newton.mode = p->correct;
     b.correct = p->correct != 0;
     b.rk_order = p->rk_order == 5 ? 5 : 4;
     b.d0 = p->fli_d0;

@@ -442,7 +442,13 @@ struct NewtonCfg {
     int max_iter;     // iteration cap
     double det_min;   // relative-determinant guard of the singular scaling
     int apply_small;  // 1: apply a step, then stop if it was within tol; 0: stop before applying it
+    int mode;         // CORR_MODE_*: what the correction restores
 };
+
+// Correction modes: spin lengths and dual scaling (Eqs. 10-13); ablations:
+// spin lengths only (Eq. 10), or spin lengths and velocity scaling p = a p*
+// to E0 (the single-factor correction of Sec. 1, Wu et al. 2007).
+enum CorrMode : int { CORR_MODE_DUAL = 1, CORR_MODE_SPINS = 2, CORR_MODE_VELOCITY = 3 };
 
 // Eq. 10, then Eqs. 11-13: p = alpha p*, r = beta r* with (alpha, beta) from
 // H(beta r*, alpha p*, S) = E0 and |J(beta r*, alpha p*, S)| = J0 by Newton's
@@ -471,6 +477,10 @@ __device__ __forceinline__ int correct(const C& c, Vec12& y, const Ref& ref,
             const double f = ref.S2 * rsqrt(l2);
             y.s2[0] *= f; y.s2[1] *= f; y.s2[2] *= f;
         }
+    }
+    if (nc.mode == CORR_MODE_SPINS) {
+        *kind = CORR_NONE;
+        return 0;
     }
     // monomial coefficients at (r*, p*, S)
     const double R = rsqrt(dot3(y.r, y.r));
@@ -509,7 +519,9 @@ __device__ __forceinline__ int correct(const C& c, Vec12& y, const Ref& ref,
     // First iteration at alpha = beta = 1 (u = 1, k = 1): the monomial sums
     // need no powers and no reciprocal; there dF2/dalpha = dF2/dbeta = dJ and
     // dH/dbeta = -dH/du, so det = dJ (Ha + Hu).
-    {
+    if (nc.mode != CORR_MODE_DUAL) {
+        stop = true;   // velocity-scaling mode: no dual scaling
+    } else {
         ++it;
         const double Pb = B0 + B2 + B4, Pc = C0 + C2 + E1;
         const double H = (A2 + A4 + A6) + Pb + Pc + D0;

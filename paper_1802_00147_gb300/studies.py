@@ -21,6 +21,12 @@ drift at t_end for eps = 1e-6, 1e-8, 1e-10 under both Newton stopping rules
 RK5 at h = 1:
 
     python -m paper_1802_00147_gb300.studies newton [--n 64] [--t-end 1e4]
+
+Correction ablation over the same grid: drift of E, |J| and |S_i| at t_end
+with no correction, the spin lengths alone (Eq. 10), the spin lengths and
+velocity scaling p = a p* to E0 (Sec. 1), and the full dual scaling:
+
+    python -m paper_1802_00147_gb300.studies ablation [--n 64] [--t-end 1e4]
 """
 import argparse
 import json
@@ -132,9 +138,31 @@ def newton_tolerance_study(n=64, t_end=1.0e4, h=1.0, eps_list=(1e-6, 1e-8, 1e-10
     return report
 
 
+def correction_ablation_study(n=64, t_end=1.0e4, h=1.0, rk_order=4, seed=1):
+    """Drift at t_end for each correction mode (0 none, 1 dual scaling,
+    2 spin lengths only, 3 spin lengths + velocity scaling) on an n x n grid
+    of the small-scan family."""
+    import torch
+    cells = W.grid_cells(n, n, 15.0, 40.0, seed)
+    m1 = cells[:, W.BETA] / (1 + cells[:, W.BETA])
+    m2 = 1 / (1 + cells[:, W.BETA])
+    spin_ref = np.stack([cells[:, W.CHI1] * m1 ** 2, cells[:, W.CHI2] * m2 ** 2], axis=1)
+    cd = torch.as_tensor(np.ascontiguousarray(cells[:, :9]), device="cuda")
+    names = {0: "none", 1: "dual_scaling", 2: "spin_lengths_only", 3: "velocity_scaling"}
+    report = {"grid": "%dx%d" % (n, n), "orbits": int(cells.shape[0]), "h": h, "t_end": t_end,
+              "rk_order": rk_order}
+    for mode in (0, 1, 2, 3):
+        with Scan(None, device=True, n=cells.shape[0], rk_order=rk_order, correct=mode) as s:
+            s.setup(cd)
+            s.run(t_end, h)
+            out = s.read()
+        report[names[mode]] = drift_stats(out, spin_ref)
+    return report
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["qm", "paper", "newton"])
+    ap.add_argument("study", choices=["qm", "paper", "newton", "ablation"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--subset", type=int, default=0)
@@ -145,6 +173,8 @@ def main():
         print(json.dumps(qm_drift_study(a.n, a.subset, a.t_end, a.h)), flush=True)
     elif a.study == "newton":
         print(json.dumps(newton_tolerance_study(a.n, a.t_end)), flush=True)
+    elif a.study == "ablation":
+        print(json.dumps(correction_ablation_study(a.n, a.t_end)), flush=True)
     else:
         print(json.dumps(paper_scans(a.t_end, 1.0, out_dir=a.out)), flush=True)
 

@@ -199,6 +199,7 @@ def test_qm_parity(pn):
                                   dict(newton_det_min=0.0),
                                   dict(rk_order=5),
                                   dict(newton_apply_small=0, newton_tol=1e-8),
+                                  dict(correct=2), dict(correct=3),
                                   dict(rk_order=5, schedule=1)])
 def test_flag_variants_parity(pn, opts):
     check(pn, W.uneven_batch(n=96, seed=12), 400, **opts)

@@ -469,6 +469,53 @@ def test_newton_tolerance_ablation_fig_4(orc):
     assert worst[0, 1e-6] > 10 * worst[0, 1e-8] > 100 * worst[0, 1e-10]
 
 
+def test_correction_modes_restore_what_they_claim(orc):
+    """The correction ablations: mode 2 (Eq. 10 alone) restores the spin
+    lengths and leaves r, p as the RK step left them; mode 3 (velocity
+    scaling, Sec. 1) restores the spin lengths and E0 by scaling p alone, so
+    r and the direction of p are untouched and |J| is not restored."""
+    beta, y0 = paper_orbit("case_II_orbit_2")
+    s = orc.system(beta, pn_order=2, use_so=1, use_ss=1)
+    I0 = orc.integrals(s, y0)
+    ref = np.array([I0[0], I0[1], I0[2], I0[3]])
+    y = orc.rk4_step(s, y0, 15.0)                  # a crude step: every integral is off
+    Iy = orc.integrals(s, y)
+    assert abs(Iy[0] - I0[0]) > 1e-9 * abs(I0[0]) and abs(Iy[1] - I0[1]) > 1e-9 * I0[1]
+    y2, code2, it2, _ = orc.correct(s, y, ref, mode=orc.MODE_SPINS)
+    I2 = orc.integrals(s, y2)
+    assert code2 == 1 and it2 == 0
+    np.testing.assert_array_equal(y2[:6], y[:6])
+    assert abs(I2[2] - I0[2]) <= 1e-15 * I0[2] and abs(I2[3] - I0[3]) <= 1e-15 * I0[3]
+    y3, code3, it3, (a, b) = orc.correct(s, y, ref, mode=orc.MODE_VELOCITY)
+    I3 = orc.integrals(s, y3)
+    assert code3 == 2 and it3 >= 1 and b == 1.0
+    np.testing.assert_array_equal(y3[:3], y[:3])
+    np.testing.assert_array_equal(y3[6:], y2[6:])
+    np.testing.assert_allclose(y3[3:6], a * y[3:6], rtol=1e-15)
+    assert abs(I3[0] - I0[0]) <= 1e-14 * abs(I0[0])
+    assert abs(I3[1] - I0[1]) > 1e-9 * I0[1]
+
+
+def test_correction_ablation_drifts(orc):
+    """Over 5000 steps of case II orbit 2: with no correction E, |J| and |S_i|
+    drift; Eq. 10 alone fixes |S_i| only; velocity scaling adds E; the dual
+    scaling holds all of them at round-off."""
+    beta, y0 = paper_orbit("case_II_orbit_2")
+    drift = {}
+    for mode in (0, 1, 2, 3):
+        cfg = orc.config(correct=mode, r_merge=0, r_escape=0)
+        o = orc.scan(y0[None], beta, 1.0, 5000, cfg)
+        I = o["integrals"][0]
+        s0 = np.linalg.norm(y0[6:9]), np.linalg.norm(y0[9:12])
+        drift[mode] = (abs(I[1] - I[0]) / abs(I[0]), abs(I[3] - I[2]) / I[2],
+                       max(abs(I[4] - s0[0]) / s0[0], abs(I[5] - s0[1]) / s0[1]))
+    dE, dJ, dS = zip(*(drift[m] for m in (0, 1, 2, 3)))
+    assert dE[0] > 1e-10 and dJ[0] > 1e-11 and dS[0] > 1e-12
+    assert dE[1] <= 1e-14 and dJ[1] <= 1e-14 and dS[1] <= 1e-15
+    assert dS[2] <= 1e-15 and dE[2] > 1e-10 and dJ[2] > 1e-11
+    assert dS[3] <= 1e-15 and dE[3] <= 1e-14 and dJ[3] > 1e-11
+
+
 # ---------------------------------------------------- set-up and statuses
 def test_setup_cell_geometry(orc):
     cells = np.array([[20.0, 0.9, 0.7, 1.1, 2.0, 4.0, 0.5, 0.8, 0.6]])
