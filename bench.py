@@ -33,12 +33,12 @@ H_STEP = 1.0
 
 # Algorithmic FP64 flops of the kernel's formulation (fma = 2, add/sub/mul = 1,
 # sqrt/rsqrt/reciprocal/division/log10 = 1 each), per trajectory-step:
-#   4 x 219 (RHS) + 171 (RK4 stages) + 138 (correction: spin lengths, Newton
+#   4 x 217 (RHS) + 171 (RK4 stages) + 138 (correction: spin lengths, Newton
 #   monomial set-up, scaling) + 43 (first Newton iteration, at alpha = beta = 1)
-#   = 1228, plus 73 per further Newton iteration; per orbit-step two
+#   = 1220, plus 73 per further Newton iteration; per orbit-step two
 #   trajectories, 5 for the termination test and 1.75 for the FLI
 #   renormalisation amortised over 100 steps.
-FLOPS_PER_TRAJ_STEP = 4 * 219 + 171 + 138 + 43
+FLOPS_PER_TRAJ_STEP = 4 * 217 + 171 + 138 + 43
 FLOPS_PER_NEWTON_ITER = 73
 FLOPS_PER_ORBIT_STEP_EXTRA = 5 + 1.75
 # Nominal FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz.

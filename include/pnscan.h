@@ -206,10 +206,10 @@ int scan_autotune(scan_handle *h, int steps, int *schedule, int *block_size, int
  * on the handle's stream; synchronises).  *ms and *launches may be NULL. */
 int scan_last_run_timing(scan_handle *h, double *ms, int *launches);
 
-/* Time `iters` x 4 x threads x blocks dependent DFMA on the handle's stream
- * and return the achieved FP64 rate (TFLOP/s, 2 flops per DFMA).  blocks =
- * threads = 0 picks 4 warps on every SM.  Used to measure the FP64 pipe's
- * peak.  Errors: ARG, CUDA. */
+/* Time iters x 8 x (256 threads on every SM) DFMA -- 8 independent chains
+ * per thread -- on the handle's stream and return the achieved FP64 rate
+ * (TFLOP/s, 2 flops per DFMA).  Used to measure the FP64 pipe's peak.
+ * Errors: ARG, OOM, CUDA. */
 int scan_fp64_peak(scan_handle *h, int iters, double *tflops);
 
 /* ---- reduction without run-time allocation ----

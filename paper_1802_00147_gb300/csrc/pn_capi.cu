@@ -578,8 +578,9 @@ int scan_autotune(scan_handle* h, int steps, int* schedule, int* block_size, int
         struct Cand { int sched, block, chunk, bps, minb; };
         std::vector<Cand> cands;
         for (int blk_sz : {64, 128}) cands.push_back({PNSCAN_SCHED_STATIC, blk_sz, 0, 0, 2});
-        for (int ch : {steps / 16, steps / 8})
-            if (ch >= 1) cands.push_back({PNSCAN_SCHED_COMPACT, 128, ch, 0, 2});
+        for (int ch : {steps / 32, steps / 16, steps / 8})
+            if (ch >= 1) cands.push_back({PNSCAN_SCHED_COMPACT, 128, ch, 0, 4});
+        if (steps / 16 >= 1) cands.push_back({PNSCAN_SCHED_COMPACT, 128, steps / 16, 0, 2});
         for (int minb : {2, 3, 4})
             for (int ch : {steps / 16, steps / 8, steps / 4}) {
                 if (ch < 1) continue;
@@ -648,7 +649,7 @@ int scan_last_run_timing(scan_handle* h, double* ms, int* launches)
 int scan_fp64_peak(scan_handle* h, int iters, double* tflops)
 {
     if (!h || !tflops || iters <= 0) return PNSCAN_ERR_ARG;
-    const int threads = 128, blocks = h->num_sms;   // 4 warps per SM: one per sub-partition
+    const int threads = 256, blocks = h->num_sms;   // 8 warps per SM: two per sub-partition
     double* buf = (double*)dev_alloc(h, sizeof(double) * threads * blocks);
     if (!buf) return PNSCAN_ERR_OOM;
     cudaEvent_t e0, e1;
@@ -665,7 +666,7 @@ int scan_fp64_peak(scan_handle* h, int iters, double* tflops)
     cudaEventDestroy(e1);
     dev_free(h, buf);
     if (r != PNSCAN_OK) return r;
-    *tflops = 2.0 * 4.0 * (double)iters * threads * blocks / (ms * 1e-3) / 1e12;
+    *tflops = 2.0 * 8.0 * (double)iters * threads * blocks / (ms * 1e-3) / 1e12;
     return PNSCAN_OK;
 }
 

@@ -126,16 +126,17 @@ __device__ __forceinline__ double dot3(const double* a, const double* b)
 //   dH/dp = 2 H_p2 p + (np W u) r + E x r
 //   dH/dr = u np W p - u^2 (u H_u + np^2 W) r + p x E - 3 u^2 (L.E) r
 //           + spin-spin / QM parts (see below)
+//
+// rhs_u takes u = 1/|r| = rsqrt(r.r) from the caller (so that the caller can
+// start it early); rhs computes it.
 template <bool QM, class C>
-__device__ __forceinline__ void rhs(const C& c, const Vec12& y, Vec12& dy)
+__device__ __forceinline__ void rhs_u(const C& c, const Vec12& y, double u, Vec12& dy)
 {
     const double* r = y.r;
     const double* p = y.p;
     const double* S1 = y.s1;
     const double* S2 = y.s2;
 
-    const double rr2 = dot3(r, r);
-    const double u = rsqrt(rr2);
     const double u2 = u * u;
     const double u3 = u2 * u;
     const double u5 = u3 * u2;
@@ -166,22 +167,27 @@ __device__ __forceinline__ void rhs(const C& c, const Vec12& y, Vec12& dy)
                     + u * fma(c[K_E1X3], u, fma(c[K_D1X2], p2, fma(c[K_D2X2], np2, c[K_H1X2])));
     const double cr = np * W * u;                                            // H_np u
 
-    // spin-spin and QM scalars
-    double T1 = c[K_IETA3] * a2s;                                               // 3 ieta a2s + 6 q1 a1s
-    double T2 = c[K_IETA3] * a1s;                                               // 3 ieta a1s + 6 q2 a2s
-    // Ar = u^2 (u H_u + np^2 W + 3 u^3 L.Seff)
-    //    + u^5 [15 u^2 (ieta a1s a2s + q1 a1s^2 + q2 a2s^2) - 3 ieta S12 - 3 (q1 S11 + q2 S22)]
-    double Q = c[K_IETA15] * (a1s * a2s);
-    double K = -c[K_IETA3] * S12;
+    // spin-spin and QM scalars:
+    //   V1 = u^5 (3 ieta a2s + 6 q1 a1s),  V2 = u^5 (3 ieta a1s + 6 q2 a2s)
+    //   Ar = u^2 (u H_u + np^2 W + 3 u^3 L.Seff)
+    //      + u^5 [15 u^2 (ieta a1s a2s + q1 a1s^2 + q2 a2s^2) - 3 ieta S12 - 3 (q1 S11 + q2 S22)]
+    double V1, V2, Ass;   // Ass: the u^5 [...] spin part of Ar
     if (QM) {
-        T1 = fma(c[K_Q1X6], a1s, T1);
-        T2 = fma(c[K_Q2X6], a2s, T2);
-        Q = fma(c[K_Q1X15] * a1s, a1s, fma(c[K_Q2X15] * a2s, a2s, Q));
-        K = fma(-c[K_Q1X3], dot3(S1, S1), fma(-c[K_Q2X3], dot3(S2, S2), K));
+        const double T1 = fma(c[K_Q1X6], a1s, c[K_IETA3] * a2s);
+        const double T2 = fma(c[K_Q2X6], a2s, c[K_IETA3] * a1s);
+        const double Q = fma(c[K_Q1X15] * a1s, a1s, fma(c[K_Q2X15] * a2s, a2s, c[K_IETA15] * (a1s * a2s)));
+        const double K = fma(-c[K_Q1X3], dot3(S1, S1), fma(-c[K_Q2X3], dot3(S2, S2), -c[K_IETA3] * S12));
+        V1 = u5 * T1;
+        V2 = u5 * T2;
+        Ass = u5 * fma(Q, u2, K);
+    } else {
+        // common factor w = 3 ieta u^5:  V1 = w a2s, V2 = w a1s, Ass = w (5 u^2 a1s a2s - S12)
+        const double w = u5 * c[K_IETA3];
+        V1 = w * a2s;
+        V2 = w * a1s;
+        Ass = w * fma(a1s * a2s, 5.0 * u2, -S12);
     }
-    const double V1 = u5 * T1;
-    const double V2 = u5 * T2;
-    const double Ar = fma(u2, fma(3.0, LE, fma(np2, W, u * Hu)), u5 * fma(Q, u2, K));
+    const double Ar = fma(u2, fma(3.0, LE, fma(np2, W, u * Hu)), Ass);
 
     // dr/dt = Hp2x2 p + cr r + E x r
     const double X0 = fma(E1, r[2], -E2 * r[1]);
@@ -213,6 +219,12 @@ __device__ __forceinline__ void rhs(const C& c, const Vec12& y, Vec12& dy)
     dy.s2[0] = fma(O21, S2[2], -O22 * S2[1]);
     dy.s2[1] = fma(O22, S2[0], -O20 * S2[2]);
     dy.s2[2] = fma(O20, S2[1], -O21 * S2[0]);
+}
+
+template <bool QM, class C>
+__device__ __forceinline__ void rhs(const C& c, const Vec12& y, Vec12& dy)
+{
+    rhs_u<QM, C>(c, y, rsqrt(dot3(y.r, y.r)), dy);
 }
 
 // ------------------------------------------------------------ Hamiltonian
@@ -311,18 +323,22 @@ __device__ __forceinline__ void rk4_step_rolled(const C& c, Vec12& y, double h)
     const double* kv = &k.r[0];
     double* sv = &st.r[0];
     double* av = &acc.r[0];
+    double u = rsqrt(dot3(y.r, y.r));
 #pragma unroll 1
     for (int j = 0; j < 4; j++) {
-        rhs<QM>(c, st, k);
-        const double w = (j == 0 || j == 3) ? h6 : h3;
-        // stage 0: acc = y + h/6 k1 (acc starts as y)
-#pragma unroll
-        for (int i = 0; i < 12; i++) av[i] = fma(w, kv[i], av[i]);
+        rhs_u<QM>(c, st, u, k);
+        // next stage state first, and its 1/|r| started before the
+        // accumulator update that does not depend on it
         if (j < 3) {
             const double a = j == 2 ? h : h2;
 #pragma unroll
             for (int i = 0; i < 12; i++) sv[i] = fma(a, kv[i], yv[i]);
+            u = rsqrt(dot3(st.r, st.r));
         }
+        const double w = (j == 0 || j == 3) ? h6 : h3;
+        // stage 0: acc = y + h/6 k1 (acc starts as y)
+#pragma unroll
+        for (int i = 0; i < 12; i++) av[i] = fma(w, kv[i], av[i]);
     }
     y = acc;
 }

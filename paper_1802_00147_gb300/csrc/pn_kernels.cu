@@ -514,17 +514,23 @@ __global__ void k_gather(DevState S, double* states, double* shadow, double* int
 
 // ----------------------------------------------------------- FP64 probe
 // Independent dependent DFMA chains; measures the FP64 pipe's throughput.
+// 8 independent DFMA chains per thread, unrolled by 4: 32 DFMA per loop
+// trip, so loop overhead and dependency latency do not limit the rate.
 __global__ void k_fp64_probe(double* out, int iters)
 {
-    double x0 = threadIdx.x * 1e-3, x1 = x0 + 1.0, x2 = x0 + 2.0, x3 = x0 + 3.0;
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) x[k] = threadIdx.x * 1e-3 + k;
     const double a = 0.9999999, b = 1e-7;
+#pragma unroll 4
     for (int i = 0; i < iters; i++) {
-        x0 = fma(x0, a, b);
-        x1 = fma(x1, a, b);
-        x2 = fma(x2, a, b);
-        x3 = fma(x3, a, b);
+#pragma unroll
+        for (int k = 0; k < 8; k++) x[k] = fma(x[k], a, b);
     }
-    out[blockIdx.x * (int64_t)blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3;
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) s += x[k];
+    out[blockIdx.x * (int64_t)blockDim.x + threadIdx.x] = s;
 }
 
 // -------------------------------------------------------------- launchers
@@ -597,7 +603,7 @@ int queue_blocks_per_sm(int block, bool qm, int minb, int rk_order)
 {
     if (rk_order == 5)
         return minb == 4 ? occupancy_queue<2, false, 5, true>(block, qm) : occupancy_queue<2, false, 5>(block, qm);
-    if (minb == 3) return occupancy_queue<3, true, 4>(block, qm);
+    if (minb == 3) return occupancy_queue<3, true, 4, true>(block, qm);
     if (minb == 4) return occupancy_queue<2, false, 4, true>(block, qm);
     return occupancy_queue<2, false, 4>(block, qm);
 }
@@ -620,7 +626,7 @@ cudaError_t launch_integrate_queue(DevState S, RunCfg rc, QueueState q, int bloc
     if (block <= 0 || block > 128 || block % 32 || grid <= 0 || chunk <= 0) return cudaErrorInvalidValue;
     if (rc.rk_order == 5 && minb == 4) launch_queue<2, false, 5, true>(S, rc, q, block, grid, chunk, use_order, st);
     else if (rc.rk_order == 5) launch_queue<2, false, 5>(S, rc, q, block, grid, chunk, use_order, st);
-    else if (minb == 3) launch_queue<3, true, 4>(S, rc, q, block, grid, chunk, use_order, st);
+    else if (minb == 3) launch_queue<3, true, 4, true>(S, rc, q, block, grid, chunk, use_order, st);
     else if (minb == 4) launch_queue<2, false, 4, true>(S, rc, q, block, grid, chunk, use_order, st);
     else launch_queue<2, false, 4>(S, rc, q, block, grid, chunk, use_order, st);
     return cudaGetLastError();
