@@ -41,8 +41,35 @@ H_STEP = 1.0
 FLOPS_PER_TRAJ_STEP = 4 * 217 + 171 + 138 + 43
 FLOPS_PER_NEWTON_ITER = 73
 FLOPS_PER_ORBIT_STEP_EXTRA = 5 + 1.75
+# Algorithmic DRAM bytes per orbit and run: the SoA state read once (main and
+# shadow 2 x 12, reference integrals 8, FLI accumulator, t, beta, kappa1,
+# kappa2: 37 doubles; nstep, status, Newton and skip counters, last kind:
+# 5 int32) and written once (2 x 12 + 4 + 2 doubles, 5 int32).
+STATE_BYTES_PER_ORBIT = (37 * 8 + 5 * 4) + (30 * 8 + 5 * 4)
 # Nominal FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz.
 FP64_PEAK_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the integrator
+# over one scan_run of this workload, from ncu captures of
+# `bench.py --profile --schedule S` (summary and commands in
+# profiles/k_integrate_queue_dram_314x314.md), keyed by schedule.  Valid only
+# for the kernel sources they were taken with: reported as null once any of
+# these files differs from the recorded SHA-256.
+TRAFFIC_SOURCES = {
+    "paper_1802_00147_gb300/csrc/pn_device.cuh": "72d0eed6d750aee37f0fd9c6d54bf0a4156b9e895b5e439ec35afb5b292daca2",
+    "paper_1802_00147_gb300/csrc/pn_kernels.cu": "e01bcacd7d85dc9470cb29b361a3c1d3641a23183dbee70ceaf0950c6701a5b3",
+    "paper_1802_00147_gb300/csrc/pn_kernels.cuh": "aecb33a6296f7cf7af5c431530b7892c7e36a33e8afb49018d0ba071a395b7d8",
+}
+TRAFFIC_BYTES_PER_RUN = {2: 30343168 + 4435456}    # queue schedule
+
+
+def traffic_per_run(schedule):
+    import hashlib
+    for path, digest in TRAFFIC_SOURCES.items():
+        with open(os.path.join(ROOT, path), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != digest:
+                return None
+    return TRAFFIC_BYTES_PER_RUN.get(schedule)
 
 
 def algorithmic_flops(orbit_steps, newton_iters):
@@ -301,10 +328,13 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    scan = pn.Scan(cells_h[:, W.BETA], device=True)
+    sched_code = {"auto": 0, "static": 1, "queue": 2, "compact": 3}[args.schedule]
+    prof_opts = dict(schedule=sched_code, chunk_steps=args.chunk) if args.profile else {}
+    scan = pn.Scan(cells_h[:, W.BETA], device=True, **prof_opts)
     scan.setup(cells_d)
     if args.profile:
-        shape = {"schedule": 2, "block_size": 128, "chunk_steps": 500, "blocks_per_sm": 0}
+        shape = {"schedule": sched_code or 2, "block_size": 128, "chunk_steps": args.chunk or 500,
+                 "blocks_per_sm": 0}
         fp64_measured = float("nan")
     else:
         shape = scan.autotune(2000)
@@ -322,6 +352,7 @@ def run_ours(args, rank, world, local_rank):
         td.barrier()
     torch.cuda.synchronize()
     kern_ms = []
+    run_launches = []
     steps_total = 0
     iters_total = 0
     with ClockSampler(local_rank) as clk:
@@ -330,7 +361,9 @@ def run_ours(args, rank, world, local_rank):
         ev0.record(stream)
         for _ in range(args.steps):
             summ = step()
-            kern_ms.append(scan.last_run_timing()[0])
+            ms_run, nl = scan.last_run_timing()
+            kern_ms.append(ms_run)
+            run_launches.append(nl)
             steps_total += summ["orbit_steps"]
             iters_total += summ["newton_iters"]
         ev1.record(stream)
@@ -382,6 +415,7 @@ def run_ours(args, rank, world, local_rank):
     ms_kernel = float(np.mean(kern_ms))
     flops = algorithmic_flops(summ["orbit_steps"], summ["newton_iters"])
     achieved = flops / (ms_kernel * 1e-3) / 1e12
+    traffic = traffic_per_run(shape["schedule"])
     cpu_rate, cpu_sample, cores, _ = cpu_oracle_rate(cells_h, target_s=15.0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -389,16 +423,23 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": dict(workload_desc(n), schedule=shape, parallelism="dp%d (independent scans)" % world),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_NOMINAL_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_NOMINAL_TFLOPS, "traffic": None,
-                     "kernel": "k_integrate_queue", "kernel_ms": ms_kernel,
-                     "flops_per_launch": flops,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_NOMINAL_TFLOPS, "traffic": traffic,
+                     "kernel": "k_integrate_queue",
+                     "per": "scan_run: one integrator launch (queue schedule) or one per epoch with a "
+                            "compaction between epochs (compacting schedule); achieved, flops and "
+                            "traffic are per run",
+                     "launches_per_run": int(run_launches[-1]), "kernel_ms": ms_kernel,
+                     "flops_per_run": flops,
+                     "traffic_algorithmic_bytes": int(n * STATE_BYTES_PER_ORBIT),
                      "peak_measured_dfma": fp64_measured,
                      "frac_of_measured": achieved / fp64_measured},
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": cpu_sample},
         "e2e": {"value": e2e_steps / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": 5 * args.steps,
+        # per step: k_setup_cells, k_init, the run's integrator (+ compaction) launches,
+        # k_finalize, k_reduce
+        "gpu_launches": int(sum(4 + nl for nl in run_launches)),
         "clocks": clk.summary(),
         "adaptive": adaptive,
         "uneven": uneven,
@@ -421,6 +462,9 @@ def main():
     ap.add_argument("--t-end", type=float, default=T_END, help="integration time (profiling only)")
     ap.add_argument("--no-adaptive", dest="adaptive", action="store_false",
                     help="skip the uneven-batch and surrogate-adaptive 1024x1024 measurements")
+    ap.add_argument("--schedule", choices=["auto", "static", "queue", "compact"], default="auto",
+                    help="schedule for --profile runs (default: the work queue)")
+    ap.add_argument("--chunk", type=int, default=0, help="steps per task for --profile runs (0: 500)")
     ap.add_argument("--profile", action="store_true",
                     help="time the device path only (no autotune, e2e or CPU leg) for ncu runs")
     args = ap.parse_args()

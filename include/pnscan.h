@@ -203,7 +203,10 @@ int scan_autotune(scan_handle *h, int steps, int *schedule, int *block_size, int
                   int *blocks_per_sm, int *register_variant);
 
 /* Device time of the integrator launches of the last scan_run (CUDA events
- * on the handle's stream; synchronises).  *ms and *launches may be NULL. */
+ * on the handle's stream; synchronises) and the number of kernels that run
+ * launched: 1 for the static and work-queue schedules, 2 per epoch for the
+ * compacting schedule (integrator + compaction).  *ms and *launches may be
+ * NULL. */
 int scan_last_run_timing(scan_handle *h, double *ms, int *launches);
 
 /* Time iters x 8 x (256 threads on every SM) DFMA -- 8 independent chains

@@ -45,7 +45,8 @@ struct scan_handle {
     bool tuned = false;
     // timing of the last run
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    int last_launches = 0;
+    int last_launches = 0;             // kernels launched by the last scan_run
+    int glaunches = 0;                 // kernels in the captured graph
     bool timed = false;
     // CUDA graph of the queue run
     cudaGraphExec_t gexec = nullptr;
@@ -194,18 +195,28 @@ std::vector<int32_t> epoch_lengths(int32_t nsteps)
     return e;
 }
 
+// Kernels launched by one run of the schedule (integrator and compaction;
+// queue resets are memsets): *launches, if not null.
 int launch_run(scan_handle* h, const RunCfg& rc, int sched, int block, int chunk, int bps, int minb,
-               const DevState& S, cudaStream_t st)
+               const DevState& S, cudaStream_t st, int* launches = nullptr)
 {
-    if (sched == PNSCAN_SCHED_STATIC) return cuda_err(launch_integrate_static(S, rc, block, st));
+    int dummy = 0;
+    int& nl = launches ? *launches : dummy;
+    nl = 0;
+    if (sched == PNSCAN_SCHED_STATIC) {
+        nl = 1;
+        return cuda_err(launch_integrate_static(S, rc, block, st));
+    }
     const int grid = queue_grid(h, block, bps, minb);
     if (sched == PNSCAN_SCHED_QUEUE) {
         int r = reset_queue(h, st);
         if (r != PNSCAN_OK) return r;
+        nl = 1;
         return cuda_err(launch_integrate_queue(S, rc, h->q, block, grid, chunk, minb, 0, st));
     }
     // PNSCAN_SCHED_COMPACT: epochs over a dense list of the running orbits
     DevState E = S;
+    nl = 1;
     int r = cuda_err(launch_compact(E, h->q, 1, 1, st));
     if (r == PNSCAN_OK) r = cuda_err(cudaMemcpyAsync(h->q.count, h->q.count + 1, sizeof(int), cudaMemcpyDeviceToDevice, st));
     std::swap(E.order, E.order_next);
@@ -218,8 +229,10 @@ int launch_run(scan_handle* h, const RunCfg& rc, int sched, int block, int chunk
         erc.first_epoch = k == 0;
         r = reset_queue(h, st);
         if (r == PNSCAN_OK) r = cuda_err(launch_integrate_queue(E, erc, h->q, block, grid, chunk, minb, 1, st));
+        ++nl;
         offset += lens[k];
         if (r == PNSCAN_OK && k + 1 < lens.size()) {
+            ++nl;
             r = cuda_err(launch_compact(E, h->q, 0, 0, st));
             if (r == PNSCAN_OK)
                 r = cuda_err(cudaMemcpyAsync(h->q.count, h->q.count + 1, sizeof(int), cudaMemcpyDeviceToDevice, st));
@@ -254,7 +267,8 @@ int run_graph(scan_handle* h, const RunCfg& rc)
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_err(e);
-        int r = launch_run(h, rc, h->sched, h->block, h->chunk, h->bps, h->minb, h->S, h->cap_stream);
+        int r = launch_run(h, rc, h->sched, h->block, h->chunk, h->bps, h->minb, h->S, h->cap_stream,
+                           &h->glaunches);
         e = cudaStreamEndCapture(h->cap_stream, &g);
         if (r != PNSCAN_OK) {
             if (g) cudaGraphDestroy(g);
@@ -267,6 +281,7 @@ int run_graph(scan_handle* h, const RunCfg& rc)
         h->gcfg = rc;
         std::memcpy(h->gshape, shape, sizeof(shape));
     }
+    h->last_launches = h->glaunches;
     return cuda_err(cudaGraphLaunch(h->gexec, h->stream));
 }
 
@@ -458,11 +473,11 @@ int scan_run(scan_handle* h, const double* initial_states, double t_end, double 
         const RunCfg rc = make_run(h, h_step, nsteps);
         if (cudaEventRecord(h->ev0, h->stream) != cudaSuccess) return PNSCAN_ERR_CUDA;
         if (h->sched != PNSCAN_SCHED_STATIC && h->p.use_graph) r = run_graph(h, rc);
-        else r = launch_run(h, rc, h->sched, h->block, h->chunk, h->bps, h->minb, h->S, h->stream);
+        else r = launch_run(h, rc, h->sched, h->block, h->chunk, h->bps, h->minb, h->S, h->stream,
+                            &h->last_launches);
         if (r != PNSCAN_OK) return r;
         if (cudaEventRecord(h->ev1, h->stream) != cudaSuccess) return PNSCAN_ERR_CUDA;
         h->timed = true;
-        h->last_launches = 1;
     }
     h->t_now = h->t_now + nsteps * h_step;
     h->nstep_now += nsteps;
