@@ -202,6 +202,20 @@ int scan_summary(scan_handle *h, scan_summary_t *out);
 int scan_autotune(scan_handle *h, int steps, int *schedule, int *block_size, int *chunk_steps,
                   int *blocks_per_sm, int *register_variant);
 
+/* Gravitational-wave polarisations of every orbit's main trajectory at its
+ * current state (Eq. 14, Sec. 4): the field of the mass quadrupole moment
+ * of the relative orbit (Fig. 10 uses it for orbits 2 and 4),
+ *     h_ij = (4 eta / R) (v_i v_j - n_i n_j / |r|),  v = dr/dt = dH/dp (Eq. 6),
+ *     h_plus = (P_i P_j - Q_i Q_j) h_ij / 2,  h_cross = (P_i Q_j + Q_i P_j) h_ij / 2,
+ * in units G = c = M = 1, observer at distance R > 0 (in M) along N = P x Q.
+ * P, Q: host arrays of 3 doubles, the radiation frame's unit vectors
+ * orthogonal to N (the paper takes P = x, Q = y, N = z).  hplus, hcross: n
+ * doubles each, host or device per device_ptrs; either may be NULL.
+ * Call after scan_run to sample a waveform along the run (e.g. run to t1,
+ * t2, ... and call this after each).  Synchronises.  Errors: ARG (R not
+ * positive and finite, non-finite P or Q), STATE (no state), CUDA. */
+int scan_waveform(scan_handle *h, double R, const double *P, const double *Q, double *hplus, double *hcross);
+
 /* Device time of the integrator launches of the last scan_run (CUDA events
  * on the handle's stream; synchronises) and the number of kernels that run
  * launched: 1 for the static and work-queue schedules, 2 per epoch for the

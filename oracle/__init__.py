@@ -63,6 +63,7 @@ def lib():
         L.orc_integrals.argtypes = [P(Sys), dp, dp]
         L.orc_correct.argtypes = [P(Sys), dp, dp, d, i, d, P(i), dp]
         L.orc_correct.restype = i
+        L.orc_waveform.argtypes = [P(Sys), dp, d, dp, dp, dp]
         L.orc_correct_rule.argtypes = [P(Sys), dp, dp, d, i, d, i, i, P(i), dp]
         L.orc_correct_rule.restype = i
         L.orc_setup_cell.argtypes = [dp, dp]
@@ -130,6 +131,15 @@ def integrals(s, y):
     out = _np.zeros(7)
     lib().orc_integrals(_ct.byref(s), _dp(y), _dp(out))
     return out
+
+
+def waveform(s, y, R=1.0, P=(1.0, 0.0, 0.0), Q=(0.0, 1.0, 0.0)):
+    """(h_plus, h_cross) of the mass quadrupole field at distance R (Eq. 14)."""
+    y = _vec(y)
+    Pv, Qv = _vec(P), _vec(Q)
+    out = _np.zeros(2)
+    lib().orc_waveform(_ct.byref(s), _dp(y), float(R), _dp(Pv), _dp(Qv), _dp(out))
+    return out[0], out[1]
 
 
 MODE_DUAL, MODE_SPINS, MODE_VELOCITY = 1, 2, 3

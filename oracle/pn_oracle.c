@@ -294,6 +294,34 @@ void orc_integrals(const orc_sys *s, const double y[12], double out[7])
     out[6] = J[2];
 }
 
+/* ------------------------------------------------------ gravitational waves */
+/* Eq. 14 with the field of the mass quadrupole moment (Sec. 4, Fig. 10): at
+ * distance R (in M) along N, with the relative velocity v = dr/dt = dH/dp
+ * (Eq. 6) and n = r/|r|,
+ *     h_ij = (4 eta / R) (v_i v_j - n_i n_j / |r|),
+ *     h_plus  = (P_i P_j - Q_i Q_j) h_ij / 2,
+ *     h_cross = (P_i Q_j + Q_i P_j) h_ij / 2,
+ * P, Q the unit vectors of the radiation frame orthogonal to N (the
+ * contraction with them takes the transverse-traceless part). */
+void orc_waveform(const orc_sys *s, const double y[12], double R, const double P[3], const double Q[3],
+                  double out[2])
+{
+    double g[12], h[3][3], r, hp = 0.0, hc = 0.0;
+    int i, j;
+    orc_gradient(s, y, g);                 /* g[3..5] = dH/dp = dr/dt */
+    r = norm3(y);
+    for (i = 0; i < 3; i++)
+        for (j = 0; j < 3; j++)
+            h[i][j] = 4.0 * s->eta / R * (g[3 + i] * g[3 + j] - (y[i] / r) * (y[j] / r) / r);
+    for (i = 0; i < 3; i++)
+        for (j = 0; j < 3; j++) {
+            hp += 0.5 * (P[i] * P[j] - Q[i] * Q[j]) * h[i][j];
+            hc += 0.5 * (P[i] * Q[j] + Q[i] * P[j]) * h[i][j];
+        }
+    out[0] = hp;
+    out[1] = hc;
+}
+
 /* ------------------------------------------------------ manifold correction */
 int orc_correct(const orc_sys *s, double y[12], const double ref[4],
                 double newton_tol, int newton_max, double det_min,

@@ -105,6 +105,12 @@ int orc_correct_rule(const orc_sys *s, double y[12], const double ref[4],
                      double newton_tol, int newton_max, double det_min, int apply_small, int mode,
                      int *iters, double alpha_beta[2]);
 
+/* Gravitational-wave polarisations (Eq. 14) from the mass quadrupole
+ * field of the relative orbit, observer at distance R along N = P x Q:
+ * out = (h_plus, h_cross). */
+void orc_waveform(const orc_sys *s, const double y[12], double R, const double P[3], const double Q[3],
+                  double out[2]);
+
 /* Initial conditions of a scan cell: cell = (x0, pfac, theta1, phi1,
  * theta2, phi2, beta, chi1, chi2).  r = (x0,0,0), p = (0, pfac/sqrt(x0), 0),
  * S_i = chi_i m_i^2 (sin th_i cos ph_i, sin th_i sin ph_i, cos th_i). */

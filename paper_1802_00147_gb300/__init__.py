@@ -100,6 +100,7 @@ def lib():
         L.scan_autotune.argtypes = [vp, i, P(i), P(i), P(i), P(i), P(i)]
         L.scan_last_run_timing.argtypes = [vp, P(d), P(i)]
         L.scan_fp64_peak.argtypes = [vp, i, P(d)]
+        L.scan_waveform.argtypes = [vp, d, P(d), P(d), vp, vp]
         L.scan_summary_noalloc.argtypes = [_ct.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, d, d, vp,
                                            P(ScanSummary)]
         f, u64, i64 = _ct.c_float, _ct.c_uint64, _ct.c_int64
@@ -127,7 +128,7 @@ def lib():
         L.scan_version.restype = _ct.c_char_p
         for name in ("scan_params_default", "scan_create", "scan_setup", "scan_run", "scan_read",
                      "scan_read_diag", "scan_summary", "scan_autotune", "scan_last_run_timing",
-                     "scan_fp64_peak", "scan_summary_noalloc"):
+                     "scan_fp64_peak", "scan_summary_noalloc", "scan_waveform"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -189,6 +190,12 @@ def scan_autotune(h, steps):
     _check(lib().scan_autotune(h, int(steps), *[_ct.byref(o) for o in out]), "scan_autotune")
     return dict(schedule=out[0].value, block_size=out[1].value, chunk_steps=out[2].value,
                 blocks_per_sm=out[3].value, register_variant=out[4].value)
+
+
+def scan_waveform(h, R, P, Q, hplus, hcross):
+    Pv = (_ct.c_double * 3)(*[float(v) for v in P])
+    Qv = (_ct.c_double * 3)(*[float(v) for v in Q])
+    _check(lib().scan_waveform(h, float(R), Pv, Qv, _ptr(hplus), _ptr(hcross)), "scan_waveform")
 
 
 def scan_last_run_timing(h):
@@ -341,6 +348,12 @@ class Scan:
 
     def summary(self):
         return scan_summary(self.h).as_dict()
+
+    def waveform(self, R=1.0, P=(1.0, 0.0, 0.0), Q=(0.0, 1.0, 0.0)):
+        """(h_plus, h_cross) of every orbit at its current state (scan_waveform)."""
+        hp, hc = self._out((self.n,), _np.float64), self._out((self.n,), _np.float64)
+        scan_waveform(self.h, R, P, Q, hp, hc)
+        return hp, hc
 
     def autotune(self, steps):
         return scan_autotune(self.h, steps)

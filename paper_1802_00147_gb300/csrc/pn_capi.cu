@@ -14,6 +14,7 @@
 
 #include "../../include/pnscan.h"
 #include "pn_kernels.cuh"
+#include "pn_waveform.cuh"
 
 using namespace pnscan;
 
@@ -646,6 +647,29 @@ int scan_autotune(scan_handle* h, int steps, int* schedule, int* block_size, int
     if (blocks_per_sm) *blocks_per_sm = h->bps;
     if (register_variant) *register_variant = h->minb;
     return PNSCAN_OK;
+}
+
+int scan_waveform(scan_handle* h, double R, const double* P, const double* Q, double* hplus, double* hcross)
+{
+    if (!h || !P || !Q || !(R > 0.0) || !std::isfinite(R)) return PNSCAN_ERR_ARG;
+    for (int k = 0; k < 3; k++)
+        if (!std::isfinite(P[k]) || !std::isfinite(Q[k])) return PNSCAN_ERR_ARG;
+    if (!h->loaded) return PNSCAN_ERR_STATE;
+    const int64_t n = h->S.n;
+    if (n == 0 || (!hplus && !hcross)) return PNSCAN_OK;
+    const RunCfg rc = make_run(h, 1.0, 0);
+    const bool dev = h->p.device_ptrs != 0;
+    double* dp = hplus ? (dev ? hplus : h->staging) : nullptr;
+    double* dc = hcross ? (dev ? hcross : h->staging + n) : nullptr;
+    int r = cuda_err(launch_waveform(h->S, rc, R, P, Q, dp, dc, h->stream));
+    if (r != PNSCAN_OK) return r;
+    if (!dev) {
+        if (hplus && cudaMemcpyAsync(hplus, dp, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+            return PNSCAN_ERR_CUDA;
+        if (hcross && cudaMemcpyAsync(hcross, dc, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+            return PNSCAN_ERR_CUDA;
+    }
+    return sync(h);
 }
 
 int scan_last_run_timing(scan_handle* h, double* ms, int* launches)

@@ -27,6 +27,12 @@ with no correction, the spin lengths alone (Eq. 10), the spin lengths and
 velocity scaling p = a p* to E0 (Sec. 1), and the full dual scaling:
 
     python -m paper_1802_00147_gb300.studies ablation [--n 64] [--t-end 1e4]
+
+Gravitational waveforms (Eq. 14, Sec. 4, Fig. 10, conservative case): h_plus
+and h_cross of the mass quadrupole field along the regular orbit 4 and the
+chaotic case II orbit 2, observer on the z axis, written as .npy:
+
+    python -m paper_1802_00147_gb300.studies waveform [--t-end 1e4] [--out DIR]
 """
 import argparse
 import json
@@ -160,9 +166,50 @@ def correction_ablation_study(n=64, t_end=1.0e4, h=1.0, rk_order=4, seed=1):
     return report
 
 
+def waveform_series(cells, t_end, every=10.0, h=1.0, R=1.0, P=(1.0, 0.0, 0.0), Q=(0.0, 1.0, 0.0), **opts):
+    """Sample (h_plus, h_cross) of the orbits of `cells` (n x >= 9) every
+    `every` time units from t = 0 to t_end: returns t (m), hp (m x n),
+    hc (m x n)."""
+    cells = np.ascontiguousarray(np.atleast_2d(cells), dtype=np.float64)
+    kap = cells.shape[1] > W.KAP2
+    ts, hps, hcs = [], [], []
+    with Scan(cells[:, W.BETA], kappa1=cells[:, W.KAP1] if kap else None,
+              kappa2=cells[:, W.KAP2] if kap else None, **opts) as s:
+        s.setup(cells[:, :9])
+        t = 0.0
+        while True:
+            hp, hc = s.waveform(R, P, Q)
+            ts.append(t)
+            hps.append(np.array(hp))
+            hcs.append(np.array(hc))
+            if t >= t_end - 1e-9 * every:
+                break
+            t = min(t + every, t_end)
+            s.run(t, h)
+    return np.array(ts), np.array(hps), np.array(hcs)
+
+
+def paper_waveforms(t_end=1.0e4, every=2.0, out_dir=None):
+    """Fig. 10, conservative case: orbit 4 (regular) and case II orbit 2
+    (chaotic), corrected RK5, h = 1, P = x, Q = y, N = z, R = 1."""
+    import os
+    names, cells = W.paper_orbit_cells()
+    names, cells = names[:2], cells[:2]
+    t, hp, hc = waveform_series(cells, t_end, every, rk_order=5, r_merge=0.0, r_escape=0.0)
+    report = {"t_end": t_end, "every": every, "R": 1.0}
+    for j, k in enumerate(names):
+        report[k] = {"h_plus_rms": float(np.sqrt(np.mean(hp[:, j] ** 2))),
+                     "h_plus_max": float(np.abs(hp[:, j]).max()),
+                     "h_cross_rms": float(np.sqrt(np.mean(hc[:, j] ** 2)))}
+        if out_dir:
+            os.makedirs(out_dir, exist_ok=True)
+            np.save(os.path.join(out_dir, k + "_waveform.npy"), np.stack([t, hp[:, j], hc[:, j]], axis=1))
+    return report
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["qm", "paper", "newton", "ablation"])
+    ap.add_argument("study", choices=["qm", "paper", "newton", "ablation", "waveform"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--subset", type=int, default=0)
@@ -175,6 +222,8 @@ def main():
         print(json.dumps(newton_tolerance_study(a.n, a.t_end)), flush=True)
     elif a.study == "ablation":
         print(json.dumps(correction_ablation_study(a.n, a.t_end)), flush=True)
+    elif a.study == "waveform":
+        print(json.dumps(paper_waveforms(a.t_end, out_dir=a.out)), flush=True)
     else:
         print(json.dumps(paper_scans(a.t_end, 1.0, out_dir=a.out)), flush=True)
 

@@ -129,6 +129,38 @@ def paper_cells(x0, p_y, beta, theta1, theta2, chi=1.0):
     return c
 
 
+def _polar(v):
+    v = np.asarray(v, dtype=np.float64)
+    v = v / np.linalg.norm(v)
+    return float(np.arccos(np.clip(v[2], -1.0, 1.0))), float(np.arctan2(v[1], v[0]))
+
+
+def paper_orbit_cells():
+    """The paper's single orbits as cells, with polar / azimuthal spin angles
+    from the printed unit vectors:
+    - orbit 4 (Sec. 4): (beta, r, p_y) = (1, 10, 0.274), theta1 = 1.0 rad,
+      theta2 = 1.325 rad in the x-z plane, chi = 1;
+    - case II orbit 2 (Sec. 3B): (1, 10.14, 0.365), S1 = (0.13036, 0.262852,
+      -0.955989), S2 = (0.118966, -0.13459, -0.983734), chi = 1;
+    - case II orbit 1 (Sec. 3B): (1/3, 20, 0.2461), S1 = (sin 60, 0, cos 60),
+      S2 = (sin 45, 0, cos 45), chi = 0.75.
+    Returns (names, cells)."""
+    names = ("orbit_4", "case_II_orbit_2", "case_II_orbit_1")
+    c = np.zeros((3, NFIELDS))
+    rows = ((10.0, 0.274, 1.0, (np.sin(1.0), 0, np.cos(1.0)), (np.sin(1.325), 0, np.cos(1.325)), 1.0),
+            (10.14, 0.365, 1.0, (0.13036, 0.262852, -0.955989), (0.118966, -0.13459, -0.983734), 1.0),
+            (20.0, 0.2461, 1.0 / 3.0, (np.sin(np.pi / 3), 0, 0.5), (np.sqrt(0.5), 0, np.sqrt(0.5)), 0.75))
+    for k, (x0, py, beta, s1, s2, chi) in enumerate(rows):
+        c[k, X0] = x0
+        c[k, PFAC] = py * np.sqrt(x0)
+        c[k, TH1], c[k, PH1] = _polar(s1)
+        c[k, TH2], c[k, PH2] = _polar(s2)
+        c[k, BETA] = beta
+        c[k, CHI1] = c[k, CHI2] = chi
+        c[k, KAP1] = c[k, KAP2] = 1.0
+    return names, c
+
+
 def paper_theta2_scan(theta1, n=314):
     """Sec. 3C, Fig. 6: theta2 from 0 in steps of 0.01 (314 orbits), theta1
     fixed, (beta, r, p) = (1/3, 5.65, 0.765)."""

@@ -516,6 +516,42 @@ def test_correction_ablation_drifts(orc):
     assert dS[3] <= 1e-15 and dE[3] <= 1e-14 and dJ[3] > 1e-11
 
 
+# ---------------------------------------------------- gravitational waves
+def test_waveform_of_a_circular_orbit(orc):
+    """Quadrupole field of a Newtonian circular orbit of radius a, face-on
+    (N = z, P = x, Q = y): h_plus = -(4 eta / (R a)) cos 2 phi and
+    h_cross = -(4 eta / (R a)) sin 2 phi at orbital phase phi; amplitude
+    proportional to eta / R."""
+    for beta in (1.0, 0.4):
+        s = orc.system(beta, pn_order=0, use_so=0, use_ss=0)
+        eta = beta / (1 + beta) ** 2
+        a, R = 20.0, 1e3
+        w = a ** -1.5
+        for phi in np.linspace(0.0, 2 * np.pi, 13):
+            y = np.zeros(12)
+            y[:3] = a * np.cos(phi), a * np.sin(phi), 0.0
+            y[3:6] = a * w * -np.sin(phi), a * w * np.cos(phi), 0.0
+            hp, hc = orc.waveform(s, y, R)
+            amp = 4 * eta / (R * a)
+            assert abs(hp + amp * np.cos(2 * phi)) <= 1e-14 * amp
+            assert abs(hc + amp * np.sin(2 * phi)) <= 1e-14 * amp
+
+
+def test_waveform_is_spin_two_under_frame_rotation(orc):
+    """Rotating the radiation frame (P, Q) by psi about N turns (h_plus,
+    h_cross) by 2 psi, for any state (a spin-2 field)."""
+    beta, y = paper_orbit("case_II_orbit_2")
+    s = orc.system(beta, pn_order=2, use_so=1, use_ss=1)
+    h0 = np.array(orc.waveform(s, y, 100.0))
+    for psi in (0.3, 1.1, 2.5):
+        P = (np.cos(psi), np.sin(psi), 0.0)
+        Q = (-np.sin(psi), np.cos(psi), 0.0)
+        h = np.array(orc.waveform(s, y, 100.0, P, Q))
+        c, sn = np.cos(2 * psi), np.sin(2 * psi)
+        want = np.array([c * h0[0] + sn * h0[1], -sn * h0[0] + c * h0[1]])
+        np.testing.assert_allclose(h, want, rtol=0, atol=1e-14 * np.abs(h0).max())
+
+
 # ---------------------------------------------------- set-up and statuses
 def test_setup_cell_geometry(orc):
     cells = np.array([[20.0, 0.9, 0.7, 1.1, 2.0, 4.0, 0.5, 0.8, 0.6]])
