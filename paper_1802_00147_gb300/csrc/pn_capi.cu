@@ -424,6 +424,16 @@ int scan_create(const scan_params* p, scan_handle** out)
     b.stall_group = p->debug_stall_group;
     h->sched = p->schedule == PNSCAN_SCHED_AUTO ? PNSCAN_SCHED_QUEUE : p->schedule;
     h->block = p->block_size ? p->block_size : 128;
+    // AUTO with few orbits: when every orbit fits in one resident wave of
+    // one-warp blocks (the integrators use <= 255 registers/thread, so at
+    // least 8 warps per SM are resident), the static kernel at block 32 puts
+    // each warp on its own SM sub-partition.  The run then takes one
+    // orbit's serial time; chained work-queue tasks would share
+    // sub-partitions and take up to twice that.
+    if (p->schedule == PNSCAN_SCHED_AUTO && n <= (int64_t)32 * 8 * h->num_sms) {
+        h->sched = PNSCAN_SCHED_STATIC;
+        if (!p->block_size) h->block = 32;
+    }
     h->chunk = p->chunk_steps ? p->chunk_steps : 500;
     h->bps = p->blocks_per_sm;
     h->minb = p->register_variant >= 2 ? p->register_variant : 4;
@@ -593,7 +603,7 @@ int scan_autotune(scan_handle* h, int steps, int* schedule, int* block_size, int
         layout_state(T, (char*)blk, h->S.n);
         struct Cand { int sched, block, chunk, bps, minb; };
         std::vector<Cand> cands;
-        for (int blk_sz : {64, 128}) cands.push_back({PNSCAN_SCHED_STATIC, blk_sz, 0, 0, 2});
+        for (int blk_sz : {32, 64, 128}) cands.push_back({PNSCAN_SCHED_STATIC, blk_sz, 0, 0, 2});
         for (int ch : {steps / 32, steps / 16, steps / 8})
             if (ch >= 1) cands.push_back({PNSCAN_SCHED_COMPACT, 128, ch, 0, 4});
         if (steps / 16 >= 1) cands.push_back({PNSCAN_SCHED_COMPACT, 128, steps / 16, 0, 2});
