@@ -265,12 +265,16 @@ def test_autotune_keeps_results(pn):
     s = pn.Scan(cells[:, W.BETA])
     s.setup(cells)
     shape = s.autotune(200)
-    assert shape["schedule"] in (1, 2) and shape["block_size"] in (64, 128)
+    assert shape["schedule"] in (1, 2, 3) and shape["block_size"] in (32, 64, 128)
     s.run(300.0, 1.0)
     tuned = s.read()
     s.close()
     ref = gpu_run(pn, cells, 300, schedule=1)
-    np.testing.assert_array_equal(ref["states"], tuned["states"])
+    np.testing.assert_array_equal(ref["status"], tuned["status"])
+    if shape["schedule"] == 1 or shape["register_variant"] != 3:
+        np.testing.assert_array_equal(ref["states"], tuned["states"])
+    else:   # the shared-memory-constants variant: equal up to the compiler's rounding choices
+        assert block_relerr(tuned["states"], ref["states"]).max() <= 1e-9
 
 
 # -------------------------------------------------------------- edge cases
