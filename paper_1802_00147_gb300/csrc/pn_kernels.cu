@@ -252,10 +252,17 @@ __global__ void k_init(DevState S, RunCfg rc)
 }
 
 // ----------------------------------------------------- static integrator
-// One orbit per thread for the whole run.
+// One orbit per thread for the whole run; stage and trajectory loops rolled
+// (one compiled copy of the equations of motion, as in the queue kernel's
+// default variant).
 template <bool QM, int RK>
 __global__ void __launch_bounds__(128) k_integrate_static(DevState S, RunCfg rc)
 {
+    __shared__ double hab[RK == 5 ? 36 : 1];
+    if (RK == 5) {
+        if (threadIdx.x == 0) rk5_scaled_tableau(rc.h, hab);
+        __syncthreads();
+    }
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= S.n) return;
     const int32_t st = S.status[i];
@@ -265,7 +272,7 @@ __global__ void __launch_bounds__(128) k_integrate_static(DevState S, RunCfg rc)
     o.status = ORBIT_RUNNING;
     const Coef c = load_coef<false>(S, i, rc.flags);
     const int32_t end = rc.nstep_base + rc.nsteps;
-    advance<QM, RK, Coef>(rc, c, o, end);
+    advance<QM, RK, Coef, true>(rc, c, o, end, hab);
     if (o.status == ORBIT_RUNNING && o.nstep == rc.final_step) o.status = ORBIT_DONE;
     store_orbit(S, i, o);
 }
