@@ -182,6 +182,19 @@ def cpu_oracle_rate(cells, target_s=15.0, steps_cap=20000):
             % (m, nsteps * H_STEP, steps_done, dt), cores, dt)
 
 
+def cpu_oracle_rate_single_core(cells, m=64, nsteps=20000):
+    """The oracle on one host core: m seeded orbits of the workload to t_end
+    (about 1 s of CPU work); returns orbit-steps/s."""
+    import oracle
+    from paper_1802_00147_gb300 import workloads as W
+    sub, _ = W.subset(cells, m, seed=33)
+    y0 = oracle.setup_cells(sub[:, :9])
+    t0 = time.perf_counter()
+    o = oracle.scan(y0, sub[:, W.BETA], H_STEP, nsteps, oracle.config(), nthreads=1)
+    dt = time.perf_counter() - t0
+    return float(o["t_stop"].sum() / H_STEP) / dt
+
+
 # -------------------------------------------------------------- reference
 def run_reference(args, rank, world):
     if rank != 0:
@@ -427,6 +440,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = flops / (ms_kernel * 1e-3) / 1e12
     traffic = traffic_per_run(shape["schedule"])
     cpu_rate, cpu_sample, cores, _ = cpu_oracle_rate(cells_h, target_s=15.0)
+    cpu_rate_1 = cpu_oracle_rate_single_core(cells_h)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
@@ -444,7 +458,8 @@ def run_ours(args, rank, world, local_rank):
                      "peak_measured_dfma": fp64_measured,
                      "frac_of_measured": achieved / fp64_measured},
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": cpu_sample},
+                         "sample": cpu_sample, "single_core_value": cpu_rate_1,
+                         "single_core_sample": "64 seeded orbits of the 314x314 scan to t_end=2e4 on one core"},
         "e2e": {"value": e2e_steps / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         # per step: k_setup_cells, k_init, the run's integrator (+ compaction) launches,

@@ -246,6 +246,22 @@ def test_schedules_chunks_and_pointers_are_bit_identical(pn):
     assert np.median(err) <= 1e-13 and err.max() <= 1e-9
 
 
+def test_qm_and_ablation_modes_are_bit_identical_across_kernels(pn):
+    """The QM term and the correction ablations through the static kernel and
+    the work-queue / compacting kernels (rolled and unrolled loops): same
+    arithmetic, identical results."""
+    cells = W.qm_grid(n=10, seed=15)
+    for extra in (dict(use_qm=1), dict(use_qm=1, correct=3), dict(correct=2, rk_order=5)):
+        h = 0.5 if extra.get("use_qm") else 1.0
+        a = gpu_run(pn, cells, 300, h=h, schedule=1, **extra)
+        for kw in (dict(schedule=2, chunk_steps=64, register_variant=4),
+                   dict(schedule=2, chunk_steps=64, register_variant=2),
+                   dict(schedule=3, chunk_steps=40)):
+            b = gpu_run(pn, cells, 300, h=h, **kw, **extra)
+            for k in ("states", "fli", "status", "t_stop", "integrals"):
+                np.testing.assert_array_equal(a[k], b[k], err_msg="%s %s %s" % (extra, kw, k))
+
+
 def test_graph_replay_repeats_the_run(pn):
     cells = W.small_scan(seed=8)
     s = pn.Scan(cells[:, W.BETA], schedule=2, use_graph=1)
