@@ -117,7 +117,9 @@ typedef struct scan_params {
     double sync_timeout_s;   /* host watchdog for synchronising calls (default 0: wait forever) */
     int queue_wait_limit_ms; /* bound on a work-queue task's wait for its predecessor; on expiry the
                                 kernel sets an error flag and returns, and the next synchronising
-                                call reports PNSCAN_ERR_KERNEL (default 20000) */
+                                call reports PNSCAN_ERR_KERNEL.  0 (default): 20 s plus 2 ms per
+                                step of the chunk, so that long chunks never time out while their
+                                predecessor is still running */
     int debug_stall_group;   /* test hook, default -1 (off): group g never publishes its first
                                 chunk, so the wait of its second chunk runs out */
     void *(*alloc_fn)(size_t bytes, void *ctx);  /* optional device allocator (e.g. PyTorch's) */

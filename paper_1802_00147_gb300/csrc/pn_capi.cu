@@ -198,9 +198,14 @@ std::vector<int32_t> epoch_lengths(int32_t nsteps)
 
 // Kernels launched by one run of the schedule (integrator and compaction;
 // queue resets are memsets): *launches, if not null.
-int launch_run(scan_handle* h, const RunCfg& rc, int sched, int block, int chunk, int bps, int minb,
+int launch_run(scan_handle* h, const RunCfg& rc_in, int sched, int block, int chunk, int bps, int minb,
                const DevState& S, cudaStream_t st, int* launches = nullptr)
 {
+    // default bound on a task's wait for its predecessor: 20 s plus 2 ms per
+    // step of the chunk (a step takes ~0.06 ms for a warp alone on its SM
+    // sub-partition, ~0.5 ms with 8 warps sharing it)
+    RunCfg rc = rc_in;
+    if (rc.wait_limit_ns == 0) rc.wait_limit_ns = 20000000000ull + (unsigned long long)chunk * 2000000ull;
     int dummy = 0;
     int& nl = launches ? *launches : dummy;
     nl = 0;
@@ -312,7 +317,7 @@ int scan_params_default(scan_params* p)
     p->r_escape = 1e3;
     p->schedule = PNSCAN_SCHED_AUTO;
     p->use_graph = 1;
-    p->queue_wait_limit_ms = 20000;
+    p->queue_wait_limit_ms = 0;
     p->debug_stall_group = -1;
     return PNSCAN_OK;
 }
@@ -420,7 +425,7 @@ int scan_create(const scan_params* p, scan_handle** out)
     b.fli_cap = p->fli_cap;
     b.rmerge2 = p->r_merge > 0.0 ? p->r_merge * p->r_merge : 0.0;
     b.rescape2 = p->r_escape > 0.0 ? p->r_escape * p->r_escape : 0.0;
-    b.wait_limit_ns = (unsigned long long)(p->queue_wait_limit_ms > 0 ? p->queue_wait_limit_ms : 20000) * 1000000ull;
+    b.wait_limit_ns = (unsigned long long)p->queue_wait_limit_ms * 1000000ull;   // 0: set per launch
     b.stall_group = p->debug_stall_group;
     h->sched = p->schedule == PNSCAN_SCHED_AUTO ? PNSCAN_SCHED_QUEUE : p->schedule;
     h->block = p->block_size ? p->block_size : 128;
