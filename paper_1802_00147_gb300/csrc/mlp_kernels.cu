@@ -51,6 +51,20 @@ struct Smem {
 
 size_t smem_bytes() { return sizeof(Smem); }
 
+// Training keeps the member's fp32 master weights in shared memory for the
+// whole run (the Adam moments live in registers) and reduces per-warp sums
+// of the batch's squared errors and output errors.
+struct TrainSmem {
+    Smem s;
+    float P[NPARAM];        // fp32 master weights of this member
+    float err_part[TILE / 32];
+    float d3_part[TILE / 32];
+};
+
+size_t smem_train_bytes() { return sizeof(TrainSmem); }
+
+constexpr int PER_THREAD = (NPARAM + TILE - 1) / TILE;   // parameters per thread in the Adam update
+
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
 {
     x += 0x9E3779B97F4A7C15ull;
@@ -168,10 +182,18 @@ __device__ float forward_tile(Smem& s)
 }
 
 // ------------------------------------------------------------- training
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __global__ void __launch_bounds__(TILE) k_mlp_train(TrainArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem& s = *reinterpret_cast<Smem*>(smem_raw);
+    TrainSmem& ts = *reinterpret_cast<TrainSmem*>(smem_raw);
+    Smem& s = ts.s;
     const int member = blockIdx.x;
     const int r = threadIdx.x, lane = r & 31, warp = r >> 5;
     float* P = A.params + (size_t)member * NPARAM;
@@ -179,8 +201,22 @@ __global__ void __launch_bounds__(TILE) k_mlp_train(TrainArgs A)
     float* V = A.adam_v + (size_t)member * NPARAM;
     const int nsteps = A.mode == 1 ? 1 : A.steps;
 
+    // master weights to shared memory, this thread's Adam moments to registers
+    // (parameter i = r + TILE k)
+    float m_reg[PER_THREAD], v_reg[PER_THREAD];
+#pragma unroll
+    for (int k = 0; k < PER_THREAD; k++) {
+        const int i = r + TILE * k;
+        if (i < NPARAM) {
+            ts.P[i] = P[i];
+            m_reg[k] = M[i];
+            v_reg[k] = V[i];
+        }
+    }
+    __syncthreads();
+
     for (int step = 0; step < nsteps; step++) {
-        load_params(s, P);
+        load_params(s, ts.P);
         // minibatch rows
         long long idx;
         if (A.mode == 1) idx = r < A.N ? r : 0;
@@ -197,6 +233,13 @@ __global__ void __launch_bounds__(TILE) k_mlp_train(TrainArgs A)
         const float d3 = 2.f * e / (float)TILE;
         s.d3[r] = d3;
         s.err2[r] = e * e;
+        {
+            const float pe = warp_sum(e * e), pd = warp_sum(d3);
+            if (lane == 0) {
+                ts.err_part[warp] = pe;
+                ts.d3_part[warp] = pd;
+            }
+        }
         for (int n = 0; n < NH; n++) {
             const float h2 = s.H2f[r][n];
             s.D2b[r][n] = __float2bfloat16_rn(d3 * s.w3[n] * (1.f - h2 * h2));
@@ -213,7 +256,8 @@ __global__ void __launch_bounds__(TILE) k_mlp_train(TrainArgs A)
             s.grad[OFF_B2 + r] = gb2;
         } else if (r == NH) {
             float gb3 = 0.f;
-            for (int t = 0; t < TILE; t++) gb3 += s.d3[t];
+#pragma unroll
+            for (int w = 0; w < TILE / 32; w++) gb3 += ts.d3_part[w];
             s.grad[OFF_B3] = gb3;
         }
         // gW2[n][k] = sum_t D2[t][n] H1[t][k]: M = 64 (n), N = 64 (k), K = 128 (t); warp owns n-rows [16 warp, +16)
@@ -293,28 +337,44 @@ __global__ void __launch_bounds__(TILE) k_mlp_train(TrainArgs A)
             for (int i = r; i < NPARAM; i += TILE) A.grad_out[(size_t)member * NPARAM + i] = s.grad[i];
             if (r == 0) {
                 float l = 0.f;
-                for (int t = 0; t < TILE; t++) l += s.err2[t];
+#pragma unroll
+                for (int w = 0; w < TILE / 32; w++) l += ts.err_part[w];
                 A.loss_out[member] = l / (float)TILE;
             }
-            break;
+            return;
         }
         // Adam (Kingma & Ba 2015), bias-corrected moments
         const int tstep = A.step0 + step + 1;
         const float c1 = 1.f - powf(0.9f, (float)tstep), c2 = 1.f - powf(0.999f, (float)tstep);
-        for (int i = r; i < NPARAM; i += TILE) {
-            const float g = s.grad[i];
-            const float m = 0.9f * M[i] + 0.1f * g;
-            const float v = 0.999f * V[i] + 0.001f * g * g;
-            M[i] = m;
-            V[i] = v;
-            P[i] = P[i] - A.lr * (m / c1) / (sqrtf(v / c2) + 1e-8f);
+#pragma unroll
+        for (int k = 0; k < PER_THREAD; k++) {
+            const int i = r + TILE * k;
+            if (i < NPARAM) {
+                const float g = s.grad[i];
+                const float m = 0.9f * m_reg[k] + 0.1f * g;
+                const float v = 0.999f * v_reg[k] + 0.001f * g * g;
+                m_reg[k] = m;
+                v_reg[k] = v;
+                ts.P[i] = ts.P[i] - A.lr * (m / c1) / (sqrtf(v / c2) + 1e-8f);
+            }
         }
         if (A.loss_hist && r == 0) {
             float l = 0.f;
-            for (int t = 0; t < TILE; t++) l += s.err2[t];
+#pragma unroll
+            for (int w = 0; w < TILE / 32; w++) l += ts.err_part[w];
             A.loss_hist[(size_t)member * A.steps + step] = l / (float)TILE;
         }
         __syncthreads();
+    }
+    // the trained weights and moments back to the handle
+#pragma unroll
+    for (int k = 0; k < PER_THREAD; k++) {
+        const int i = r + TILE * k;
+        if (i < NPARAM) {
+            P[i] = ts.P[i];
+            M[i] = m_reg[k];
+            V[i] = v_reg[k];
+        }
     }
 }
 
@@ -484,7 +544,7 @@ cudaError_t launch_init(float* params, float* m, float* v, int members, uint64_t
 
 cudaError_t launch_train(const TrainArgs& A, int members, cudaStream_t st)
 {
-    const size_t sm = smem_bytes();
+    const size_t sm = smem_train_bytes();
     cudaError_t e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k_mlp_train<<<members, TILE, sm, st>>>(A);
