@@ -207,6 +207,39 @@ def test_flag_variants_parity(pn, opts):
     check(pn, W.uneven_batch(n=96, seed=12), 400, **opts)
 
 
+@pytest.mark.parametrize("n", [1, 31, 33, 257])
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_tail_sizes(pn, n, schedule):
+    """Batch sizes around the warp and block boundaries, through the static
+    and the work-queue kernels."""
+    cells = W.uneven_batch(n=n, seed=40 + n)
+    check(pn, cells, 150, schedule=schedule, chunk_steps=40)
+
+
+def test_degenerate_inputs_become_statuses(pn):
+    """r = 0 (1/|r| infinite), a start inside the merger radius and a start
+    beyond the escape radius are per-orbit statuses, not device faults: the
+    batch's other orbits are unaffected."""
+    cells = W.small_scan(seed=3)[:40].copy()
+    y0 = oracle.setup_cells(cells[:, :9])
+    y0[5, 0:3] = 0.0                       # r = 0
+    y0[6, 0:3] = (2.0, 0.0, 0.0)           # inside r_merge = 6
+    y0[7, 0:3] = (2.0e3, 0.0, 0.0)         # beyond r_escape = 1e3
+    s = pn.Scan(cells[:, W.BETA], schedule=2, chunk_steps=20)
+    s.setup(cells)
+    s.run(60.0, 1.0, initial_states=y0)
+    g = s.read()
+    s.close()
+    o = oracle.scan(y0, cells[:, W.BETA], 1.0, 60, oracle.config())
+    np.testing.assert_array_equal(g["status"], o["status"])
+    assert g["status"][5] == pn.ORBIT_NONFINITE
+    assert g["status"][6] == pn.ORBIT_MERGED and g["status"][7] == pn.ORBIT_ESCAPED
+    ok = np.ones(40, bool)
+    ok[5:8] = False
+    assert np.all(g["status"][ok] == pn.ORBIT_DONE)
+    assert block_relerr(g["states"][ok], o["y"][ok]).max() <= STATE_TOL
+
+
 def test_zero_spins_and_fli_cap(pn):
     cells = W.small_scan(seed=4)[::6].copy()
     cells[:20, W.CHI1] = 0.0
