@@ -64,6 +64,8 @@ def lib():
         L.orc_correct.argtypes = [P(Sys), dp, dp, d, i, d, P(i), dp]
         L.orc_correct.restype = i
         L.orc_waveform.argtypes = [P(Sys), dp, d, dp, dp, dp]
+        L.orc_newton_trace.argtypes = [P(Sys), dp, dp, i, dp, dp]
+        L.orc_newton_trace.restype = i
         L.orc_correct_rule.argtypes = [P(Sys), dp, dp, d, i, d, i, i, P(i), dp]
         L.orc_correct_rule.restype = i
         L.orc_setup_cell.argtypes = [dp, dp]
@@ -140,6 +142,15 @@ def waveform(s, y, R=1.0, P=(1.0, 0.0, 0.0), Q=(0.0, 1.0, 0.0)):
     out = _np.zeros(2)
     lib().orc_waveform(_ct.byref(s), _dp(y), float(R), _dp(Pv), _dp(Qv), _dp(out))
     return out[0], out[1]
+
+
+def newton_trace(s, y, ref, kmax=8):
+    """Dual-scaling Newton iterates (alpha_k, beta_k), k = 1..m <= kmax, of
+    Eq. 13 at the state y = (r*, p*, S) from (1, 1), no stopping rule."""
+    y, ref = _vec(y), _vec(ref)
+    a, b = _np.zeros(kmax), _np.zeros(kmax)
+    m = lib().orc_newton_trace(_ct.byref(s), _dp(y), _dp(ref), int(kmax), _dp(a), _dp(b))
+    return a[:m], b[:m]
 
 
 MODE_DUAL, MODE_SPINS, MODE_VELOCITY = 1, 2, 3

@@ -330,11 +330,67 @@ int orc_correct(const orc_sys *s, double y[12], const double ref[4],
     return orc_correct_rule(s, y, ref, newton_tol, newton_max, det_min, 1, ORC_MODE_DUAL, iters, alpha_beta);
 }
 
+/* One Newton step of Eq. 13 at (alpha, beta): F = (H(beta r*, alpha p*, S)
+ * - E0, |J(beta r*, alpha p*, S)| - J0) and its Jacobian in (alpha, beta).
+ * y holds (r*, p*, S); returns 0 and the step (da, db) to subtract, or -1
+ * where the dual scaling is singular (|det| <= det_min (|J11 J22| + |J12 J21|))
+ * or not finite. */
+static int dual_newton_step(const orc_sys *s, const double y[12], const double ref[4], double alpha,
+                            double beta, double det_min, double *da, double *db)
+{
+    double yb[12], g[12], rs[3], ps[3];
+    double J[3], rxp[3], rsxp[3], rxps[3], Jn, F1, F2, A, B, C, D, det;
+    int i;
+    memcpy(yb, y, sizeof(yb));
+    for (i = 0; i < 3; i++) {
+        rs[i] = y[i];
+        ps[i] = y[3 + i];
+        yb[i] = beta * rs[i];
+        yb[3 + i] = alpha * ps[i];
+    }
+    F1 = orc_hamiltonian(s, yb) - ref[0];
+    cross3(yb, yb + 3, rxp);
+    for (i = 0; i < 3; i++) J[i] = rxp[i] + yb[6 + i] + yb[9 + i];
+    Jn = norm3(J);
+    F2 = Jn - ref[1];
+    orc_gradient(s, yb, g);
+    A = dot3(g + 3, ps);           /* dF1/dalpha = dH/dp . p* */
+    B = dot3(g, rs);               /* dF1/dbeta  = dH/dr . r* */
+    cross3(yb, ps, rsxp);          /* d(r x p)/dalpha = (beta r*) x p* */
+    cross3(rs, yb + 3, rxps);      /* d(r x p)/dbeta  = r* x (alpha p*) */
+    C = dot3(J, rsxp) / Jn;        /* dF2/dalpha */
+    D = dot3(J, rxps) / Jn;        /* dF2/dbeta */
+    det = A * D - B * C;
+    /* The dual scaling is singular where alpha p*.dH/dp = beta r*.dH/dr
+     * (twice per orbit); there rounding noise in F would be amplified by
+     * 1/det.  Below det_min relative cancellation the dual scaling is not
+     * used for this step (the paper does not treat this case). */
+    if (!(fabs(det) > det_min * (fabs(A * D) + fabs(B * C))) || !isfinite(det)) return -1;
+    *da = (F1 * D - B * F2) / det;
+    *db = (A * F2 - C * F1) / det;
+    return 0;
+}
+
+int orc_newton_trace(const orc_sys *s, const double y[12], const double ref[4], int kmax,
+                     double *alpha, double *beta)
+{
+    double a = 1.0, b = 1.0, da, db;
+    int k;
+    for (k = 0; k < kmax; k++) {
+        if (dual_newton_step(s, y, ref, a, b, 0.0, &da, &db)) break;
+        a = a - da;
+        b = b - db;
+        alpha[k] = a;
+        beta[k] = b;
+    }
+    return k;
+}
+
 int orc_correct_rule(const orc_sys *s, double y[12], const double ref[4],
                      double newton_tol, int newton_max, double det_min, int apply_small, int mode,
                      int *iters, double alpha_beta[2])
 {
-    double rs[3], ps[3], yb[12], g[12];
+    double rs[3], ps[3], yb[12];
     double alpha = 1.0, beta = 1.0;
     int it = 0, i, converged = 0;
 
@@ -368,31 +424,8 @@ int orc_correct_rule(const orc_sys *s, double y[12], const double ref[4],
     /* mode ORC_MODE_VELOCITY (ablation): no dual scaling, straight to the
      * velocity scaling below */
     for (it = 1; mode == ORC_MODE_DUAL && it <= newton_max; it++) {
-        double J[3], rxp[3], rsxp[3], rxps[3], Jn, F1, F2, A, B, C, D, det, da, db;
-        for (i = 0; i < 3; i++) {
-            yb[i] = beta * rs[i];
-            yb[3 + i] = alpha * ps[i];
-        }
-        F1 = orc_hamiltonian(s, yb) - ref[0];
-        cross3(yb, yb + 3, rxp);
-        for (i = 0; i < 3; i++) J[i] = rxp[i] + yb[6 + i] + yb[9 + i];
-        Jn = norm3(J);
-        F2 = Jn - ref[1];
-        orc_gradient(s, yb, g);
-        A = dot3(g + 3, ps);           /* dF1/dalpha = dH/dp . p* */
-        B = dot3(g, rs);               /* dF1/dbeta  = dH/dr . r* */
-        cross3(yb, ps, rsxp);          /* d(r x p)/dalpha = (beta r*) x p* */
-        cross3(rs, yb + 3, rxps);      /* d(r x p)/dbeta  = r* x (alpha p*) */
-        C = dot3(J, rsxp) / Jn;        /* dF2/dalpha */
-        D = dot3(J, rxps) / Jn;        /* dF2/dbeta */
-        det = A * D - B * C;
-        /* The dual scaling is singular where alpha p*.dH/dp = beta r*.dH/dr
-         * (twice per orbit); there rounding noise in F would be amplified
-         * by 1/det.  Below det_min relative cancellation the dual scaling
-         * is not used for this step (the paper does not treat this case). */
-        if (!(fabs(det) > det_min * (fabs(A * D) + fabs(B * C))) || !isfinite(det)) break;
-        da = (F1 * D - B * F2) / det;
-        db = (A * F2 - C * F1) / det;
+        double da, db;
+        if (dual_newton_step(s, y, ref, alpha, beta, det_min, &da, &db)) break;
         /* stopping rule: apply the step and then test it (default), or stop
          * before applying a step already within the tolerance */
         if (!apply_small && fabs(da) <= newton_tol && fabs(db) <= newton_tol) {

@@ -111,6 +111,14 @@ int orc_correct_rule(const orc_sys *s, double y[12], const double ref[4],
 void orc_waveform(const orc_sys *s, const double y[12], double R, const double P[3], const double Q[3],
                   double out[2]);
 
+/* The dual-scaling Newton iterates of Eq. 13 from (1, 1) at the state y =
+ * (r*, p*, S) toward ref, without stopping rule or singularity guard:
+ * (alpha[k], beta[k]) after k + 1 steps, k < kmax.  Returns the number of
+ * iterates written (fewer than kmax if the Jacobian became singular or not
+ * finite). */
+int orc_newton_trace(const orc_sys *s, const double y[12], const double ref[4], int kmax,
+                     double *alpha, double *beta);
+
 /* Initial conditions of a scan cell: cell = (x0, pfac, theta1, phi1,
  * theta2, phi2, beta, chi1, chi2).  r = (x0,0,0), p = (0, pfac/sqrt(x0), 0),
  * S_i = chi_i m_i^2 (sin th_i cos ph_i, sin th_i sin ph_i, cos th_i). */

@@ -11,7 +11,8 @@ a wrong sign or coefficient, a transposed operand -- fails one of them:
 * time reversal (r, p, S) -> (r, -p, -S)                         -> RK4 + correction
 * RK4 global error order 4
 * exact restoration of E, |J|, |S_i| by the correction (Eqs. 10-13)
-* the Newton root of Eq. 13 vs an independent 2-D root finder
+* the Newton root of Eq. 13 vs an independent 2-D root finder, and its
+  quadratic convergence (a wrong Jacobian entry would make it linear)
 * FLI of an integrable orbit grows as a power law; the paper's case II
   orbits 1 / 2 are regular / chaotic (Sec. 3B, Fig. 3)
 * the Newton tolerance matters only under the stop-before-applying rule,
@@ -377,6 +378,34 @@ def test_newton_root_matches_independent_root_finder(orc):
     _, code, _, (a, b) = orc.correct(s, ystar, ref)
     assert code == 0
     assert abs(a - sol.x[0]) < 1e-12 and abs(b - sol.x[1]) < 1e-12
+
+
+def test_newton_converges_quadratically(orc):
+    """Newton's method with the exact Jacobian converges quadratically,
+    e_{k+1} <= C e_k^2, while a wrong Jacobian entry (a sign, a transposed
+    derivative) gives linear convergence at best.  From a crude RK step the
+    dual-scaling iterates of Eq. 13 are followed for 6 steps: while the error
+    is above rounding, each error is bounded by a fixed multiple of the
+    square of the previous one (and the ratio e_{k+1} / e_k collapses)."""
+    for name in ("case_II_orbit_1", "case_II_orbit_2"):
+        beta, y0 = paper_orbit(name)
+        s = orc.system(beta, pn_order=2, use_so=1, use_ss=1)
+        I0 = orc.integrals(s, y0)
+        ref = np.array([I0[0], I0[1], I0[2], I0[3]])
+        y = orc.rk4_step(s, y0, 25.0)
+        for k in (0, 1):                      # spins on their fixed lengths first (Eq. 10)
+            S = y[6 + 3 * k:9 + 3 * k]
+            y[6 + 3 * k:9 + 3 * k] = S * (ref[2 + k] / np.linalg.norm(S))
+        a, b = orc.newton_trace(s, y, ref, kmax=6)
+        assert a.size == 6
+        err = np.maximum(np.abs(a - a[-1]), np.abs(b - b[-1]))[:-1]
+        e = np.r_[max(abs(1 - a[-1]), abs(1 - b[-1])), err]     # e_0 at the start (1, 1)
+        assert e[0] > 1e-6, (name, e)                           # a visible first correction
+        for k in range(len(e) - 1):
+            if e[k] < 1e-13:
+                break
+            assert e[k + 1] <= 50.0 * e[k] ** 2 + 1e-14, (name, k, e)   # + rounding of the limit
+        assert e[2] <= 1e-3 * e[1], (name, e)
 
 
 def test_singular_scaling_falls_back_to_velocity_scaling(orc):
