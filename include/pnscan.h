@@ -64,13 +64,15 @@ extern "C" {
 #define PNSCAN_ORBIT_NONFINITE 5      /* a state component became Inf/NaN */
 
 /* ---- integrator scheduling ---- */
-#define PNSCAN_SCHED_AUTO 0    /* use the autotuned choice (scan_autotune); else STATIC at block 32 when
+#define PNSCAN_SCHED_AUTO 0    /* use the autotuned choice (scan_autotune); else PAIR at block 32 when
                                   every orbit fits in one wave of one-warp blocks (n <= 256 x SMs),
                                   QUEUE otherwise */
 #define PNSCAN_SCHED_STATIC 1  /* one orbit per thread, one pass over the batch */
 #define PNSCAN_SCHED_QUEUE 2   /* persistent work-queue kernel over (32-orbit group, step chunk) tasks */
 #define PNSCAN_SCHED_COMPACT 3 /* the work queue over epochs of 256, 512, 1024, ... steps, the running
                                   orbits compacted into a dense list between epochs (uneven batches) */
+#define PNSCAN_SCHED_PAIR 4    /* two threads per orbit (main / shadow trajectory), one pass over the
+                                  batch: half an orbit's serial time per step (small batches) */
 
 /* Per-scan configuration.  scan_params_default() fills the paper's values. */
 typedef struct scan_params {

@@ -22,7 +22,7 @@ __all__ = [
     "scan_read_diag", "scan_summary", "scan_autotune", "scan_last_run_timing",
     "scan_fp64_peak", "scan_summary_noalloc", "scan_destroy", "scan_strerror", "scan_version", "Scan",
     "OK", "ORBIT_RUNNING", "ORBIT_DONE", "ORBIT_MERGED", "ORBIT_ESCAPED",
-    "ORBIT_FLI_SATURATED", "ORBIT_NONFINITE", "SCHED_AUTO", "SCHED_STATIC", "SCHED_QUEUE", "SCHED_COMPACT",
+    "ORBIT_FLI_SATURATED", "ORBIT_NONFINITE", "SCHED_AUTO", "SCHED_STATIC", "SCHED_QUEUE", "SCHED_COMPACT", "SCHED_PAIR",
     "MLP_PARAMS", "MLP_BATCH", "Surrogate", "adaptive_features", "adaptive_select", "adaptive_merge",
 ]
 
@@ -32,7 +32,7 @@ library_path = _os.path.join(_HERE, "libpnscan.so")
 OK = 0
 ERR_ARG, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, ERR_STATE, ERR_KERNEL, ERR_NODEVICE = -1, -2, -3, -4, -5, -6, -7
 ORBIT_RUNNING, ORBIT_DONE, ORBIT_MERGED, ORBIT_ESCAPED, ORBIT_FLI_SATURATED, ORBIT_NONFINITE = range(6)
-SCHED_AUTO, SCHED_STATIC, SCHED_QUEUE, SCHED_COMPACT = 0, 1, 2, 3
+SCHED_AUTO, SCHED_STATIC, SCHED_QUEUE, SCHED_COMPACT, SCHED_PAIR = 0, 1, 2, 3, 4
 
 _ALLOC_FN = _ct.CFUNCTYPE(_ct.c_void_p, _ct.c_size_t, _ct.c_void_p)
 _FREE_FN = _ct.CFUNCTYPE(None, _ct.c_void_p, _ct.c_void_p)

@@ -213,6 +213,10 @@ int launch_run(scan_handle* h, const RunCfg& rc_in, int sched, int block, int ch
         nl = 1;
         return cuda_err(launch_integrate_static(S, rc, block, st));
     }
+    if (sched == PNSCAN_SCHED_PAIR) {
+        nl = 1;
+        return cuda_err(launch_integrate_pair(S, rc, block, st));
+    }
     const int grid = queue_grid(h, block, bps, minb);
     if (sched == PNSCAN_SCHED_QUEUE) {
         int r = reset_queue(h, st);
@@ -335,7 +339,7 @@ int scan_create(const scan_params* p, scan_handle** out)
     if (p->chunk_steps < 0 || p->blocks_per_sm < 0 || p->queue_wait_limit_ms < 0) return PNSCAN_ERR_ARG;
     if (p->register_variant != 0 && (p->register_variant < 2 || p->register_variant > 4)) return PNSCAN_ERR_ARG;
     if (p->rk_order != 0 && p->rk_order != 4 && p->rk_order != 5) return PNSCAN_ERR_ARG;
-    if (p->schedule < 0 || p->schedule > 3) return PNSCAN_ERR_ARG;
+    if (p->schedule < 0 || p->schedule > 4) return PNSCAN_ERR_ARG;
     if (p->correct < 0 || p->correct > 3) return PNSCAN_ERR_ARG;
     if ((p->alloc_fn == nullptr) != (p->free_fn == nullptr)) return PNSCAN_ERR_ARG;
     int ndev = 0;
@@ -429,14 +433,15 @@ int scan_create(const scan_params* p, scan_handle** out)
     b.stall_group = p->debug_stall_group;
     h->sched = p->schedule == PNSCAN_SCHED_AUTO ? PNSCAN_SCHED_QUEUE : p->schedule;
     h->block = p->block_size ? p->block_size : 128;
-    // AUTO with few orbits: when every orbit fits in one resident wave of
-    // one-warp blocks (the integrators use <= 255 registers/thread, so at
-    // least 8 warps per SM are resident), the static kernel at block 32 puts
-    // each warp on its own SM sub-partition.  The run then takes one
-    // orbit's serial time; chained work-queue tasks would share
-    // sub-partitions and take up to twice that.
+    // AUTO with few orbits (n <= 256 x SMs: every orbit fits in one resident
+    // wave of one-warp blocks, since the integrators use <= 255 registers per
+    // thread and so at least 8 warps per SM are resident): the paired kernel
+    // in one-warp blocks spreads the warps over the SM sub-partitions, each
+    // warp issuing half of an orbit's instructions per step.  Chained
+    // work-queue tasks would share sub-partitions and take up to twice one
+    // orbit's serial time.
     if (p->schedule == PNSCAN_SCHED_AUTO && n <= (int64_t)32 * 8 * h->num_sms) {
-        h->sched = PNSCAN_SCHED_STATIC;
+        h->sched = PNSCAN_SCHED_PAIR;
         if (!p->block_size) h->block = 32;
     }
     h->chunk = p->chunk_steps ? p->chunk_steps : 500;
@@ -488,7 +493,7 @@ int scan_run(scan_handle* h, const double* initial_states, double t_end, double 
     if (nsteps > 0 && h->S.n > 0) {
         const RunCfg rc = make_run(h, h_step, nsteps);
         if (cudaEventRecord(h->ev0, h->stream) != cudaSuccess) return PNSCAN_ERR_CUDA;
-        if (h->sched != PNSCAN_SCHED_STATIC && h->p.use_graph) r = run_graph(h, rc);
+        if (h->sched != PNSCAN_SCHED_STATIC && h->sched != PNSCAN_SCHED_PAIR && h->p.use_graph) r = run_graph(h, rc);
         else r = launch_run(h, rc, h->sched, h->block, h->chunk, h->bps, h->minb, h->S, h->stream,
                             &h->last_launches);
         if (r != PNSCAN_OK) return r;
@@ -609,6 +614,7 @@ int scan_autotune(scan_handle* h, int steps, int* schedule, int* block_size, int
         struct Cand { int sched, block, chunk, bps, minb; };
         std::vector<Cand> cands;
         for (int blk_sz : {32, 64, 128}) cands.push_back({PNSCAN_SCHED_STATIC, blk_sz, 0, 0, 2});
+        for (int blk_sz : {32, 64}) cands.push_back({PNSCAN_SCHED_PAIR, blk_sz, 0, 0, 2});
         for (int ch : {steps / 32, steps / 16, steps / 8})
             if (ch >= 1) cands.push_back({PNSCAN_SCHED_COMPACT, 128, ch, 0, 4});
         if (steps / 16 >= 1) cands.push_back({PNSCAN_SCHED_COMPACT, 128, steps / 16, 0, 2});
@@ -651,7 +657,7 @@ int scan_autotune(scan_handle* h, int steps, int* schedule, int* block_size, int
         h->block = bestc.block;
         // a tuned chunk is a fraction of the tuning run; keep the same number
         // of chunks per run length as a lower bound on the task count
-        h->chunk = bestc.sched != PNSCAN_SCHED_STATIC ? bestc.chunk : h->chunk;
+        h->chunk = (bestc.sched != PNSCAN_SCHED_STATIC && bestc.sched != PNSCAN_SCHED_PAIR) ? bestc.chunk : h->chunk;
         h->bps = bestc.bps;
         h->minb = bestc.minb;
         h->tuned = true;

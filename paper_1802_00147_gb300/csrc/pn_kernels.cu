@@ -277,6 +277,123 @@ __global__ void __launch_bounds__(128) k_integrate_static(DevState S, RunCfg rc)
     store_orbit(S, i, o);
 }
 
+// ------------------------------------------------ paired static integrator
+// Two lanes per orbit: the even lane of a pair integrates the main
+// trajectory, the odd lane the shadow.  Each lane issues half of an orbit's
+// instructions per step, so a batch too small to fill the SM sub-partitions
+// finishes in about half the time.  The lanes exchange data only where the
+// method couples the trajectories: the termination tests after each step
+// (non-finite either side; merger / escape on the main trajectory) and the
+// FLI renormalisation every `renorm` steps (the shadow lane needs the main
+// state; the main lane the new distance).  Shuffles are masked to the pair,
+// whose lanes always take the same branches.  The operations and their order
+// per trajectory are those of advance(): results are bit-identical.
+template <bool QM, int RK>
+__global__ void __launch_bounds__(128) k_integrate_pair(DevState S, RunCfg rc)
+{
+    __shared__ double hab[RK == 5 ? 36 : 1];
+    if (RK == 5) {
+        if (threadIdx.x == 0) rk5_scaled_tableau(rc.h, hab);
+        __syncthreads();
+    }
+    extern __shared__ double kst_dyn[];          // RK5 stage derivatives (rk_order 5 only)
+    double* kst = kst_dyn + threadIdx.x;
+    const int kstride = (int)blockDim.x;
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = gt >> 1;                   // both lanes of a pair share i
+    const bool shadow = (gt & 1) != 0;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned pair = 3u << (lane & ~1u);
+    const int main_lane = (int)(lane & ~1u), shadow_lane = (int)(lane | 1u);
+    if (i >= S.n) return;
+    const int32_t st0 = S.status[i];
+    if (st0 != ORBIT_RUNNING && st0 != ORBIT_DONE) return;
+    const int64_t n = S.ld;
+    const Coef c = load_coef<false>(S, i, rc.flags);
+    Vec12 y;
+    load12<false>(shadow ? S.ys : S.y, n, i, y);
+    const int rb = shadow ? 4 : 0;
+    Ref ref;
+    ref.E = S.ref[(rb + 0) * n + i];
+    ref.J = S.ref[(rb + 1) * n + i];
+    ref.S1 = S.ref[(rb + 2) * n + i];
+    ref.S2 = S.ref[(rb + 3) * n + i];
+    double acc = S.fli_acc[i];
+    const double t0 = S.t[i];
+    const int32_t n0 = S.nstep[i];
+    int32_t nstep = n0, iters = 0, skips = 0, last_kind = S.last_kind[i];
+    int32_t status = ORBIT_RUNNING;
+    const int32_t step_end = rc.nstep_base + rc.nsteps;
+    double* yv = &y.r[0];
+    while (nstep < step_end) {
+        if (RK == 5) rk5_step_rolled<QM, Coef>(c, y, hab, kst, kstride);
+        else rk4_step_rolled<QM, Coef>(c, y, rc.h);
+        if (rc.correct) {
+            int kind;
+            iters += correct<QM, Coef>(c, y, ref, rc.newton, &kind);
+            skips += kind != CORR_DUAL;
+            if (!shadow) last_kind = kind;
+        }
+        nstep++;
+        const int fin = finite12(y) ? 1 : 0;
+        if (!(fin & __shfl_xor_sync(pair, fin, 1))) { status = ORBIT_NONFINITE; break; }
+        int code = 0;
+        if (!shadow) {
+            const double rr2 = dot3(y.r, y.r);
+            if (rc.rmerge2 > 0.0 && rr2 < rc.rmerge2) code = ORBIT_MERGED;
+            else if (rc.rescape2 > 0.0 && rr2 > rc.rescape2) code = ORBIT_ESCAPED;
+        }
+        code = __shfl_sync(pair, code, main_lane);
+        if (code) { status = code; break; }
+        if (rc.renorm > 0 && (nstep % rc.renorm) == 0) {
+            double a[12];
+#pragma unroll
+            for (int k = 0; k < 12; k++) a[k] = __shfl_sync(pair, yv[k], main_lane);
+            double d = 0.0;
+            if (shadow) {
+                double dv[12];
+                double d2 = 0.0;
+#pragma unroll
+                for (int k = 0; k < 12; k++) {
+                    dv[k] = yv[k] - a[k];
+                    d2 = fma(dv[k], dv[k], d2);
+                }
+                d = sqrt(d2);
+                const double f = rc.d0 / d;
+#pragma unroll
+                for (int k = 0; k < 12; k++) yv[k] = fma(f, dv[k], a[k]);
+                ref = integrals<QM, Coef>(c, y);
+            }
+            d = __shfl_sync(pair, d, shadow_lane);
+            int sat = 0;
+            if (!shadow) {
+                acc += log10(d / rc.d0);
+                sat = rc.fli_cap > 0.0 && acc >= rc.fli_cap;
+            }
+            if (__shfl_sync(pair, sat, main_lane)) { status = ORBIT_FLI_SATURATED; break; }
+        }
+    }
+    if (status == ORBIT_RUNNING && nstep == rc.final_step) status = ORBIT_DONE;
+    const int32_t it_pair = iters + __shfl_xor_sync(pair, iters, 1);
+    const int32_t sk_pair = skips + __shfl_xor_sync(pair, skips, 1);
+    if (shadow) {
+        store12(S.ys, n, i, y);
+        S.ref[4 * n + i] = ref.E;
+        S.ref[5 * n + i] = ref.J;
+        S.ref[6 * n + i] = ref.S1;
+        S.ref[7 * n + i] = ref.S2;
+    } else {
+        store12(S.y, n, i, y);
+        S.fli_acc[i] = acc;
+        S.t[i] = t0 + (double)(nstep - n0) * rc.h;
+        S.nstep[i] = nstep;
+        S.status[i] = status;
+        S.newton_iters[i] += it_pair;
+        S.n_skip[i] += sk_pair;
+        S.last_kind[i] = last_kind;
+    }
+}
+
 // ------------------------------------------- persistent work-queue integrator
 // Tasks are (chunk c, group g): advance the 32 orbits of group g (one warp)
 // through steps [c K, (c+1) K) of the run.  Warps claim tasks in order from
@@ -575,6 +692,28 @@ static void launch_static(DevState S, RunCfg rc, int block, cudaStream_t st)
     }
     if (rc.flags.use_qm) k_integrate_static<true, RK><<<grid_for(S.n, block), block, sm, st>>>(S, rc);
     else k_integrate_static<false, RK><<<grid_for(S.n, block), block, sm, st>>>(S, rc);
+}
+
+template <int RK>
+static void launch_pair(DevState S, RunCfg rc, int block, cudaStream_t st)
+{
+    const size_t sm = RK == 5 ? rk5_smem_bytes(block) : 0;
+    if (sm > 48 * 1024) {
+        cudaFuncSetAttribute(k_integrate_pair<true, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_integrate_pair<false, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    }
+    const unsigned grid = grid_for(2 * S.n, block);
+    if (rc.flags.use_qm) k_integrate_pair<true, RK><<<grid, block, sm, st>>>(S, rc);
+    else k_integrate_pair<false, RK><<<grid, block, sm, st>>>(S, rc);
+}
+
+cudaError_t launch_integrate_pair(DevState S, RunCfg rc, int block, cudaStream_t st)
+{
+    if (S.n == 0 || rc.nsteps <= 0) return cudaSuccess;
+    if (block <= 0 || block > 128 || block % 32) return cudaErrorInvalidValue;
+    if (rc.rk_order == 5) launch_pair<5>(S, rc, block, st);
+    else launch_pair<4>(S, rc, block, st);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_integrate_static(DevState S, RunCfg rc, int block, cudaStream_t st)

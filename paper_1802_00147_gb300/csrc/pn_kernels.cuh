@@ -95,6 +95,8 @@ cudaError_t launch_setup_cells(const double* cells_aos, int64_t n, DevState S, i
 cudaError_t launch_load_states(const double* states_aos, int64_t n, DevState S, cudaStream_t st);
 cudaError_t launch_init(DevState S, RunCfg rc, cudaStream_t st);
 cudaError_t launch_integrate_static(DevState S, RunCfg rc, int block, cudaStream_t st);
+// Two lanes per orbit (main / shadow trajectory), one pass over the batch.
+cudaError_t launch_integrate_pair(DevState S, RunCfg rc, int block, cudaStream_t st);
 // minb: variant of the queue kernel: 2 resident 128-thread blocks per SM
 // with the per-orbit constants in registers (up to 255 per thread), or 3
 // with them in shared memory (168 registers)

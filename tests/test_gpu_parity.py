@@ -208,7 +208,7 @@ def test_flag_variants_parity(pn, opts):
 
 
 @pytest.mark.parametrize("n", [1, 31, 33, 257])
-@pytest.mark.parametrize("schedule", [1, 2])
+@pytest.mark.parametrize("schedule", [1, 2, 4])
 def test_tail_sizes(pn, n, schedule):
     """Batch sizes around the warp and block boundaries, through the static
     and the work-queue kernels."""
@@ -225,19 +225,20 @@ def test_degenerate_inputs_become_statuses(pn):
     y0[5, 0:3] = 0.0                       # r = 0
     y0[6, 0:3] = (2.0, 0.0, 0.0)           # inside r_merge = 6
     y0[7, 0:3] = (2.0e3, 0.0, 0.0)         # beyond r_escape = 1e3
-    s = pn.Scan(cells[:, W.BETA], schedule=2, chunk_steps=20)
-    s.setup(cells)
-    s.run(60.0, 1.0, initial_states=y0)
-    g = s.read()
-    s.close()
     o = oracle.scan(y0, cells[:, W.BETA], 1.0, 60, oracle.config())
-    np.testing.assert_array_equal(g["status"], o["status"])
-    assert g["status"][5] == pn.ORBIT_NONFINITE
-    assert g["status"][6] == pn.ORBIT_MERGED and g["status"][7] == pn.ORBIT_ESCAPED
-    ok = np.ones(40, bool)
-    ok[5:8] = False
-    assert np.all(g["status"][ok] == pn.ORBIT_DONE)
-    assert block_relerr(g["states"][ok], o["y"][ok]).max() <= STATE_TOL
+    for kw in (dict(schedule=4), dict(schedule=2, chunk_steps=20)):
+        s = pn.Scan(cells[:, W.BETA], **kw)
+        s.setup(cells)
+        s.run(60.0, 1.0, initial_states=y0)
+        g = s.read()
+        s.close()
+        np.testing.assert_array_equal(g["status"], o["status"])
+        assert g["status"][5] == pn.ORBIT_NONFINITE
+        assert g["status"][6] == pn.ORBIT_MERGED and g["status"][7] == pn.ORBIT_ESCAPED
+        ok = np.ones(40, bool)
+        ok[5:8] = False
+        assert np.all(g["status"][ok] == pn.ORBIT_DONE)
+        assert block_relerr(g["states"][ok], o["y"][ok]).max() <= STATE_TOL
 
 
 def test_zero_spins_and_fli_cap(pn):
@@ -260,15 +261,23 @@ def test_schedules_chunks_and_pointers_are_bit_identical(pn):
     # queue kernel with the stage / trajectory loops unrolled (2) and rolled (4)
     r2 = gpu_run(pn, cells, 300, schedule=2, chunk_steps=64, register_variant=2)
     r4 = gpu_run(pn, cells, 300, schedule=3, chunk_steps=64, register_variant=4)
-    for other in (b, c, d, f, g, r2, r4):
+    # two lanes per orbit (main / shadow), one and three scan_run calls
+    p1 = gpu_run(pn, cells, 300, schedule=4, block_size=32)
+    p3 = gpu_run(pn, cells, 300, schedule=4, block_size=64, chunks=3, read_diag=True)
+    for other in (b, c, d, f, g, r2, r4, p1, p3):
         for k in ("states", "fli", "status", "t_stop", "integrals"):
             np.testing.assert_array_equal(a[k], other[k], err_msg=k)
-    # RK5: static kernel, queue kernel unrolled (2) and rolled (4)
+    a_diag = gpu_run(pn, cells, 300, schedule=1, chunks=3, read_diag=True)
+    for k in ("shadow", "newton_iters", "n_skip", "last_kind"):
+        np.testing.assert_array_equal(a_diag[k], p3[k], err_msg="pair " + k)
+    # RK5: static kernel, queue kernel unrolled (2) and rolled (4), paired kernel
     a5 = gpu_run(pn, cells, 200, schedule=1, rk_order=5)
-    for rv in (2, 4):
-        o5 = gpu_run(pn, cells, 200, schedule=2, chunk_steps=64, rk_order=5, register_variant=rv)
+    for kw in (dict(schedule=2, chunk_steps=64, register_variant=2),
+               dict(schedule=2, chunk_steps=64, register_variant=4), dict(schedule=4)):
+        rv = kw.get("register_variant", "pair")
+        o5 = gpu_run(pn, cells, 200, rk_order=5, **kw)
         for k in ("states", "fli", "status", "t_stop", "integrals"):
-            np.testing.assert_array_equal(a5[k], o5[k], err_msg="rk5 variant %d %s" % (rv, k))
+            np.testing.assert_array_equal(a5[k], o5[k], err_msg="rk5 variant %s %s" % (rv, k))
     # the shared-memory-constants variant is compiled separately: the same
     # arithmetic up to the compiler's rounding choices, so equal statuses and
     # states within rounding (amplified near merger)
@@ -289,7 +298,7 @@ def test_qm_and_ablation_modes_are_bit_identical_across_kernels(pn):
         a = gpu_run(pn, cells, 300, h=h, schedule=1, **extra)
         for kw in (dict(schedule=2, chunk_steps=64, register_variant=4),
                    dict(schedule=2, chunk_steps=64, register_variant=2),
-                   dict(schedule=3, chunk_steps=40)):
+                   dict(schedule=3, chunk_steps=40), dict(schedule=4)):
             b = gpu_run(pn, cells, 300, h=h, **kw, **extra)
             for k in ("states", "fli", "status", "t_stop", "integrals"):
                 np.testing.assert_array_equal(a[k], b[k], err_msg="%s %s %s" % (extra, kw, k))
@@ -314,13 +323,13 @@ def test_autotune_keeps_results(pn):
     s = pn.Scan(cells[:, W.BETA])
     s.setup(cells)
     shape = s.autotune(200)
-    assert shape["schedule"] in (1, 2, 3) and shape["block_size"] in (32, 64, 128)
+    assert shape["schedule"] in (1, 2, 3, 4) and shape["block_size"] in (32, 64, 128)
     s.run(300.0, 1.0)
     tuned = s.read()
     s.close()
     ref = gpu_run(pn, cells, 300, schedule=1)
     np.testing.assert_array_equal(ref["status"], tuned["status"])
-    if shape["schedule"] == 1 or shape["register_variant"] != 3:
+    if shape["schedule"] in (1, 4) or shape["register_variant"] != 3:
         np.testing.assert_array_equal(ref["states"], tuned["states"])
     else:   # the shared-memory-constants variant: equal up to the compiler's rounding choices
         assert block_relerr(tuned["states"], ref["states"]).max() <= 1e-9
