@@ -64,9 +64,9 @@ extern "C" {
 #define PNSCAN_ORBIT_NONFINITE 5      /* a state component became Inf/NaN */
 
 /* ---- integrator scheduling ---- */
-#define PNSCAN_SCHED_AUTO 0    /* use the autotuned choice (scan_autotune); else PAIR at block 32 when
-                                  every orbit fits in one wave of one-warp blocks (n <= 256 x SMs),
-                                  QUEUE otherwise */
+#define PNSCAN_SCHED_AUTO 0    /* use the autotuned choice (scan_autotune); else, at block 32, PAIR for
+                                  n <= 128 x SMs and STATIC for n <= 256 x SMs (every orbit in one
+                                  wave of one-warp blocks); QUEUE otherwise */
 #define PNSCAN_SCHED_STATIC 1  /* one orbit per thread, one pass over the batch */
 #define PNSCAN_SCHED_QUEUE 2   /* persistent work-queue kernel over (32-orbit group, step chunk) tasks */
 #define PNSCAN_SCHED_COMPACT 3 /* the work queue over epochs of 256, 512, 1024, ... steps, the running

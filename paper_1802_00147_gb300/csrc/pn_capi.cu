@@ -433,15 +433,16 @@ int scan_create(const scan_params* p, scan_handle** out)
     b.stall_group = p->debug_stall_group;
     h->sched = p->schedule == PNSCAN_SCHED_AUTO ? PNSCAN_SCHED_QUEUE : p->schedule;
     h->block = p->block_size ? p->block_size : 128;
-    // AUTO with few orbits (n <= 256 x SMs: every orbit fits in one resident
-    // wave of one-warp blocks, since the integrators use <= 255 registers per
-    // thread and so at least 8 warps per SM are resident): the paired kernel
-    // in one-warp blocks spreads the warps over the SM sub-partitions, each
-    // warp issuing half of an orbit's instructions per step.  Chained
-    // work-queue tasks would share sub-partitions and take up to twice one
-    // orbit's serial time.
+    // AUTO with few orbits.  Chained work-queue tasks would share SM
+    // sub-partitions and take up to twice one orbit's serial time, so:
+    // - n <= 128 x SMs (one warp of 32 orbits per sub-partition): the paired
+    //   kernel in one-warp blocks, each warp issuing half of an orbit's
+    //   instructions per step (2,048-16,384 orbits: 1.2-2x faster than static);
+    // - n <= 256 x SMs (every orbit in one resident wave of one-warp blocks;
+    //   the integrators use <= 255 registers per thread, so at least 8 warps
+    //   per SM are resident): the static kernel in one-warp blocks.
     if (p->schedule == PNSCAN_SCHED_AUTO && n <= (int64_t)32 * 8 * h->num_sms) {
-        h->sched = PNSCAN_SCHED_PAIR;
+        h->sched = n <= (int64_t)32 * 4 * h->num_sms ? PNSCAN_SCHED_PAIR : PNSCAN_SCHED_STATIC;
         if (!p->block_size) h->block = 32;
     }
     h->chunk = p->chunk_steps ? p->chunk_steps : 500;
