@@ -78,6 +78,12 @@ def test_bad_arguments_are_rejected_before_any_device_work(pn):
     p.n = 0
     p.pn_order = 3
     assert L.scan_create(ctypes.byref(p), ctypes.byref(h)) == pn.ERR_ARG
+    for field, bad in (("schedule", 5), ("schedule", -1), ("correct", 4), ("rk_order", 3),
+                       ("register_variant", 1), ("register_variant", 5), ("queue_wait_limit_ms", -1)):
+        p = pn.scan_params_default()
+        p.n = 4
+        setattr(p, field, bad)
+        assert L.scan_create(ctypes.byref(p), ctypes.byref(h)) == pn.ERR_ARG, (field, bad)
     assert h.value is None
     assert L.scan_run(None, None, 1.0, 1.0) == pn.ERR_ARG
     assert L.scan_read(None, None, None, None, None, None) == pn.ERR_ARG
