@@ -59,6 +59,8 @@ struct TrainSmem {
     float P[NPARAM];        // fp32 master weights of this member
     float err_part[TILE / 32];
     float d3_part[TILE / 32];
+    float red_out[2][2][NH];           // output-layer / b2 gradient partials over two row halves
+    float red_in[2][NIN + 1][NH];      // first-layer gradient partials over two row halves
 };
 
 size_t smem_train_bytes() { return sizeof(TrainSmem); }
@@ -245,20 +247,18 @@ __global__ void __launch_bounds__(TILE) k_mlp_train(TrainArgs A)
             s.D2b[r][n] = __float2bfloat16_rn(d3 * s.w3[n] * (1.f - h2 * h2));
         }
         __syncthreads();
-        // output layer and b2 gradients (reductions over the batch)
-        if (r < NH) {
+        // output layer and b2 gradients (reductions over the batch): thread r
+        // sums unit r % NH over half r / NH of the rows; halves combined below
+        {
+            static_assert(TILE == 2 * NH, "two row halves per hidden unit");
+            const int u = r % NH, half = r / NH;
             float gw3 = 0.f, gb2 = 0.f;
-            for (int t = 0; t < TILE; t++) {
-                gw3 = fmaf(s.d3[t], s.H2f[t][r], gw3);
-                gb2 += __bfloat162float(s.D2b[t][r]);
+            for (int t = half * (TILE / 2); t < (half + 1) * (TILE / 2); t++) {
+                gw3 = fmaf(s.d3[t], s.H2f[t][u], gw3);
+                gb2 += __bfloat162float(s.D2b[t][u]);
             }
-            s.grad[OFF_W3 + r] = gw3;
-            s.grad[OFF_B2 + r] = gb2;
-        } else if (r == NH) {
-            float gb3 = 0.f;
-#pragma unroll
-            for (int w = 0; w < TILE / 32; w++) gb3 += ts.d3_part[w];
-            s.grad[OFF_B3] = gb3;
+            ts.red_out[half][0][u] = gw3;
+            ts.red_out[half][1][u] = gb2;
         }
         // gW2[n][k] = sum_t D2[t][n] H1[t][k]: M = 64 (n), N = 64 (k), K = 128 (t); warp owns n-rows [16 warp, +16)
         {
@@ -320,17 +320,35 @@ __global__ void __launch_bounds__(TILE) k_mlp_train(TrainArgs A)
                     }
         }
         __syncthreads();
-        // first-layer gradients: gW1[j][i] = sum_t D1[t][j] z[t][i], gb1[j] = sum_t D1[t][j]
-        for (int o = r; o < NH * (NIN + 1); o += TILE) {
-            const int j = o / (NIN + 1), i = o % (NIN + 1);
-            float g = 0.f;
-            if (i < NIN) {
-                for (int t = 0; t < TILE; t++) g = fmaf(s.D1f[t][j], s.z[t][i], g);
-                s.grad[OFF_W1 + j * NIN + i] = g;
-            } else {
-                for (int t = 0; t < TILE; t++) g += s.D1f[t][j];
-                s.grad[OFF_B1 + j] = g;
+        // first-layer gradients: gW1[j][i] = sum_t D1[t][j] z[t][i], gb1[j] = sum_t D1[t][j];
+        // thread r sums unit r % NH over half r / NH of the rows
+        {
+            const int j = r % NH, half = r / NH;
+            float g[NIN + 1];
+#pragma unroll
+            for (int i = 0; i <= NIN; i++) g[i] = 0.f;
+            for (int t = half * (TILE / 2); t < (half + 1) * (TILE / 2); t++) {
+                const float d = s.D1f[t][j];
+#pragma unroll
+                for (int i = 0; i < NIN; i++) g[i] = fmaf(d, s.z[t][i], g[i]);
+                g[NIN] += d;
             }
+#pragma unroll
+            for (int i = 0; i <= NIN; i++) ts.red_in[half][i][j] = g[i];
+        }
+        __syncthreads();
+        // combine the two row halves
+        if (r < NH) {
+            s.grad[OFF_W3 + r] = ts.red_out[0][0][r] + ts.red_out[1][0][r];
+            s.grad[OFF_B2 + r] = ts.red_out[0][1][r] + ts.red_out[1][1][r];
+#pragma unroll
+            for (int i = 0; i < NIN; i++) s.grad[OFF_W1 + r * NIN + i] = ts.red_in[0][i][r] + ts.red_in[1][i][r];
+            s.grad[OFF_B1 + r] = ts.red_in[0][NIN][r] + ts.red_in[1][NIN][r];
+        } else if (r == NH) {
+            float gb3 = 0.f;
+#pragma unroll
+            for (int w = 0; w < TILE / 32; w++) gb3 += ts.d3_part[w];
+            s.grad[OFF_B3] = gb3;
         }
         __syncthreads();
         if (A.mode == 1) {
