@@ -656,8 +656,9 @@ int scan_autotune(scan_handle* h, int steps, int* schedule, int* block_size, int
         if (r != PNSCAN_OK) return r;
         h->sched = bestc.sched;
         h->block = bestc.block;
-        // a tuned chunk is a fraction of the tuning run; keep the same number
-        // of chunks per run length as a lower bound on the task count
+        // the tuned chunk length (in steps) is kept for longer runs too: more
+        // chunks per group only shorten the tail (the static and paired
+        // schedules have no chunks and keep the previous setting)
         h->chunk = (bestc.sched != PNSCAN_SCHED_STATIC && bestc.sched != PNSCAN_SCHED_PAIR) ? bestc.chunk : h->chunk;
         h->bps = bestc.bps;
         h->minb = bestc.minb;
