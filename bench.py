@@ -351,12 +351,12 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    sched_code = {"auto": 0, "static": 1, "queue": 2, "compact": 3}[args.schedule]
-    prof_opts = dict(schedule=sched_code, chunk_steps=args.chunk) if args.profile else {}
+    sched_code = {"auto": 0, "static": 1, "queue": 2, "compact": 3, "pair": 4}[args.schedule]
+    prof_opts = dict(schedule=sched_code, chunk_steps=args.chunk, block_size=args.block) if args.profile else {}
     scan = pn.Scan(cells_h[:, W.BETA], device=True, **prof_opts)
     scan.setup(cells_d)
     if args.profile:
-        shape = {"schedule": sched_code or 2, "block_size": 128, "chunk_steps": args.chunk or 500,
+        shape = {"schedule": sched_code, "block_size": args.block or 0, "chunk_steps": args.chunk or 500,
                  "blocks_per_sm": 0}
         fp64_measured = float("nan")
     else:
@@ -487,8 +487,9 @@ def main():
     ap.add_argument("--t-end", type=float, default=T_END, help="integration time (profiling only)")
     ap.add_argument("--no-adaptive", dest="adaptive", action="store_false",
                     help="skip the uneven-batch and surrogate-adaptive 1024x1024 measurements")
-    ap.add_argument("--schedule", choices=["auto", "static", "queue", "compact"], default="auto",
-                    help="schedule for --profile runs (default: the work queue)")
+    ap.add_argument("--schedule", choices=["auto", "static", "queue", "compact", "pair"], default="auto",
+                    help="schedule for --profile runs (default: the library's AUTO choice)")
+    ap.add_argument("--block", type=int, default=0, help="threads per block for --profile runs (0: default)")
     ap.add_argument("--chunk", type=int, default=0, help="steps per task for --profile runs (0: 500)")
     ap.add_argument("--profile", action="store_true",
                     help="time the device path only (no autotune, e2e or CPU leg) for ncu runs")
