@@ -328,7 +328,9 @@ def run_uneven(n=100_000, t_end=2.0e4):
                         "x0~U[10,50], p_y 50-100% of circular; stops at r<6, r>1e3, FLI>=12; t_end 2e4",
             "schedule": shape, "kernel_ms": ms, "orbit_steps": summ["orbit_steps"],
             "value": summ["orbit_steps"] / (ms * 1e-3), "unit": UNIT,
-            "status_count": summ["status_count"]}
+            "status_count": summ["status_count"],
+            "newton_iters_per_orbit_step": summ["newton_iters"] / max(1, summ["orbit_steps"]),
+            "tflops_algorithmic": algorithmic_flops(summ["orbit_steps"], summ["newton_iters"]) / (ms * 1e-3) / 1e12}
 
 
 # -------------------------------------------------------------------- ours
@@ -404,8 +406,11 @@ def run_ours(args, rank, world, local_rank):
         return
 
     # end-to-end through the C ABI with host buffers (H2D of the cells and
-    # D2H of the per-orbit results inside the timed region)
-    host = pn.Scan(cells_h[:, W.BETA], device=False)
+    # D2H of the per-orbit results inside the timed region), with the shape
+    # the device timing was tuned to
+    tuned = {k: shape[k] for k in ("schedule", "block_size", "chunk_steps", "blocks_per_sm", "register_variant")
+             if shape.get(k)}
+    host = pn.Scan(cells_h[:, W.BETA], device=False, **tuned)
     cells9 = np.ascontiguousarray(cells_h[:, :9])
     out = dict(states=np.empty((n, 12)), integrals=np.empty((n, 6)), fli=np.empty(n),
                status=np.empty(n, np.int32), t_stop=np.empty(n))
@@ -413,6 +418,8 @@ def run_ours(args, rank, world, local_rank):
     host.run(t_end, H_STEP)
     pn.scan_read(host.h, **out)
     torch.cuda.synchronize()
+    if dist:
+        td.barrier()
     t0 = time.perf_counter()
     e2e_steps = 0
     e2e_k = max(1, args.steps)
@@ -424,8 +431,10 @@ def run_ours(args, rank, world, local_rank):
         e2e_steps += int(np.round(out["t_stop"].sum() / H_STEP))
     e2e_dt = time.perf_counter() - t0
     host.close()
-    h2d = cells9.nbytes
-    d2h = sum(a.nbytes for a in out.values())
+    # whole job: the slowest rank's time, every rank's orbit-steps and bytes
+    e2e_dt, e2e_steps = aggregate_ranks(e2e_dt, e2e_steps, dev if dist else None)
+    h2d = cells9.nbytes * world
+    d2h = sum(a.nbytes for a in out.values()) * world
 
     uneven = run_uneven() if (rank == 0 and args.adaptive) else None
     adaptive = None
