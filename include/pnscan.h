@@ -109,6 +109,7 @@ typedef struct scan_params {
     int schedule;            /* PNSCAN_SCHED_* (default AUTO) */
     int block_size;          /* threads per block, 32..128, multiple of 32 (0: 128) */
     int chunk_steps;         /* steps per work-queue task (0: 500) */
+    int epoch_steps;         /* compacting schedule: steps per epoch (0: 256, 512, 1024, ... doubling) */
     int blocks_per_sm;       /* resident blocks per SM for the queue kernel (0: occupancy maximum) */
     int register_variant;    /* RK4 queue kernel variant: 2 -- up to 255 registers/thread, 2 resident
                                 128-thread blocks per SM; 3 -- 168 registers, 3 blocks, per-orbit

@@ -50,6 +50,7 @@ class ScanParams(_ct.Structure):
         ("fli_cap", _ct.c_double), ("r_merge", _ct.c_double), ("r_escape", _ct.c_double),
         ("device_ptrs", _ct.c_int), ("cuda_stream", _ct.c_void_p),
         ("schedule", _ct.c_int), ("block_size", _ct.c_int), ("chunk_steps", _ct.c_int),
+        ("epoch_steps", _ct.c_int),
         ("blocks_per_sm", _ct.c_int), ("register_variant", _ct.c_int), ("use_graph", _ct.c_int),
         ("sync_timeout_s", _ct.c_double),
         ("queue_wait_limit_ms", _ct.c_int), ("debug_stall_group", _ct.c_int),

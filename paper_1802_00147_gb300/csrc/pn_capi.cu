@@ -180,18 +180,18 @@ int queue_grid(scan_handle* h, int block, int bps, int minb)
 }
 
 // Launch the integrator for one run on stream st (no timing).
-// Epoch lengths of the compacting schedule: 256, 512, 1024, ... steps, the
-// last one cut to the run's end, so orbits that stop early leave the dense
-// list soon after they stop.
-std::vector<int32_t> epoch_lengths(int32_t nsteps)
+// Epoch lengths of the compacting schedule: `fixed` steps each, or (fixed =
+// 0) 256, 512, 1024, ... steps; the last one cut to the run's end, so orbits
+// that stop early leave the dense list soon after they stop.
+std::vector<int32_t> epoch_lengths(int32_t nsteps, int32_t fixed)
 {
     std::vector<int32_t> e;
-    int32_t len = 256, done = 0;
+    int32_t len = fixed > 0 ? fixed : 256, done = 0;
     while (done < nsteps) {
         const int32_t l = len < nsteps - done ? len : nsteps - done;
         e.push_back(l);
         done += l;
-        if (len < (1 << 30) / 2) len *= 2;
+        if (fixed <= 0 && len < (1 << 30) / 2) len *= 2;
     }
     return e;
 }
@@ -231,7 +231,7 @@ int launch_run(scan_handle* h, const RunCfg& rc_in, int sched, int block, int ch
     if (r == PNSCAN_OK) r = cuda_err(cudaMemcpyAsync(h->q.count, h->q.count + 1, sizeof(int), cudaMemcpyDeviceToDevice, st));
     std::swap(E.order, E.order_next);
     int32_t offset = 0;
-    const std::vector<int32_t> lens = epoch_lengths(rc.nsteps);
+    const std::vector<int32_t> lens = epoch_lengths(rc.nsteps, h->p.epoch_steps);
     for (size_t k = 0; k < lens.size() && r == PNSCAN_OK; k++) {
         RunCfg erc = rc;
         erc.nstep_base = rc.nstep_base + offset;
@@ -336,7 +336,8 @@ int scan_create(const scan_params* p, scan_handle** out)
         return PNSCAN_ERR_ARG;
     if (!(p->fli_d0 > 0.0)) return PNSCAN_ERR_ARG;
     if (p->block_size && (p->block_size < 32 || p->block_size > 128 || p->block_size % 32)) return PNSCAN_ERR_ARG;
-    if (p->chunk_steps < 0 || p->blocks_per_sm < 0 || p->queue_wait_limit_ms < 0) return PNSCAN_ERR_ARG;
+    if (p->chunk_steps < 0 || p->blocks_per_sm < 0 || p->queue_wait_limit_ms < 0 || p->epoch_steps < 0)
+        return PNSCAN_ERR_ARG;
     if (p->register_variant != 0 && (p->register_variant < 2 || p->register_variant > 4)) return PNSCAN_ERR_ARG;
     if (p->rk_order != 0 && p->rk_order != 4 && p->rk_order != 5) return PNSCAN_ERR_ARG;
     if (p->schedule < 0 || p->schedule > 4) return PNSCAN_ERR_ARG;
