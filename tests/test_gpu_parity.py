@@ -166,17 +166,31 @@ def test_ragged_batch_parity(pn):
     check(pn, W.full_scan(seed=2, nx=11, nt=7), 700)           # 77 orbits
 
 
-@pytest.mark.parametrize("schedule", [1, 2])
+@pytest.mark.parametrize("schedule", [1, 2, 3])
 def test_full_scan_sampled_parity_bench_shape(pn, schedule):
-    """The 314 x 314 scan in the launch configuration the benchmark times
-    (work-queue kernel; and the static kernel), checked on a seeded sample of
-    orbits the oracle integrates one by one."""
+    """The 314 x 314 scan in the launch configurations the benchmark times
+    (the autotuner's compacting schedule at chunk 62, the work-queue kernel;
+    and the static kernel), checked on a seeded sample of orbits the oracle
+    integrates one by one."""
     cells = W.full_scan(seed=2)
-    g = gpu_run(pn, cells, 1000, schedule=schedule, read_diag=True)
+    g = gpu_run(pn, cells, 1000, schedule=schedule, chunk_steps=62 if schedule == 3 else 0, read_diag=True)
     sub, idx = W.subset(cells, 64, seed=21)
     o, s_state, s_fli = oracle_sensitivity(sub, 1000)
     gs = {k: v[idx] for k, v in g.items() if isinstance(v, np.ndarray)}
     assert_parity(gs, o, s_state, s_fli, 1000)
+
+
+def test_largest_grid_sampled_parity(pn):
+    """The largest configured batch: the 1024 x 1024 quadrupole-monopole grid
+    (1,048,576 orbits, QM term on, h = 0.5) through the default schedule,
+    checked on a seeded sample of orbits the oracle integrates one by one."""
+    cells = W.qm_grid(1024, seed=5)
+    g = gpu_run(pn, cells, 40, h=0.5, device=True, use_qm=1)
+    sub, idx = W.subset(cells, 48, seed=22)
+    o, s_state, s_fli = oracle_sensitivity(sub, 40, h=0.5, use_qm=1)
+    gs = {k: v[idx] for k, v in g.items() if isinstance(v, np.ndarray)}
+    assert_parity(gs, o, s_state, s_fli, 40)
+    assert g["summary"]["status_count"][pn.ORBIT_RUNNING] == 0
 
 
 @pytest.mark.parametrize("schedule", [2, 3])
