@@ -104,6 +104,35 @@ def qm_grid(n=1024, seed=5):
     return grid_cells(n, n, 15.0, 40.0, seed, kappa=(1.0, 10.0))
 
 
+def random_states(n, seed=31):
+    """Seeded states in random orientations: |r| ~ U[12, 40] along an isotropic
+    direction, p perpendicular to r in a random direction with |p| 60-100 %
+    of the Newtonian circular value 1/sqrt(|r|), a small random radial part,
+    and spin vectors of isotropic direction with |S_i| = chi_i m_i^2, chi_i ~
+    U[0, 1].  Also beta ~ U[0.2, 1] and kappa_i ~ U[1, 10].  Returns
+    (states n x 12, beta, kappa1, kappa2)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+
+    def unit(m):
+        v = rng.normal(size=(m, 3))
+        return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+    r = rng.uniform(12.0, 40.0, n)
+    nr = unit(n)
+    t = unit(n)
+    t = t - np.sum(t * nr, axis=1, keepdims=True) * nr
+    t /= np.linalg.norm(t, axis=1, keepdims=True)
+    pmag = rng.uniform(0.6, 1.0, n) / np.sqrt(r)
+    beta = rng.uniform(0.2, 1.0, n)
+    m1, m2 = beta / (1 + beta), 1 / (1 + beta)
+    y = np.zeros((n, 12))
+    y[:, 0:3] = r[:, None] * nr
+    y[:, 3:6] = pmag[:, None] * (t + rng.uniform(-0.1, 0.1, n)[:, None] * nr)
+    y[:, 6:9] = (rng.uniform(0, 1, n) * m1 * m1)[:, None] * unit(n)
+    y[:, 9:12] = (rng.uniform(0, 1, n) * m2 * m2)[:, None] * unit(n)
+    return y, beta, rng.uniform(1, 10, n), rng.uniform(1, 10, n)
+
+
 def subset(cells, m, seed=6):
     """A seeded subset of m cells (sorted indices) and the indices themselves."""
     rng = np.random.Generator(np.random.PCG64(seed))

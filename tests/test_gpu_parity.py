@@ -255,6 +255,30 @@ def test_degenerate_inputs_become_statuses(pn):
         assert block_relerr(g["states"][ok], o["y"][ok]).max() <= STATE_TOL
 
 
+@pytest.mark.parametrize("schedule", [2, 4])
+def test_random_orientation_states_parity(pn, schedule):
+    """Orbits in random planes with random spin directions, mass ratios and
+    kappas (QM term on), started from explicit states: every component of
+    the equations of motion and of the correction is exercised."""
+    y0, beta, k1, k2 = W.random_states(160, seed=31)
+    s = pn.Scan(beta, kappa1=k1, kappa2=k2, use_qm=1, schedule=schedule, chunk_steps=50)
+    s.run(400.0, 1.0, initial_states=y0)
+    g = s.read()
+    g.update(s.read_diag())
+    s.close()
+    o = oracle.scan(y0, beta, 1.0, 400, oracle.config(use_qm=1), kappa1=k1, kappa2=k2)
+    s_state = np.zeros(y0.shape[0])
+    s_fli = np.zeros(y0.shape[0])
+    for comp in (0, 4, 6):
+        y1 = y0.copy()
+        y1[:, comp] = np.nextafter(y1[:, comp], np.inf)
+        o1 = oracle.scan(y1, beta, 1.0, 400, oracle.config(use_qm=1), kappa1=k1, kappa2=k2)
+        same = o1["status"] == o["status"]
+        s_state = np.maximum(s_state, np.where(same, block_relerr(o1["y"], o["y"]), 0.0))
+        s_fli = np.maximum(s_fli, np.where(same, np.abs(o1["fli"] - o["fli"]), 0.0))
+    assert_parity(g, o, s_state, s_fli, 400)
+
+
 def test_zero_spins_and_fli_cap(pn):
     cells = W.small_scan(seed=4)[::6].copy()
     cells[:20, W.CHI1] = 0.0

@@ -380,6 +380,35 @@ def test_newton_root_matches_independent_root_finder(orc):
     assert abs(a - sol.x[0]) < 1e-12 and abs(b - sol.x[1]) < 1e-12
 
 
+def test_correction_restores_integrals_on_random_states(orc):
+    """Over random states, mass ratios and kappas, a crude RK4 step followed by
+    the correction (Eqs. 10-13) restores what its outcome code promises: the
+    dual scaling (code 0) E, |J| and both spin lengths to rounding; the
+    velocity scaling (code 2) E and the spin lengths, with r unchanged."""
+    rng = np.random.default_rng(123)
+    seen = set()
+    for _ in range(60):
+        beta = rng.uniform(0.1, 1.0)
+        s = orc.system(beta, kappa1=rng.uniform(1, 10), kappa2=rng.uniform(1, 10),
+                       pn_order=2, use_so=1, use_ss=1, use_qm=1)
+        y0 = random_state(rng, 10.0, 40.0)
+        I0 = orc.integrals(s, y0)
+        ref = np.array(I0[:4])
+        y1 = orc.rk4_step(s, y0, rng.uniform(2.0, 6.0))
+        y2, code, it, _ = orc.correct(s, y1, ref)
+        I2 = orc.integrals(s, y2)
+        seen.add(code)
+        assert code in (0, 2), code
+        assert abs(I2[0] - I0[0]) <= 1e-13 * abs(I0[0])
+        assert abs(I2[2] - I0[2]) <= 1e-14 * I0[2] and abs(I2[3] - I0[3]) <= 1e-14 * I0[3]
+        if code == 0:
+            assert abs(I2[1] - I0[1]) <= 1e-13 * I0[1]
+            assert it >= 1
+        else:
+            np.testing.assert_array_equal(y2[:3], y1[:3])
+    assert 0 in seen
+
+
 def test_newton_converges_quadratically(orc):
     """Newton's method with the exact Jacobian converges quadratically,
     e_{k+1} <= C e_k^2, while a wrong Jacobian entry (a sign, a transposed
