@@ -33,6 +33,11 @@ and h_cross of the mass quadrupole field along the regular orbit 4 and the
 chaotic case II orbit 2, observer on the z axis, written as .npy:
 
     python -m paper_1802_00147_gb300.studies waveform [--t-end 1e4] [--out DIR]
+
+FLI against time (Sec. 3B, Fig. 3): case II orbits 1 (regular: power-law
+growth) and 2 (chaotic: exponential growth), corrected RK5 to t = 1e5:
+
+    python -m paper_1802_00147_gb300.studies fli [--t-end 1e5] [--out DIR]
 """
 import argparse
 import json
@@ -207,9 +212,43 @@ def paper_waveforms(t_end=1.0e4, every=2.0, out_dir=None):
     return report
 
 
+def fli_curves(cells, t_end, every=1000.0, h=1.0, **opts):
+    """FLI(t) of the orbits of `cells` (n x >= 9), sampled every `every` time
+    units by runs to t1, t2, ...: returns t (m) and fli (m x n)."""
+    cells = np.ascontiguousarray(np.atleast_2d(cells), dtype=np.float64)
+    kap = cells.shape[1] > W.KAP2
+    ts, flis = [], []
+    with Scan(cells[:, W.BETA], kappa1=cells[:, W.KAP1] if kap else None,
+              kappa2=cells[:, W.KAP2] if kap else None, **opts) as s:
+        s.setup(cells[:, :9])
+        t = 0.0
+        while t < t_end - 1e-9 * every:
+            t = min(t + every, t_end)
+            s.run(t, h)
+            ts.append(t)
+            flis.append(np.array(s.read()["fli"]))
+    return np.array(ts), np.array(flis)
+
+
+def paper_fli_curves(t_end=1.0e5, every=500.0, out_dir=None, thr=5.8):
+    """Fig. 3: FLI(t) of case II orbits 1 and 2, corrected RK5, h = 1."""
+    import os
+    names, cells = W.paper_orbit_cells()
+    pick = [names.index("case_II_orbit_1"), names.index("case_II_orbit_2")]
+    t, fli = fli_curves(cells[pick], t_end, every, rk_order=5, r_merge=0.0, r_escape=0.0)
+    report = {"t_end": t_end, "every": every, "threshold": thr}
+    for j, k in enumerate(("case_II_orbit_1", "case_II_orbit_2")):
+        report[k] = {"fli_end": float(fli[-1, j]), "chaotic": bool(fli[-1, j] > thr),
+                     "fli_at": {"%g" % t[i]: float(fli[i, j]) for i in (len(t) // 10 - 1, len(t) // 2 - 1, len(t) - 1)}}
+        if out_dir:
+            os.makedirs(out_dir, exist_ok=True)
+            np.save(os.path.join(out_dir, k + "_fli.npy"), np.stack([t, fli[:, j]], axis=1))
+    return report
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["qm", "paper", "newton", "ablation", "waveform"])
+    ap.add_argument("study", choices=["qm", "paper", "newton", "ablation", "waveform", "fli"])
     ap.add_argument("--out", default=None)
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--subset", type=int, default=0)
@@ -224,6 +263,8 @@ def main():
         print(json.dumps(correction_ablation_study(a.n, a.t_end)), flush=True)
     elif a.study == "waveform":
         print(json.dumps(paper_waveforms(a.t_end, out_dir=a.out)), flush=True)
+    elif a.study == "fli":
+        print(json.dumps(paper_fli_curves(a.t_end, out_dir=a.out)), flush=True)
     else:
         print(json.dumps(paper_scans(a.t_end, 1.0, out_dir=a.out)), flush=True)
 

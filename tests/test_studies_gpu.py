@@ -67,3 +67,28 @@ def test_correction_ablation_over_a_grid():
     assert dual["dE"]["max"] <= 1e-13 and dual["dJ"]["max"] <= 1e-13 and dual["dS"]["max"] <= 1e-14
     assert spins["dS"]["max"] <= 1e-14 and spins["dE"]["median"] > 1e-11 and spins["dJ"]["median"] > 1e-12
     assert vel["dS"]["max"] <= 1e-14 and vel["dE"]["max"] <= 1e-13 and vel["dJ"]["median"] > 1e-12
+
+
+def test_fli_curves_of_the_paper_case_II_orbits():
+    """Fig. 3 / Sec. 3B: along t the FLI of case II orbit 1 grows slowly
+    (regular) and that of orbit 2 outgrows it and crosses the threshold 5.8
+    by t = 1e5 (chaotic); the end values agree with the oracle's classification."""
+    import numpy as np
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_00147_gb300 import build
+    build.build()
+    from paper_1802_00147_gb300 import studies
+    from paper_1802_00147_gb300 import workloads as W
+    import oracle
+    names, cells = W.paper_orbit_cells()
+    pick = [names.index("case_II_orbit_1"), names.index("case_II_orbit_2")]
+    t, fli = studies.fli_curves(cells[pick], 1.0e5, 5000.0, r_merge=0.0, r_escape=0.0)
+    assert t.size == 20 and fli.shape == (20, 2)
+    assert fli[-1, 0] < 5.8 < fli[-1, 1]
+    # faster growth late in the run (oracle, t = 5e4 -> 1e5: +2.05 vs +1.03)
+    assert fli[-1, 1] - fli[9, 1] > 1.5 * (fli[-1, 0] - fli[9, 0])
+    o = oracle.scan(oracle.setup_cells(cells[pick, :9]), cells[pick, W.BETA], 1.0, 100_000,
+                    oracle.config(r_merge=0, r_escape=0))
+    assert (o["fli"] > 5.8).tolist() == [False, True]
