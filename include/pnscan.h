@@ -13,6 +13,10 @@
  *     |J| by Newton's method                                            Eqs. 11-13, Sec. 3A
  *   - fast Lyapunov indicator from two nearby trajectories with periodic
  *     renormalisation                                                   Secs. 3B-3C
+ *   - gravitational-wave polarisations of the mass quadrupole field
+ *     (scan_waveform)                                                   Eq. 14, Sec. 4
+ *   - a learned surrogate of the FLI (mlp_*) and the adaptive scan it
+ *     drives (adaptive_*); not in the paper
  *
  * Units: G = c = M = 1.  r in M, p in mu, energies in mu, t in M, spins in
  * M^2 (S_i = chi_i m_i^2 S_hat_i).  A state is 12 doubles
