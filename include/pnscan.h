@@ -213,6 +213,27 @@ int scan_summary(scan_handle *h, scan_summary_t *out);
 int scan_autotune(scan_handle *h, int steps, int *schedule, int *block_size, int *chunk_steps,
                   int *blocks_per_sm, int *register_variant);
 
+/* ---- checkpoint / resume ----
+ * A checkpoint is the handle's complete orbit state: both trajectories,
+ * reference integrals, FLI accumulators, times, step counters, statuses,
+ * Newton counters and per-orbit parameters, with a header recording the
+ * orbit count and the run configuration (term flags, correction mode,
+ * Newton settings, RK order, FLI and termination settings).  Restored into
+ * a handle created with the same n and configuration, the next scan_run
+ * continues exactly where the checkpointed handle stood: the results are
+ * bit-identical to an uninterrupted run.  The paper has no counterpart.
+ *
+ * scan_checkpoint_size: bytes of a checkpoint of h (0 for a NULL handle).
+ * scan_checkpoint: write it to buf, HOST memory of at least that many bytes
+ *   (whatever device_ptrs says).  Synchronises.  Errors: ARG (NULL, small
+ *   buffer), STATE (no state yet), CUDA.
+ * scan_restore: load a checkpoint from host memory into h.  Synchronises.
+ *   Errors: ARG (not a checkpoint, a different n or configuration, short
+ *   buffer), CUDA. */
+size_t scan_checkpoint_size(scan_handle *h);
+int scan_checkpoint(scan_handle *h, void *buf, size_t bytes);
+int scan_restore(scan_handle *h, const void *buf, size_t bytes);
+
 /* Gravitational-wave polarisations of every orbit's main trajectory at its
  * current state (Eq. 14, Sec. 4): the field of the mass quadrupole moment
  * of the relative orbit (Fig. 10 uses it for orbits 2 and 4),

@@ -102,6 +102,10 @@ def lib():
         L.scan_last_run_timing.argtypes = [vp, P(d), P(i)]
         L.scan_fp64_peak.argtypes = [vp, i, P(d)]
         L.scan_waveform.argtypes = [vp, d, P(d), P(d), vp, vp]
+        L.scan_checkpoint_size.argtypes = [vp]
+        L.scan_checkpoint_size.restype = _ct.c_size_t
+        L.scan_checkpoint.argtypes = [vp, vp, _ct.c_size_t]
+        L.scan_restore.argtypes = [vp, vp, _ct.c_size_t]
         L.scan_summary_noalloc.argtypes = [_ct.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, d, d, vp,
                                            P(ScanSummary)]
         f, u64, i64 = _ct.c_float, _ct.c_uint64, _ct.c_int64
@@ -129,7 +133,8 @@ def lib():
         L.scan_version.restype = _ct.c_char_p
         for name in ("scan_params_default", "scan_create", "scan_setup", "scan_run", "scan_read",
                      "scan_read_diag", "scan_summary", "scan_autotune", "scan_last_run_timing",
-                     "scan_fp64_peak", "scan_summary_noalloc", "scan_waveform"):
+                     "scan_fp64_peak", "scan_summary_noalloc", "scan_waveform", "scan_checkpoint",
+                     "scan_restore"):
             getattr(L, name).restype = i
         _lib = L
     return _lib
@@ -197,6 +202,19 @@ def scan_waveform(h, R, P, Q, hplus, hcross):
     Pv = (_ct.c_double * 3)(*[float(v) for v in P])
     Qv = (_ct.c_double * 3)(*[float(v) for v in Q])
     _check(lib().scan_waveform(h, float(R), Pv, Qv, _ptr(hplus), _ptr(hcross)), "scan_waveform")
+
+
+def scan_checkpoint(h):
+    """The handle's complete orbit state as bytes (host memory)."""
+    n = int(lib().scan_checkpoint_size(h))
+    buf = _ct.create_string_buffer(n)
+    _check(lib().scan_checkpoint(h, buf, n), "scan_checkpoint")
+    return buf.raw
+
+
+def scan_restore(h, data):
+    buf = _ct.create_string_buffer(bytes(data), len(data))
+    _check(lib().scan_restore(h, buf, len(data)), "scan_restore")
 
 
 def scan_last_run_timing(h):
@@ -349,6 +367,14 @@ class Scan:
 
     def summary(self):
         return scan_summary(self.h).as_dict()
+
+    def checkpoint(self):
+        """Bytes of the complete orbit state (scan_checkpoint)."""
+        return scan_checkpoint(self.h)
+
+    def restore(self, data):
+        """Continue from a checkpoint of a handle with the same n and configuration."""
+        scan_restore(self.h, data)
 
     def waveform(self, R=1.0, P=(1.0, 0.0, 0.0), Q=(0.0, 1.0, 0.0)):
         """(h_plus, h_cross) of every orbit at its current state (scan_waveform)."""

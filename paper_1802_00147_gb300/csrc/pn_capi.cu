@@ -673,6 +673,88 @@ int scan_autotune(scan_handle* h, int steps, int* schedule, int* block_size, int
     return PNSCAN_OK;
 }
 
+// Checkpoint: a header with the run configuration and the handle's time and
+// step counters, then the whole device state block (both trajectories,
+// reference integrals, FLI accumulators, times, step counters, statuses,
+// Newton counters, per-orbit parameters).
+struct CheckpointHeader {
+    char magic[8];
+    int64_t n;
+    uint64_t state_bytes;
+    double t_now;
+    int64_t nstep_now;
+    Flags flags;
+    int newton_max, newton_apply_small, newton_mode, correct, rk_order, renorm;
+    double newton_tol, newton_det_min, d0, fli_cap, rmerge2, rescape2;
+};
+
+static const char kCheckpointMagic[8] = {'P', 'N', 'S', 'C', 'A', 'N', '0', '1'};
+
+static void fill_header(const scan_handle* h, CheckpointHeader& c)
+{
+    std::memset(&c, 0, sizeof(c));
+    std::memcpy(c.magic, kCheckpointMagic, sizeof(c.magic));
+    c.n = h->S.n;
+    c.state_bytes = h->state_bytes;
+    c.t_now = h->t_now;
+    c.nstep_now = h->nstep_now;
+    const RunCfg& b = h->base;
+    c.flags = b.flags;
+    c.newton_max = b.newton.max_iter;
+    c.newton_apply_small = b.newton.apply_small;
+    c.newton_mode = b.newton.mode;
+    c.correct = b.correct;
+    c.rk_order = b.rk_order;
+    c.renorm = b.renorm;
+    c.newton_tol = b.newton.tol;
+    c.newton_det_min = b.newton.det_min;
+    c.d0 = b.d0;
+    c.fli_cap = b.fli_cap;
+    c.rmerge2 = b.rmerge2;
+    c.rescape2 = b.rescape2;
+}
+
+size_t scan_checkpoint_size(scan_handle* h)
+{
+    return h ? sizeof(CheckpointHeader) + h->state_bytes : 0;
+}
+
+int scan_checkpoint(scan_handle* h, void* buf, size_t bytes)
+{
+    if (!h || !buf || bytes < scan_checkpoint_size(h)) return PNSCAN_ERR_ARG;
+    if (!h->loaded) return PNSCAN_ERR_STATE;
+    CheckpointHeader c;
+    fill_header(h, c);
+    std::memcpy(buf, &c, sizeof(c));
+    char* dst = (char*)buf + sizeof(c);
+    if (h->state_bytes &&
+        cudaMemcpyAsync(dst, h->state_block, h->state_bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        return PNSCAN_ERR_CUDA;
+    return sync(h);
+}
+
+int scan_restore(scan_handle* h, const void* buf, size_t bytes)
+{
+    if (!h || !buf || bytes < sizeof(CheckpointHeader)) return PNSCAN_ERR_ARG;
+    CheckpointHeader c, mine;
+    std::memcpy(&c, buf, sizeof(c));
+    fill_header(h, mine);
+    // the checkpoint must come from a handle with the same orbits and physics
+    mine.t_now = c.t_now;
+    mine.nstep_now = c.nstep_now;
+    if (std::memcmp(&c, &mine, sizeof(c)) != 0 || bytes < sizeof(c) + c.state_bytes) return PNSCAN_ERR_ARG;
+    const char* src = (const char*)buf + sizeof(c);
+    if (h->state_bytes &&
+        cudaMemcpyAsync(h->state_block, src, h->state_bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+        return PNSCAN_ERR_CUDA;
+    const int r = sync(h);
+    if (r != PNSCAN_OK) return r;
+    h->t_now = c.t_now;
+    h->nstep_now = (int32_t)c.nstep_now;
+    h->loaded = true;
+    return PNSCAN_OK;
+}
+
 int scan_waveform(scan_handle* h, double R, const double* P, const double* Q, double* hplus, double* hcross)
 {
     if (!h || !P || !Q || !(R > 0.0) || !std::isfinite(R)) return PNSCAN_ERR_ARG;

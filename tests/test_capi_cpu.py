@@ -89,6 +89,10 @@ def test_bad_arguments_are_rejected_before_any_device_work(pn):
     assert L.scan_read(None, None, None, None, None, None) == pn.ERR_ARG
     P3 = (ctypes.c_double * 3)(1.0, 0.0, 0.0)
     assert L.scan_waveform(None, 1.0, P3, P3, None, None) == pn.ERR_ARG
+    assert L.scan_checkpoint_size(None) == 0
+    buf = ctypes.create_string_buffer(64)
+    assert L.scan_checkpoint(None, buf, 64) == pn.ERR_ARG
+    assert L.scan_restore(None, buf, 64) == pn.ERR_ARG
     L.scan_destroy(None)
 
 

@@ -344,6 +344,36 @@ def test_qm_and_ablation_modes_are_bit_identical_across_kernels(pn):
                 np.testing.assert_array_equal(a[k], b[k], err_msg="%s %s %s" % (extra, kw, k))
 
 
+@pytest.mark.parametrize("schedule", [3, 4])
+def test_checkpoint_restore_continues_bit_identically(pn, schedule):
+    """A run interrupted by a checkpoint, its handle destroyed and a new
+    handle restored from the checkpoint, ends exactly where an uninterrupted
+    run ends: states, shadow, FLI, statuses, stop times, counters."""
+    cells = W.uneven_batch(n=600, seed=23)
+    opts = dict(kappa1=cells[:, W.KAP1], kappa2=cells[:, W.KAP2], schedule=schedule, chunk_steps=40,
+                fli_cap=12.0)
+    a = pn.Scan(cells[:, W.BETA], **opts)
+    a.setup(cells)
+    a.run(140.0, 1.0)
+    ck = a.checkpoint()
+    a.run(330.0, 1.0)
+    whole = dict(a.read(), **a.read_diag())
+    a.close()
+    b = pn.Scan(cells[:, W.BETA], **opts)
+    b.restore(ck)
+    b.run(330.0, 1.0)
+    resumed = dict(b.read(), **b.read_diag())
+    b.close()
+    for k in whole:
+        np.testing.assert_array_equal(whole[k], resumed[k], err_msg=k)
+    # a checkpoint does not load into a handle of another size or configuration
+    for bad in (pn.Scan(cells[:300, W.BETA]), pn.Scan(cells[:, W.BETA], correct=3)):
+        with pytest.raises(pn.ScanError) as e:
+            bad.restore(ck)
+        assert e.value.code == pn.ERR_ARG
+        bad.close()
+
+
 def test_graph_replay_repeats_the_run(pn):
     cells = W.small_scan(seed=8)
     s = pn.Scan(cells[:, W.BETA], schedule=2, use_graph=1)
