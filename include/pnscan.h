@@ -121,7 +121,11 @@ typedef struct scan_params {
                                 loops not unrolled (smaller code, bit-identical results)
                                 (0: 4, or the autotuned choice) */
     int use_graph;           /* 1: capture a queue / compact run in a CUDA graph and replay it (default 1) */
-    double sync_timeout_s;   /* host watchdog for synchronising calls (default 0: wait forever) */
+    double sync_timeout_s;   /* host watchdog for the stream wait of synchronising calls: after this
+                                many seconds they return PNSCAN_ERR_TIMEOUT with the work still
+                                queued (default 0: wait forever).  With host output pointers the
+                                device-to-host copies themselves wait for the preceding work; the
+                                bound is strict with device pointers (or pinned host memory) */
     int queue_wait_limit_ms; /* bound on a work-queue task's wait for its predecessor; on expiry the
                                 kernel sets an error flag and returns, and the next synchronising
                                 call reports PNSCAN_ERR_KERNEL.  0 (default): 20 s plus 2 ms per

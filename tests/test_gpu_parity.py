@@ -454,6 +454,28 @@ def test_bounded_queue_wait_reports_an_error_and_the_device_stays_usable(pn):
     np.testing.assert_array_equal(ok["states"], ref["states"])
 
 
+def test_host_watchdog_reports_a_timeout_and_the_handle_recovers(pn):
+    """sync_timeout_s bounds a synchronising call: a read issued while a long
+    (healthy) run is still on the device returns PNSCAN_ERR_TIMEOUT instead of
+    blocking; once the device has finished, the same handle reads normally."""
+    import torch
+    cells = W.subset(W.adaptive_grid(256, seed=4), 8000, seed=3)[0]
+    # device pointers: every copy of a read is asynchronous, so the only wait is
+    # the watchdog's (a copy into pageable host memory would itself block)
+    s = pn.Scan(cells[:, W.BETA], device=True, sync_timeout_s=0.05)
+    s.setup(torch.as_tensor(np.ascontiguousarray(cells[:, :9]), device="cuda"))
+    s.run(1.0e4, 1.0)                       # ~0.3 s of device work, queued asynchronously
+    with pytest.raises(pn.ScanError) as e:
+        s.read()
+    assert e.value.code == pn.ERR_TIMEOUT
+    torch.cuda.synchronize()
+    out = {k: v.cpu().numpy() for k, v in s.read().items()}
+    s.close()
+    assert np.all(out["status"] != pn.ORBIT_RUNNING)
+    ref = gpu_run(pn, cells, 10000)
+    np.testing.assert_array_equal(out["states"], ref["states"])
+
+
 def test_bad_calls_are_rejected(pn):
     s = pn.Scan(np.ones(4))
     with pytest.raises(pn.ScanError):
