@@ -1,8 +1,10 @@
 // pn_device.cuh -- FP64 device arithmetic of the manifold-corrected PN scan
 // (arXiv:1802.00147): Hamiltonian and equations of motion (Sec. 2, Eqs. 1-9),
-// classical RK4, manifold correction (Eqs. 10-13) and the FLI bookkeeping.
+// fixed-step RK4 and fifth-order Runge-Kutta steps, the manifold correction
+// (Eqs. 10-13) and its ablation modes.
 //
-// Everything here runs in registers of one thread per orbit.  On GB300 the
+// Everything here runs in the registers of the thread that owns an orbit (or,
+// in the paired kernel, one of its two trajectories).  On GB300 the
 // FP64 pipe retires two DFMA per SM per clock, so these routines are written
 // to minimise FP64 instructions: every product-sum is an fma, per-orbit
 // constants are pre-multiplied once, and the Newton solve of Eq. 13 evaluates

@@ -1,7 +1,8 @@
 // pn_kernels.cu -- kernels of the batched manifold-corrected PN scan
-// (arXiv:1802.00147, Secs. 2-3).  One orbit per thread; the state of both
-// trajectories lives in registers for a whole run (or a whole chunk of the
-// persistent work-queue kernel) and HBM is touched only at entry and exit.
+// (arXiv:1802.00147, Secs. 2-3).  One orbit per thread (a lane pair per
+// orbit in the paired kernel); the state of both trajectories lives in
+// registers for a whole run (or a whole chunk of the persistent work-queue
+// kernel) and HBM is touched only at entry and exit.
 #include <cmath>
 
 #include "pn_kernels.cuh"

@@ -97,9 +97,10 @@ cudaError_t launch_init(DevState S, RunCfg rc, cudaStream_t st);
 cudaError_t launch_integrate_static(DevState S, RunCfg rc, int block, cudaStream_t st);
 // Two lanes per orbit (main / shadow trajectory), one pass over the batch.
 cudaError_t launch_integrate_pair(DevState S, RunCfg rc, int block, cudaStream_t st);
-// minb: variant of the queue kernel: 2 resident 128-thread blocks per SM
-// with the per-orbit constants in registers (up to 255 per thread), or 3
-// with them in shared memory (168 registers)
+// minb: variant of the queue kernel: 2 -- two resident 128-thread blocks per
+// SM, per-orbit constants in registers (up to 255 per thread); 3 -- three,
+// constants in shared memory (168 registers); 4 -- as 2 with the RK stage
+// and trajectory loops rolled (the default)
 int queue_blocks_per_sm(int block, bool qm, int minb, int rk_order);
 cudaError_t launch_integrate_queue(DevState S, RunCfg rc, QueueState q, int block, int grid,
                                    int chunk, int minb, int use_order, cudaStream_t st);
