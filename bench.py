@@ -2,16 +2,22 @@
 
 One step = one pass of the whole hot path over one batch: grid set-up and
 reference integrals on the device, integration of every orbit to t_end
-(RK4 + manifold correction + FLI for both trajectories, persistent
-work-queue kernel replayed from a CUDA graph), final integrals and the
-scan-level reduction.  Workload: the 314 x 314 (x0, theta) scan, seeded
+(RK4 + manifold correction + FLI for both trajectories, in the schedule the
+library's autotuner picks, replayed from a CUDA graph), final integrals and
+the scan-level reduction.  Workload: the 314 x 314 (x0, theta) scan, seeded
 synthetic cells, h = 1, t_end = 2e4.
+
+The same JSON line also carries: the end-to-end rate through the C ABI with
+host buffers, the roofline of the integrator, the CPU oracle's rate on the
+host cores, the uneven 1e5-orbit batch and the surrogate-adaptive
+1024 x 1024 map against integrating every cell (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
 (the reference arm of this build: plain FP64 C, OpenMP over orbits) on a
-bounded sample of the same workload.
+bounded sample of the same workload.  ``--profile`` runs the device path
+alone (fixed shape, for ncu).
 """
 import argparse
 import json
