@@ -20,7 +20,8 @@ A *cell* is one orbit's scan parameters, 11 FP64 fields:
 
 The scans stand in for the paper's phase-space scans (Sec. 3C, Figs. 6-7,
 Table 3), which use no external dataset.  Random draws use numpy's PCG64
-generator with the given seed.
+generator with the given seed.  ``random_states`` draws explicit states in
+random orientations instead of cells; both sides receive the same states.
 """
 import numpy as np
 
