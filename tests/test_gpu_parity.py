@@ -214,6 +214,7 @@ def test_qm_parity(pn):
                                   dict(rk_order=5),
                                   dict(newton_apply_small=0, newton_tol=1e-8),
                                   dict(correct=2), dict(correct=3),
+                                  dict(rk_order=5, use_qm=1), dict(pn_order=1, use_qm=1, correct=3),
                                   dict(rk_order=5, schedule=1)])
 def test_flag_variants_parity(pn, opts):
     # the work-queue kernel (rolled loops) unless the variant names a schedule
