@@ -120,7 +120,9 @@ def assert_parity(g, o, s_state, s_fli, nsteps):
         assert np.median(err) <= 3 * np.median(s) + floor, (np.median(err), np.median(s))
         assert np.quantile(err, 0.99) <= 3 * np.quantile(s, 0.99) + floor
         assert err.max() <= max(STATE_TOL, 3 * s.max()), (err.max(), s.max())
-        assert np.mean(err <= STATE_TOL) >= 0.99
+        # >= 99 % within 1e-10, not counting orbits that the oracle itself
+        # cannot reproduce to 1e-10 within a factor 3 under a one-ulp move
+        assert np.mean((err <= STATE_TOL) | (s >= STATE_TOL / 3)) >= 0.99
     gi, oi = g["integrals"][ok], o["integrals"][ok]
     for col in (0, 1, 2, 3, 4, 5):
         assert np.all(np.abs(gi[:, col] - oi[:, col]) <= 1e-13 * np.abs(oi[:, col]) + 1e-300), col
