@@ -25,6 +25,7 @@ class Config(_ct.Structure):
         ("fli_d0", _ct.c_double), ("fli_renorm", _ct.c_int), ("fli_cap", _ct.c_double),
         ("r_merge", _ct.c_double), ("r_escape", _ct.c_double), ("rk_order", _ct.c_int),
         ("newton_apply_small", _ct.c_int),
+        ("rr", _ct.c_int), ("rr_gauge_a", _ct.c_double), ("rr_gauge_b", _ct.c_double),
     ]
 
 
@@ -38,9 +39,11 @@ class Sys(_ct.Structure):
 
 def config(pn_order=2, use_so=1, use_ss=1, use_qm=0, correct=1, newton_tol=1e-10,
            newton_max=50, det_min=1e-5, fli_d0=1e-9, fli_renorm=100, fli_cap=0.0,
-           r_merge=6.0, r_escape=1e3, rk_order=4, newton_apply_small=1):
+           r_merge=6.0, r_escape=1e3, rk_order=4, newton_apply_small=1, rr=0,
+           rr_gauge_a=4.0, rr_gauge_b=5.0):
     return Config(pn_order, use_so, use_ss, use_qm, correct, newton_tol, newton_max,
-                  det_min, fli_d0, fli_renorm, fli_cap, r_merge, r_escape, rk_order, newton_apply_small)
+                  det_min, fli_d0, fli_renorm, fli_cap, r_merge, r_escape, rk_order, newton_apply_small,
+                  rr, rr_gauge_a, rr_gauge_b)
 
 
 def lib():
@@ -61,6 +64,9 @@ def lib():
         L.orc_rk4_step.argtypes = [P(Sys), dp, d]
         L.orc_rk5_step.argtypes = [P(Sys), dp, d]
         L.orc_integrals.argtypes = [P(Sys), dp, dp]
+        L.orc_rr_accel.argtypes = [P(Sys), d, d, dp, dp]
+        L.orc_rhs_rr.argtypes = [P(Sys), d, d, dp, dp]
+        L.orc_rk_step_rr.argtypes = [P(Sys), d, d, i, dp, d]
         L.orc_correct.argtypes = [P(Sys), dp, dp, d, i, d, P(i), dp]
         L.orc_correct.restype = i
         L.orc_waveform.argtypes = [P(Sys), dp, d, dp, dp, dp]
@@ -125,6 +131,28 @@ def rk5_step(s, y, h):
     y = _vec(y).copy()
     lib().orc_rk5_step(_ct.byref(s), _dp(y), float(h))
     return y
+
+
+def rr_accel(s, y, gauge=(4.0, 5.0)):
+    """2.5PN radiation-reaction acceleration a_2.5PN (Eq. 6) at the state y."""
+    y = _vec(y)
+    a = _np.zeros(3)
+    lib().orc_rr_accel(_ct.byref(s), float(gauge[0]), float(gauge[1]), _dp(y), _dp(a))
+    return a
+
+
+def rhs_rr(s, y14, gauge=(4.0, 5.0)):
+    """d/dt of (r, p, S1, S2, E, |J|) with radiation reaction."""
+    y14 = _vec(y14)
+    dy = _np.zeros(14)
+    lib().orc_rhs_rr(_ct.byref(s), float(gauge[0]), float(gauge[1]), _dp(y14), _dp(dy))
+    return dy
+
+
+def rk_step_rr(s, y14, h, rk_order=4, gauge=(4.0, 5.0)):
+    y14 = _vec(y14).copy()
+    lib().orc_rk_step_rr(_ct.byref(s), float(gauge[0]), float(gauge[1]), int(rk_order), _dp(y14), float(h))
+    return y14
 
 
 def integrals(s, y):

@@ -15,6 +15,9 @@
  *   Eqs. 11-13         dual scaling p = alpha p*, r = beta r*, (alpha, beta)
  *                      from E and |J| by Newton's method (Sec. 3A)
  *   Sec. 3B/3C         FLI from two nearby trajectories (Wu et al. 2006)
+ *   Eq. 6, Sec. 3B     optional 2.5PN radiation reaction a_2.5PN, with the
+ *                      reference E and |J| carried by their integral-
+ *                      invariant relations (dissipative orbit 3, Fig. 5)
  *
  * The orbital terms H_N, H_1PN, H_2PN and H_SO are not printed in the paper
  * (Sec. 2 defers to Buonanno et al. 2006); they are the standard ADM
@@ -278,6 +281,99 @@ void orc_rk5_step(const orc_sys *s, double y[12], double h)
         y[i] = y[i] + h * (b1 * k1[i] + b3 * k3[i] + b4 * k4[i] + b5 * k5[i] + b6 * k6[i]);
 }
 
+/* ------------------------------------------------------ radiation reaction */
+/* a_2.5PN of Eq. 6 at leading order, relative motion per unit reduced mass
+ * (Iyer & Will 1993):
+ *   a = (8/5) eta u^3 [A (n.v) n - B v],  u = 1/|r|, n = u r, v = p,
+ *   A = 3 (1 + gb) v^2 + (23 + 6 ga - 9 gb) u / 3 - 5 gb (n.v)^2,
+ *   B = (2 + ga) v^2 + (2 - ga) u - 3 (1 + ga) (n.v)^2.
+ * (ga, gb) = (4, 5): A = 18 v^2 + 2u/3 - 25 (n.v)^2, B = 6 v^2 - 2u - 15 (n.v)^2,
+ * the harmonic-gauge force.  For every (ga, gb) the losses of energy and
+ * angular momentum averaged over a Kepler orbit are those of the quadrupole
+ * formula (Peters & Mathews 1963), which the tests check. */
+void orc_rr_accel(const orc_sys *s, double ga, double gb, const double y[12], double a[3])
+{
+    const double *r = y, *v = y + 3;
+    double rr = norm3(r);
+    double u = 1.0 / rr;
+    double n[3], nv, v2, A, B, k;
+    int i;
+    for (i = 0; i < 3; i++) n[i] = r[i] / rr;
+    nv = dot3(n, v);
+    v2 = dot3(v, v);
+    A = 3.0 * (1.0 + gb) * v2 + (23.0 + 6.0 * ga - 9.0 * gb) * u / 3.0 - 5.0 * gb * nv * nv;
+    B = (2.0 + ga) * v2 + (2.0 - ga) * u - 3.0 * (1.0 + ga) * nv * nv;
+    k = 8.0 / 5.0 * s->eta * u * u * u;
+    for (i = 0; i < 3; i++) a[i] = k * (A * nv * n[i] - B * v[i]);
+}
+
+/* Eqs. 6-7 with a_2.5PN on y14 = (r, p, S1, S2, E, |J|).  Along the flow
+ * dH/dt = (dH/dr).(dr/dt) + (dH/dp).(dp/dt) + sum_i (dH/dS_i).(dS_i/dt)
+ *       = (dH/dp).a  (the conservative parts cancel, Omega_i.(Omega_i x S_i) = 0),
+ * and dJ/dt = r x a (the conservative flow conserves J = L + S1 + S2), so
+ * d|J|/dt = J.(r x a)/|J|: the integral-invariant relations of Sec. 3B. */
+void orc_rhs_rr(const orc_sys *s, double ga, double gb, const double y[14], double dy[14])
+{
+    double g[12], a[3], L[3], J[3], ra[3];
+    int i;
+    orc_gradient(s, y, g);
+    orc_rr_accel(s, ga, gb, y, a);
+    for (i = 0; i < 3; i++) {
+        dy[i] = g[3 + i];              /* Eq. 6: dr/dt = dH/dp */
+        dy[3 + i] = -g[i] + a[i];      /* Eq. 6: dp/dt = -dH/dr + a_2.5PN */
+    }
+    cross3(g + 6, y + 6, dy + 6);      /* Eq. 7 */
+    cross3(g + 9, y + 9, dy + 9);
+    dy[12] = dot3(g + 3, a);
+    cross3(y, y + 3, L);
+    for (i = 0; i < 3; i++) J[i] = L[i] + y[6 + i] + y[9 + i];
+    cross3(y, a, ra);
+    dy[13] = dot3(J, ra) / norm3(J);
+}
+
+/* The RK4 and fifth-order steps of orc_rk4_step / orc_rk5_step on the
+ * 14-component system orc_rhs_rr. */
+void orc_rk_step_rr(const orc_sys *s, double ga, double gb, int rk_order, double y[14], double h)
+{
+    int i;
+    if (rk_order == 5) {
+        static const double a21 = 1.0 / 5.0;
+        static const double a31 = 3.0 / 40.0, a32 = 9.0 / 40.0;
+        static const double a41 = 44.0 / 45.0, a42 = -56.0 / 15.0, a43 = 32.0 / 9.0;
+        static const double a51 = 19372.0 / 6561.0, a52 = -25360.0 / 2187.0, a53 = 64448.0 / 6561.0,
+                            a54 = -212.0 / 729.0;
+        static const double a61 = 9017.0 / 3168.0, a62 = -355.0 / 33.0, a63 = 46732.0 / 5247.0,
+                            a64 = 49.0 / 176.0, a65 = -5103.0 / 18656.0;
+        static const double b1 = 35.0 / 384.0, b3 = 500.0 / 1113.0, b4 = 125.0 / 192.0,
+                            b5 = -2187.0 / 6784.0, b6 = 11.0 / 84.0;
+        double k1[14], k2[14], k3[14], k4[14], k5[14], k6[14], t[14];
+        orc_rhs_rr(s, ga, gb, y, k1);
+        for (i = 0; i < 14; i++) t[i] = y[i] + h * (a21 * k1[i]);
+        orc_rhs_rr(s, ga, gb, t, k2);
+        for (i = 0; i < 14; i++) t[i] = y[i] + h * (a31 * k1[i] + a32 * k2[i]);
+        orc_rhs_rr(s, ga, gb, t, k3);
+        for (i = 0; i < 14; i++) t[i] = y[i] + h * (a41 * k1[i] + a42 * k2[i] + a43 * k3[i]);
+        orc_rhs_rr(s, ga, gb, t, k4);
+        for (i = 0; i < 14; i++) t[i] = y[i] + h * (a51 * k1[i] + a52 * k2[i] + a53 * k3[i] + a54 * k4[i]);
+        orc_rhs_rr(s, ga, gb, t, k5);
+        for (i = 0; i < 14; i++)
+            t[i] = y[i] + h * (a61 * k1[i] + a62 * k2[i] + a63 * k3[i] + a64 * k4[i] + a65 * k5[i]);
+        orc_rhs_rr(s, ga, gb, t, k6);
+        for (i = 0; i < 14; i++)
+            y[i] = y[i] + h * (b1 * k1[i] + b3 * k3[i] + b4 * k4[i] + b5 * k5[i] + b6 * k6[i]);
+    } else {
+        double k1[14], k2[14], k3[14], k4[14], tmp[14];
+        orc_rhs_rr(s, ga, gb, y, k1);
+        for (i = 0; i < 14; i++) tmp[i] = y[i] + 0.5 * h * k1[i];
+        orc_rhs_rr(s, ga, gb, tmp, k2);
+        for (i = 0; i < 14; i++) tmp[i] = y[i] + 0.5 * h * k2[i];
+        orc_rhs_rr(s, ga, gb, tmp, k3);
+        for (i = 0; i < 14; i++) tmp[i] = y[i] + h * k3[i];
+        orc_rhs_rr(s, ga, gb, tmp, k4);
+        for (i = 0; i < 14; i++) y[i] = y[i] + h * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]) / 6.0;
+    }
+}
+
 /* --------------------------------------------------------------- integrals */
 void orc_integrals(const orc_sys *s, const double y[12], double out[7])
 {
@@ -539,6 +635,27 @@ static double distance12(const double a[12], const double b[12])
     return sqrt(d2);
 }
 
+/* One integration step of a trajectory.  Without radiation reaction the
+ * reference integrals stay fixed; with it, ref[0] = E and ref[1] = |J|
+ * advance with the state by their integral-invariant relations. */
+static void step(const orc_config *cfg, const orc_sys *s, double y[12], double ref[4], double h)
+{
+    if (cfg->rr) {
+        double y14[14];
+        memcpy(y14, y, 12 * sizeof(double));
+        y14[12] = ref[0];
+        y14[13] = ref[1];
+        orc_rk_step_rr(s, cfg->rr_gauge_a, cfg->rr_gauge_b, cfg->rk_order, y14, h);
+        memcpy(y, y14, 12 * sizeof(double));
+        ref[0] = y14[12];
+        ref[1] = y14[13];
+    } else if (cfg->rk_order == 5) {
+        orc_rk5_step(s, y, h);
+    } else {
+        orc_rk4_step(s, y, h);
+    }
+}
+
 static void integrate_one(const orc_config *cfg, const orc_sys *s, const double y0[12],
                           double h, int64_t nsteps, double y[12], double ys[12],
                           double integ[6], double *fli_out, int32_t *status_out,
@@ -558,16 +675,14 @@ static void integrate_one(const orc_config *cfg, const orc_sys *s, const double 
 
     for (k = 1; k <= nsteps; k++) {
         int it = 0;
-        if (cfg->rk_order == 5) orc_rk5_step(s, y, h);
-        else orc_rk4_step(s, y, h);
+        step(cfg, s, y, ref, h);
         if (cfg->correct) {
             last_kind = orc_correct_rule(s, y, ref, cfg->newton_tol, cfg->newton_max, cfg->det_min,
                                          cfg->newton_apply_small, cfg->correct, &it, 0);
             if (last_kind != ORC_CORR_OK) skips++;
             iters += it;
         }
-        if (cfg->rk_order == 5) orc_rk5_step(s, ys, h);
-        else orc_rk4_step(s, ys, h);
+        step(cfg, s, ys, refs, h);
         if (cfg->correct) {
             if (orc_correct_rule(s, ys, refs, cfg->newton_tol, cfg->newton_max, cfg->det_min,
                                  cfg->newton_apply_small, cfg->correct, &it, 0))
@@ -649,8 +764,7 @@ int orc_trace(const double y0[12], double beta, double kappa1, double kappa2,
     reference_integrals(&s, y, ref);
     for (k = 1; k <= nsteps; k++) {
         int it;
-        if (cfg->rk_order == 5) orc_rk5_step(&s, y, h);
-        else orc_rk4_step(&s, y, h);
+        step(cfg, &s, y, ref, h);
         if (cfg->correct)
             orc_correct_rule(&s, y, ref, cfg->newton_tol, cfg->newton_max, cfg->det_min,
                              cfg->newton_apply_small, cfg->correct, &it, 0);

@@ -49,6 +49,9 @@ typedef struct {
     int rk_order;         /* 4: classical RK4; 5: Dormand-Prince fifth-order weights */
     int newton_apply_small; /* 1: apply a Newton step, then stop if it was within newton_tol;
                                0: stop before applying a step already within newton_tol */
+    int rr;               /* 1: add the 2.5PN radiation reaction a_2.5PN to dp/dt (Eq. 6) and
+                             correct toward integral-invariant reference values (Sec. 3B) */
+    double rr_gauge_a, rr_gauge_b; /* gauge constants of orc_rr_accel (harmonic gauge: 4, 5) */
 } orc_config;
 
 /* Per-orbit final status (oracle's own numbering). */
@@ -85,6 +88,22 @@ void orc_rk4_step(const orc_sys *s, double y[12], double h);
 /* One fifth-order Runge-Kutta step (Dormand-Prince 1980 tableau, fifth-order
  * weights, fixed step), in place. */
 void orc_rk5_step(const orc_sys *s, double y[12], double h);
+
+/* Leading-order (2.5PN) radiation-reaction acceleration a_2.5PN of Eq. 6
+ * for the state y (velocity v = p at this order), in the two-parameter gauge
+ * family of Iyer & Will (1993) with constants (ga, gb); (4, 5) is the
+ * harmonic-gauge force of Damour & Deruelle.  The paper takes the force from
+ * Levin et al. (2011) without printing it. */
+void orc_rr_accel(const orc_sys *s, double ga, double gb, const double y[12], double a[3]);
+
+/* Equations of motion with radiation reaction on the extended state
+ * y14 = (r, p, S1, S2, E, |J|): Eqs. 6-7 with a_2.5PN, and the integral-
+ * invariant relations dE/dt = (dH/dp).a, d|J|/dt = J.(r x a)/|J| that carry
+ * the reference values of the dissipative system (Sec. 3B). */
+void orc_rhs_rr(const orc_sys *s, double ga, double gb, const double y[14], double dy[14]);
+
+/* One RK4 (rk_order 4) or fifth-order (5) step of orc_rhs_rr, in place. */
+void orc_rk_step_rr(const orc_sys *s, double ga, double gb, int rk_order, double y[14], double h);
 
 /* Integrals: out = (E, |J|, |S1|, |S2|, Jx, Jy, Jz). */
 void orc_integrals(const orc_sys *s, const double y[12], double out[7]);
@@ -127,7 +146,8 @@ void orc_setup_cell(const double cell[9], double y[12]);
 /* Integrate n independent orbits for nsteps steps of size h with manifold
  * correction and FLI (two trajectories).  Arrays are AoS: y0/y_out/ys_out
  * n*12; kappa1/kappa2 nullable (1.0); outputs:
- *   integrals n*6 = (E0, E, J0, |J|, |S1|, |S2|) of the main trajectory,
+ *   integrals n*6 = (E0, E, J0, |J|, |S1|, |S2|) of the main trajectory
+ *   (with cfg->rr, E0 and J0 are the reference values at the final time),
  *   fli n, status n, t_stop n, newton_iters n (sum over both trajectories),
  *   n_skip n (steps whose dual scaling was replaced by velocity scaling or
  *   skipped), last_kind n (ORC_CORR_* of the main trajectory's last step).
