@@ -55,6 +55,7 @@ class ScanParams(_ct.Structure):
         ("sync_timeout_s", _ct.c_double),
         ("queue_wait_limit_ms", _ct.c_int), ("debug_stall_group", _ct.c_int),
         ("alloc_fn", _ALLOC_FN), ("free_fn", _FREE_FN), ("alloc_ctx", _ct.c_void_p),
+        ("radiation_reaction", _ct.c_int), ("rr_gauge_a", _ct.c_double), ("rr_gauge_b", _ct.c_double),
     ]
 
 

@@ -323,6 +323,9 @@ int scan_params_default(scan_params* p)
     p->use_graph = 1;
     p->queue_wait_limit_ms = 0;
     p->debug_stall_group = -1;
+    p->radiation_reaction = 0;
+    p->rr_gauge_a = 4.0;
+    p->rr_gauge_b = 5.0;
     return PNSCAN_OK;
 }
 
@@ -343,6 +346,11 @@ int scan_create(const scan_params* p, scan_handle** out)
     if (p->schedule < 0 || p->schedule > 4) return PNSCAN_ERR_ARG;
     if (p->correct < 0 || p->correct > 3) return PNSCAN_ERR_ARG;
     if ((p->alloc_fn == nullptr) != (p->free_fn == nullptr)) return PNSCAN_ERR_ARG;
+    if (p->radiation_reaction != 0 && p->radiation_reaction != 1) return PNSCAN_ERR_ARG;
+    if (p->radiation_reaction &&
+        ((p->schedule != PNSCAN_SCHED_AUTO && p->schedule != PNSCAN_SCHED_STATIC) ||
+         !std::isfinite(p->rr_gauge_a) || !std::isfinite(p->rr_gauge_b)))
+        return PNSCAN_ERR_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();
@@ -432,6 +440,8 @@ int scan_create(const scan_params* p, scan_handle** out)
     b.rescape2 = p->r_escape > 0.0 ? p->r_escape * p->r_escape : 0.0;
     b.wait_limit_ns = (unsigned long long)p->queue_wait_limit_ms * 1000000ull;   // 0: set per launch
     b.stall_group = p->debug_stall_group;
+    b.rr = p->radiation_reaction;
+    b.rrc = make_rr_coef(p->rr_gauge_a, p->rr_gauge_b);
     h->sched = p->schedule == PNSCAN_SCHED_AUTO ? PNSCAN_SCHED_QUEUE : p->schedule;
     h->block = p->block_size ? p->block_size : 128;
     // AUTO with few orbits.  Chained work-queue tasks would share SM
@@ -445,6 +455,12 @@ int scan_create(const scan_params* p, scan_handle** out)
     if (p->schedule == PNSCAN_SCHED_AUTO && n <= (int64_t)32 * 8 * h->num_sms) {
         h->sched = n <= (int64_t)32 * 4 * h->num_sms ? PNSCAN_SCHED_PAIR : PNSCAN_SCHED_STATIC;
         if (!p->block_size) h->block = 32;
+    }
+    // radiation reaction: the static integrator, one-warp blocks while they
+    // all fit in one resident wave
+    if (p->radiation_reaction) {
+        h->sched = PNSCAN_SCHED_STATIC;
+        if (!p->block_size) h->block = n <= (int64_t)32 * 8 * h->num_sms ? 32 : 128;
     }
     h->chunk = p->chunk_steps ? p->chunk_steps : 500;
     h->bps = p->blocks_per_sm;
@@ -616,10 +632,15 @@ int scan_autotune(scan_handle* h, int steps, int* schedule, int* block_size, int
         struct Cand { int sched, block, chunk, bps, minb; };
         std::vector<Cand> cands;
         for (int blk_sz : {32, 64, 128}) cands.push_back({PNSCAN_SCHED_STATIC, blk_sz, 0, 0, 2});
+        // radiation reaction runs on the static integrator alone
+        const bool static_only = h->base.rr != 0;
+        if (!static_only)
         for (int blk_sz : {32, 64}) cands.push_back({PNSCAN_SCHED_PAIR, blk_sz, 0, 0, 2});
+        if (!static_only)
         for (int ch : {steps / 32, steps / 16, steps / 8})
             if (ch >= 1) cands.push_back({PNSCAN_SCHED_COMPACT, 128, ch, 0, 4});
-        if (steps / 16 >= 1) cands.push_back({PNSCAN_SCHED_COMPACT, 128, steps / 16, 0, 2});
+        if (!static_only && steps / 16 >= 1) cands.push_back({PNSCAN_SCHED_COMPACT, 128, steps / 16, 0, 2});
+        if (!static_only)
         for (int minb : {2, 3, 4})
             for (int ch : {steps / 16, steps / 8, steps / 4}) {
                 if (ch < 1) continue;
@@ -686,6 +707,8 @@ struct CheckpointHeader {
     Flags flags;
     int newton_max, newton_apply_small, newton_mode, correct, rk_order, renorm;
     double newton_tol, newton_det_min, d0, fli_cap, rmerge2, rescape2;
+    int rr;
+    RRCoef rrc;
 };
 
 static const char kCheckpointMagic[8] = {'P', 'N', 'S', 'C', 'A', 'N', '0', '1'};
@@ -712,6 +735,8 @@ static void fill_header(const scan_handle* h, CheckpointHeader& c)
     c.fli_cap = b.fli_cap;
     c.rmerge2 = b.rmerge2;
     c.rescape2 = b.rescape2;
+    c.rr = b.rr;
+    c.rrc = b.rrc;
 }
 
 size_t scan_checkpoint_size(scan_handle* h)

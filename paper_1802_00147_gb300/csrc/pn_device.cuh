@@ -1,7 +1,8 @@
 // pn_device.cuh -- FP64 device arithmetic of the manifold-corrected PN scan
 // (arXiv:1802.00147): Hamiltonian and equations of motion (Sec. 2, Eqs. 1-9),
 // fixed-step RK4 and fifth-order Runge-Kutta steps, the manifold correction
-// (Eqs. 10-13) and its ablation modes.
+// (Eqs. 10-13) and its ablation modes; the optional 2.5PN radiation
+// reaction of Eq. 6 with the integral-invariant reference values of Sec. 3B.
 //
 // Everything here runs in the registers of the thread that owns an orbit (or,
 // in the paired kernel, one of its two trajectories).  On GB300 the
@@ -440,6 +441,139 @@ __device__ __forceinline__ void rk5_step_rolled(const C& c, Vec12& y, const doub
             }
         }
         rhs<QM, C>(c, st, k);
+#pragma unroll
+        for (int i = 0; i < 12; i++) kst[(j * 12 + i) * stride] = kv[i];
+    }
+#pragma unroll 1
+    for (int m = 0; m < 6; m++) {
+        if (m == 1) continue;                        // b2 = 0
+        const double b = hab[30 + m];
+#pragma unroll
+        for (int i = 0; i < 12; i++) yv[i] = fma(b, kst[(m * 12 + i) * stride], yv[i]);
+    }
+}
+
+// ------------------------------------------------------ radiation reaction
+// Leading-order (2.5PN) radiation-reaction acceleration a_2.5PN of Eq. 6, in
+// the gauge family of Iyer & Will (1993), velocity v = p at this order:
+//   a = (8/5) eta u^3 [A (n.p) n - B p]
+//   A = 3 (1 + gb) p^2 + (23 + 6 ga - 9 gb) u / 3 - 5 gb (n.p)^2
+//   B = (2 + ga) p^2 + (2 - ga) u - 3 (1 + ga) (n.p)^2
+// ((ga, gb) = (4, 5): the harmonic-gauge force).  With rp = r.p:
+//   a = sr r + sp p,  sr = (8/5) eta u^5 A rp,  sp = -(8/5) eta u^3 B.
+// The reference values of the dissipative system follow the integral-
+// invariant relations (Sec. 3B): dE/dt = (dH/dp).a = (dr/dt).a and, since
+// r x a = sp L, d|J|/dt = J.(r x a)/|J| = sp (J.L)/|J|.
+struct RRCoef {
+    double A0, A1, A2;   // A = A0 p^2 + A1 u + A2 (n.p)^2
+    double B0, B1, B2;   // B = B0 p^2 + B1 u + B2 (n.p)^2
+};
+
+__host__ __device__ inline RRCoef make_rr_coef(double ga, double gb)
+{
+    RRCoef g;
+    g.A0 = 3.0 * (1.0 + gb);
+    g.A1 = (23.0 + 6.0 * ga - 9.0 * gb) / 3.0;
+    g.A2 = -5.0 * gb;
+    g.B0 = 2.0 + ga;
+    g.B1 = 2.0 - ga;
+    g.B2 = -3.0 * (1.0 + ga);
+    return g;
+}
+
+// Eqs. 6-7 with a_2.5PN: dy, and dE/dt, d|J|/dt of the reference values.
+// k8eta = (8/5) eta of the orbit.
+template <bool QM, class C>
+__device__ __forceinline__ void rhs_rr(const C& c, const RRCoef& g, double k8eta, const Vec12& y, double u,
+                                       Vec12& dy, double& dE, double& dJ)
+{
+    rhs_u<QM, C>(c, y, u, dy);
+    const double rp = dot3(y.r, y.p);
+    const double p2 = dot3(y.p, y.p);
+    const double u2 = u * u;
+    const double np2 = rp * rp * u2;
+    const double A = fma(g.A0, p2, fma(g.A1, u, g.A2 * np2));
+    const double B = fma(g.B0, p2, fma(g.B1, u, g.B2 * np2));
+    const double ku3 = k8eta * u2 * u;
+    const double sr = ku3 * u2 * A * rp;
+    const double sp = -ku3 * B;
+    double a[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        a[i] = fma(sr, y.r[i], sp * y.p[i]);
+        dy.p[i] += a[i];
+    }
+    dE = dot3(dy.r, a);
+    const double L0 = fma(y.r[1], y.p[2], -y.r[2] * y.p[1]);
+    const double L1 = fma(y.r[2], y.p[0], -y.r[0] * y.p[2]);
+    const double L2 = fma(y.r[0], y.p[1], -y.r[1] * y.p[0]);
+    const double J0 = L0 + y.s1[0] + y.s2[0];
+    const double J1 = L1 + y.s1[1] + y.s2[1];
+    const double J2 = L2 + y.s1[2] + y.s2[2];
+    const double JL = fma(J0, L0, fma(J1, L1, J2 * L2));
+    dJ = sp * JL * rsqrt(fma(J0, J0, fma(J1, J1, J2 * J2)));
+}
+
+// RK4 step of rhs_rr (stage loop rolled, as rk4_step_rolled).  The reference
+// values ref.E, ref.J advance with the state; the equations of motion do not
+// depend on them, so they need no stage values.
+template <bool QM, class C>
+__device__ __forceinline__ void rk4_step_rr(const C& c, const RRCoef& g, double k8eta, Vec12& y, Ref& ref, double h)
+{
+    const double h2 = 0.5 * h, h3 = h * (1.0 / 3.0), h6 = h * (1.0 / 6.0);
+    Vec12 k, st = y, acc = y;
+    const double* yv = &y.r[0];
+    const double* kv = &k.r[0];
+    double* sv = &st.r[0];
+    double* av = &acc.r[0];
+    double eA = ref.E, jA = ref.J;
+    double u = rsqrt(dot3(y.r, y.r));
+#pragma unroll 1
+    for (int j = 0; j < 4; j++) {
+        double dE, dJ;
+        rhs_rr<QM>(c, g, k8eta, st, u, k, dE, dJ);
+        if (j < 3) {
+            const double a = j == 2 ? h : h2;
+#pragma unroll
+            for (int i = 0; i < 12; i++) sv[i] = fma(a, kv[i], yv[i]);
+            u = rsqrt(dot3(st.r, st.r));
+        }
+        const double w = (j == 0 || j == 3) ? h6 : h3;
+#pragma unroll
+        for (int i = 0; i < 12; i++) av[i] = fma(w, kv[i], av[i]);
+        eA = fma(w, dE, eA);
+        jA = fma(w, dJ, jA);
+    }
+    y = acc;
+    ref.E = eA;
+    ref.J = jA;
+}
+
+// Fifth-order step of rhs_rr (as rk5_step_rolled); the reference values take
+// the fifth-order weights stage by stage.
+template <bool QM, class C>
+__device__ __forceinline__ void rk5_step_rr(const C& c, const RRCoef& g, double k8eta, Vec12& y, Ref& ref,
+                                            const double* hab, double* kst, int stride)
+{
+    double* yv = &y.r[0];
+    Vec12 st = y, k;
+    double* sv = &st.r[0];
+    const double* kv = &k.r[0];
+#pragma unroll 1
+    for (int j = 0; j < 6; j++) {
+        if (j > 0) {
+            st = y;
+#pragma unroll 1
+            for (int m = 0; m < j; m++) {
+                const double a = hab[5 * j + m];
+#pragma unroll
+                for (int i = 0; i < 12; i++) sv[i] = fma(a, kst[(m * 12 + i) * stride], sv[i]);
+            }
+        }
+        double dE, dJ;
+        rhs_rr<QM, C>(c, g, k8eta, st, rsqrt(dot3(st.r, st.r)), k, dE, dJ);
+        ref.E = fma(hab[30 + j], dE, ref.E);
+        ref.J = fma(hab[30 + j], dJ, ref.J);
 #pragma unroll
         for (int i = 0; i < 12; i++) kst[(j * 12 + i) * stride] = kv[i];
     }

@@ -113,6 +113,10 @@ __device__ __forceinline__ Coef load_coef(const DevState& S, int64_t i, const Fl
 // correction instead of eight (RK4) or twelve (RK5) and two; the trajectories
 // are swapped in registers between the passes.  Same operations in the same
 // order.  hab: the step-scaled RK5 tableau (RK5 only).
+//
+// RR: the steps include the 2.5PN radiation reaction and advance the
+// reference E and |J| of each trajectory with it (rolled form only); k8eta =
+// (8/5) eta of the orbit.
 template <class T>
 __device__ __forceinline__ void swap_regs(T& a, T& b)
 {
@@ -121,10 +125,11 @@ __device__ __forceinline__ void swap_regs(T& a, T& b)
     b = t;
 }
 
-template <bool QM, int RK, class C, bool ROLLED = false>
+template <bool QM, int RK, class C, bool ROLLED = false, bool RR = false>
 __device__ __forceinline__ void advance(const RunCfg& rc, const C& c, Orbit& o, int32_t step_end,
-                                        const double* hab = nullptr)
+                                        const double* hab = nullptr, double k8eta = 0.0)
 {
+    static_assert(!RR || ROLLED, "radiation reaction runs in the rolled form");
     extern __shared__ double kst_dyn[];      // RK5 stage derivatives (rk_order 5 only)
     double* kst = kst_dyn + threadIdx.x;
     const int kstride = (int)blockDim.x;
@@ -134,8 +139,14 @@ __device__ __forceinline__ void advance(const RunCfg& rc, const C& c, Orbit& o, 
         if (ROLLED) {
 #pragma unroll 1
             for (int tr = 0; tr < 2; tr++) {
-                if (RK == 5) rk5_step_rolled<QM, C>(c, o.y, hab, kst, kstride);
-                else rk4_step_rolled<QM, C>(c, o.y, rc.h);
+                if (RR) {
+                    if (RK == 5) rk5_step_rr<QM, C>(c, rc.rrc, k8eta, o.y, o.ref, hab, kst, kstride);
+                    else rk4_step_rr<QM, C>(c, rc.rrc, k8eta, o.y, o.ref, rc.h);
+                } else if (RK == 5) {
+                    rk5_step_rolled<QM, C>(c, o.y, hab, kst, kstride);
+                } else {
+                    rk4_step_rolled<QM, C>(c, o.y, rc.h);
+                }
                 if (rc.correct) {
                     int kind;
                     o.iters += correct<QM, C>(c, o.y, o.ref, rc.newton, &kind);
@@ -255,8 +266,9 @@ __global__ void k_init(DevState S, RunCfg rc)
 // ----------------------------------------------------- static integrator
 // One orbit per thread for the whole run; stage and trajectory loops rolled
 // (one compiled copy of the equations of motion, as in the queue kernel's
-// default variant).
-template <bool QM, int RK>
+// default variant).  RR: with the 2.5PN radiation reaction; the main
+// trajectory's reference E and |J| then change and are stored back.
+template <bool QM, int RK, bool RR = false>
 __global__ void __launch_bounds__(128) k_integrate_static(DevState S, RunCfg rc)
 {
     __shared__ double hab[RK == 5 ? 36 : 1];
@@ -273,9 +285,18 @@ __global__ void __launch_bounds__(128) k_integrate_static(DevState S, RunCfg rc)
     o.status = ORBIT_RUNNING;
     const Coef c = load_coef<false>(S, i, rc.flags);
     const int32_t end = rc.nstep_base + rc.nsteps;
-    advance<QM, RK, Coef, true>(rc, c, o, end, hab);
+    double k8eta = 0.0;
+    if (RR) {
+        const double beta = S.beta[i];
+        k8eta = 1.6 * (beta / ((1.0 + beta) * (1.0 + beta)));
+    }
+    advance<QM, RK, Coef, true, RR>(rc, c, o, end, hab, k8eta);
     if (o.status == ORBIT_RUNNING && o.nstep == rc.final_step) o.status = ORBIT_DONE;
     store_orbit(S, i, o);
+    if (RR) {
+        S.ref[0 * S.ld + i] = o.ref.E;
+        S.ref[1 * S.ld + i] = o.ref.J;
+    }
 }
 
 // ------------------------------------------------ paired static integrator
@@ -683,16 +704,16 @@ cudaError_t launch_init(DevState S, RunCfg rc, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <int RK>
+template <int RK, bool RR>
 static void launch_static(DevState S, RunCfg rc, int block, cudaStream_t st)
 {
     const size_t sm = RK == 5 ? rk5_smem_bytes(block) : 0;
     if (sm > 48 * 1024) {
-        cudaFuncSetAttribute(k_integrate_static<true, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_integrate_static<false, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_integrate_static<true, RK, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_integrate_static<false, RK, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     }
-    if (rc.flags.use_qm) k_integrate_static<true, RK><<<grid_for(S.n, block), block, sm, st>>>(S, rc);
-    else k_integrate_static<false, RK><<<grid_for(S.n, block), block, sm, st>>>(S, rc);
+    if (rc.flags.use_qm) k_integrate_static<true, RK, RR><<<grid_for(S.n, block), block, sm, st>>>(S, rc);
+    else k_integrate_static<false, RK, RR><<<grid_for(S.n, block), block, sm, st>>>(S, rc);
 }
 
 template <int RK>
@@ -710,6 +731,7 @@ static void launch_pair(DevState S, RunCfg rc, int block, cudaStream_t st)
 
 cudaError_t launch_integrate_pair(DevState S, RunCfg rc, int block, cudaStream_t st)
 {
+    if (rc.rr) return cudaErrorInvalidValue;
     if (S.n == 0 || rc.nsteps <= 0) return cudaSuccess;
     if (block <= 0 || block > 128 || block % 32) return cudaErrorInvalidValue;
     if (rc.rk_order == 5) launch_pair<5>(S, rc, block, st);
@@ -721,8 +743,13 @@ cudaError_t launch_integrate_static(DevState S, RunCfg rc, int block, cudaStream
 {
     if (S.n == 0 || rc.nsteps <= 0) return cudaSuccess;
     if (block <= 0 || block > 128 || block % 32) return cudaErrorInvalidValue;
-    if (rc.rk_order == 5) launch_static<5>(S, rc, block, st);
-    else launch_static<4>(S, rc, block, st);
+    if (rc.rr) {
+        if (rc.rk_order == 5) launch_static<5, true>(S, rc, block, st);
+        else launch_static<4, true>(S, rc, block, st);
+    } else {
+        if (rc.rk_order == 5) launch_static<5, false>(S, rc, block, st);
+        else launch_static<4, false>(S, rc, block, st);
+    }
     return cudaGetLastError();
 }
 
@@ -769,6 +796,7 @@ static void launch_queue(DevState S, RunCfg rc, QueueState q, int block, int gri
 cudaError_t launch_integrate_queue(DevState S, RunCfg rc, QueueState q, int block, int grid,
                                    int chunk, int minb, int use_order, cudaStream_t st)
 {
+    if (rc.rr) return cudaErrorInvalidValue;
     if (S.n == 0 || rc.nsteps <= 0) return cudaSuccess;
     if (block <= 0 || block > 128 || block % 32 || grid <= 0 || chunk <= 0) return cudaErrorInvalidValue;
     if (rc.rk_order == 5 && minb == 4) launch_queue<2, false, 5, true>(S, rc, q, block, grid, chunk, use_order, st);

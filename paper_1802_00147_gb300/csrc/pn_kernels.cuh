@@ -25,7 +25,8 @@ struct DevState {
     int64_t ld;            // plane stride (n rounded up to a multiple of 32)
     double* y;             // [12][n] main trajectory (r, p, S1, S2)
     double* ys;            // [12][n] shadow trajectory
-    double* ref;           // [8][n]  E0, J0, |S1|0, |S2|0 of main, then of shadow
+    double* ref;           // [8][n]  E0, J0, |S1|0, |S2|0 of main, then of shadow (with
+                           //         radiation reaction E and J are the values at t)
     double* fli_acc;       // [n]     sum of log10(d_k / d0) over renormalisations
     double* t;             // [n]     time reached
     int32_t* nstep;        // [n]     steps taken since the initial state
@@ -46,6 +47,8 @@ struct RunCfg {
     NewtonCfg newton;
     int correct;           // apply the manifold correction each step
     int rk_order;          // 4: classical RK4; 5: Dormand-Prince fifth order
+    int rr;                // 2.5PN radiation reaction (static integrator only)
+    RRCoef rrc;            // its gauge constants
     double h;              // step size
     double d0;             // FLI separation
     int renorm;            // renormalise every `renorm` steps (<= 0: never)
@@ -94,6 +97,7 @@ cudaError_t launch_setup_cells(const double* cells_aos, int64_t n, DevState S, i
                                cudaStream_t st);
 cudaError_t launch_load_states(const double* states_aos, int64_t n, DevState S, cudaStream_t st);
 cudaError_t launch_init(DevState S, RunCfg rc, cudaStream_t st);
+// One orbit per thread; the only integrator with radiation reaction (rc.rr).
 cudaError_t launch_integrate_static(DevState S, RunCfg rc, int block, cudaStream_t st);
 // Two lanes per orbit (main / shadow trajectory), one pass over the batch.
 cudaError_t launch_integrate_pair(DevState S, RunCfg rc, int block, cudaStream_t st);

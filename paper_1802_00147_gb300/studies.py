@@ -38,6 +38,17 @@ FLI against time (Sec. 3B, Fig. 3): case II orbits 1 (regular: power-law
 growth) and 2 (chaotic: exponential growth), corrected RK5 to t = 1e5:
 
     python -m paper_1802_00147_gb300.studies fli [--t-end 1e5] [--out DIR]
+
+Non-conservative orbit 3 (Sec. 3B, Fig. 5) with the 2.5PN radiation
+reaction: |r|, the energy and its integral-invariant reference, sampled until
+the merger cut, corrected and uncorrected RK5:
+
+    python -m paper_1802_00147_gb300.studies orbit3 [--t-end 3e5] [--out DIR]
+
+Fig. 10's non-conservative waveforms (radiation reaction on, until the
+merger cut) for orbit 4 and case II orbit 2:
+
+    python -m paper_1802_00147_gb300.studies waveform --dissipative [--out DIR]
 """
 import argparse
 import json
@@ -171,10 +182,11 @@ def correction_ablation_study(n=64, t_end=1.0e4, h=1.0, rk_order=4, seed=1):
     return report
 
 
-def waveform_series(cells, t_end, every=10.0, h=1.0, R=1.0, P=(1.0, 0.0, 0.0), Q=(0.0, 1.0, 0.0), **opts):
+def waveform_series(cells, t_end, every=10.0, h=1.0, R=1.0, P=(1.0, 0.0, 0.0), Q=(0.0, 1.0, 0.0),
+                    until_stopped=False, **opts):
     """Sample (h_plus, h_cross) of the orbits of `cells` (n x >= 9) every
-    `every` time units from t = 0 to t_end: returns t (m), hp (m x n),
-    hc (m x n)."""
+    `every` time units from t = 0 to t_end (or, with until_stopped, until
+    every orbit has stopped): returns t (m), hp (m x n), hc (m x n)."""
     cells = np.ascontiguousarray(np.atleast_2d(cells), dtype=np.float64)
     kap = cells.shape[1] > W.KAP2
     ts, hps, hcs = [], [], []
@@ -189,26 +201,93 @@ def waveform_series(cells, t_end, every=10.0, h=1.0, R=1.0, P=(1.0, 0.0, 0.0), Q
             hcs.append(np.array(hc))
             if t >= t_end - 1e-9 * every:
                 break
+            if until_stopped and t > 0.0 and np.all(s.read()["status"] != ORBIT_DONE):
+                break
             t = min(t + every, t_end)
             s.run(t, h)
     return np.array(ts), np.array(hps), np.array(hcs)
 
 
-def paper_waveforms(t_end=1.0e4, every=2.0, out_dir=None):
-    """Fig. 10, conservative case: orbit 4 (regular) and case II orbit 2
-    (chaotic), corrected RK5, h = 1, P = x, Q = y, N = z, R = 1."""
+def paper_waveforms(t_end=1.0e4, every=2.0, out_dir=None, dissipative=False):
+    """Fig. 10: orbit 4 (regular) and case II orbit 2 (chaotic), corrected
+    RK5, h = 1, P = x, Q = y, N = z, R = 1.  Conservative (upper panels), or
+    with the 2.5PN radiation reaction until the merger cut r < 6 (lower
+    panels; samples after an orbit stopped repeat its last state)."""
     import os
     names, cells = W.paper_orbit_cells()
     names, cells = names[:2], cells[:2]
-    t, hp, hc = waveform_series(cells, t_end, every, rk_order=5, r_merge=0.0, r_escape=0.0)
-    report = {"t_end": t_end, "every": every, "R": 1.0}
+    if dissipative:
+        opts = dict(rk_order=5, radiation_reaction=1, r_escape=0.0, until_stopped=True)
+        every = min(every, 1.0)
+    else:
+        opts = dict(rk_order=5, r_merge=0.0, r_escape=0.0)
+    t, hp, hc = waveform_series(cells, t_end, every, **opts)
+    report = {"t_end": t_end, "every": every, "R": 1.0, "dissipative": bool(dissipative)}
+    tag = "_dissipative" if dissipative else ""
     for j, k in enumerate(names):
-        report[k] = {"h_plus_rms": float(np.sqrt(np.mean(hp[:, j] ** 2))),
-                     "h_plus_max": float(np.abs(hp[:, j]).max()),
-                     "h_cross_rms": float(np.sqrt(np.mean(hc[:, j] ** 2)))}
+        # the stretch before the orbit stopped (constant samples after it)
+        moving = np.flatnonzero(np.diff(hp[:, j]) != 0.0)
+        last = int(moving[-1]) + 2 if moving.size else 1
+        report[k] = {"h_plus_rms": float(np.sqrt(np.mean(hp[:last, j] ** 2))),
+                     "h_plus_max": float(np.abs(hp[:last, j]).max()),
+                     "h_cross_rms": float(np.sqrt(np.mean(hc[:last, j] ** 2))),
+                     "duration": float(t[last - 1])}
         if out_dir:
             os.makedirs(out_dir, exist_ok=True)
-            np.save(os.path.join(out_dir, k + "_waveform.npy"), np.stack([t, hp[:, j], hc[:, j]], axis=1))
+            np.save(os.path.join(out_dir, k + tag + "_waveform.npy"),
+                    np.stack([t[:last], hp[:last, j], hc[:last, j]], axis=1))
+    return report
+
+
+def dissipative_series(cells, t_end, every=1000.0, h=1.0, **opts):
+    """Orbits of `cells` with the 2.5PN radiation reaction (Eq. 6; Sec. 3B),
+    sampled every `every` time units by runs to t1, t2, ... until t_end or
+    until every orbit has stopped.  Returns a dict of arrays (m x n): t, r
+    (|r| of the main trajectory), E, E_ref, J, J_ref (the integrals and their
+    integral-invariant references), status."""
+    cells = np.ascontiguousarray(np.atleast_2d(cells), dtype=np.float64)
+    kap = cells.shape[1] > W.KAP2
+    rec = {k: [] for k in ("t", "r", "E", "E_ref", "J", "J_ref", "status")}
+    with Scan(cells[:, W.BETA], kappa1=cells[:, W.KAP1] if kap else None,
+              kappa2=cells[:, W.KAP2] if kap else None, radiation_reaction=1, **opts) as s:
+        s.setup(cells[:, :9])
+        t = 0.0
+        while t < t_end - 1e-9 * every:
+            t = min(t + every, t_end)
+            s.run(t, h)
+            out = s.read()
+            rec["t"].append(np.array(out["t_stop"]))
+            rec["r"].append(np.linalg.norm(out["states"][:, 0:3], axis=1))
+            rec["E_ref"].append(np.array(out["integrals"][:, 0]))
+            rec["E"].append(np.array(out["integrals"][:, 1]))
+            rec["J_ref"].append(np.array(out["integrals"][:, 2]))
+            rec["J"].append(np.array(out["integrals"][:, 3]))
+            rec["status"].append(np.array(out["status"]))
+            if np.all(out["status"] != ORBIT_DONE):
+                break
+    return {k: np.array(v) for k, v in rec.items()}
+
+
+def paper_orbit3(t_end=3.0e5, every=1000.0, h=1.0, out_dir=None):
+    """Fig. 5: orbit 3 with radiation reaction, corrected and uncorrected
+    RK5 (h = 1): the relative energy error against the integral-invariant
+    reference (a), |r| decaying to the merger cut (b)."""
+    import os
+    names, cells = W.paper_orbit_cells()
+    cell = cells[[names.index("orbit_3")]]
+    report = {"t_end": t_end, "every": every, "h": h}
+    for label, corr in (("corrected", 1), ("uncorrected", 0)):
+        d = dissipative_series(cell, t_end, every, h, rk_order=5, correct=corr, r_escape=0.0)
+        err = np.abs(d["E"][:, 0] - d["E_ref"][:, 0]) / np.abs(d["E_ref"][:, 0])
+        report[label] = {"t_stop": float(d["t"][-1, 0]), "status": int(d["status"][-1, 0]),
+                         "r_first": float(d["r"][0, 0]), "r_last": float(d["r"][-1, 0]),
+                         "dE_rel_max": float(err.max()),
+                         "dE_rel_at": {"%g" % d["t"][i, 0]: float(err[i])
+                                       for i in sorted({len(err) // 10, len(err) // 2, len(err) - 1})}}
+        if out_dir:
+            os.makedirs(out_dir, exist_ok=True)
+            np.save(os.path.join(out_dir, "orbit_3_%s.npy" % label),
+                    np.stack([d["t"][:, 0], d["r"][:, 0], d["E"][:, 0], d["E_ref"][:, 0]], axis=1))
     return report
 
 
@@ -248,7 +327,8 @@ def paper_fli_curves(t_end=1.0e5, every=500.0, out_dir=None, thr=5.8):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("study", choices=["qm", "paper", "newton", "ablation", "waveform", "fli"])
+    ap.add_argument("study", choices=["qm", "paper", "newton", "ablation", "waveform", "fli", "orbit3"])
+    ap.add_argument("--dissipative", action="store_true")
     ap.add_argument("--out", default=None)
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--subset", type=int, default=0)
@@ -262,7 +342,9 @@ def main():
     elif a.study == "ablation":
         print(json.dumps(correction_ablation_study(a.n, a.t_end)), flush=True)
     elif a.study == "waveform":
-        print(json.dumps(paper_waveforms(a.t_end, out_dir=a.out)), flush=True)
+        print(json.dumps(paper_waveforms(a.t_end, out_dir=a.out, dissipative=a.dissipative)), flush=True)
+    elif a.study == "orbit3":
+        print(json.dumps(paper_orbit3(a.t_end, out_dir=a.out)), flush=True)
     elif a.study == "fli":
         print(json.dumps(paper_fli_curves(a.t_end, out_dir=a.out)), flush=True)
     else:

@@ -173,20 +173,24 @@ def paper_orbit_cells():
     - case II orbit 2 (Sec. 3B): (1, 10.14, 0.365), S1 = (0.13036, 0.262852,
       -0.955989), S2 = (0.118966, -0.13459, -0.983734), chi = 1;
     - case II orbit 1 (Sec. 3B): (1/3, 20, 0.2461), S1 = (sin 60, 0, cos 60),
-      S2 = (sin 45, 0, cos 45), chi = 0.75.
+      S2 = (sin 45, 0, cos 45), chi = 0.75;
+    - orbit 3 (Sec. 3B, with radiation reaction): (1, 50, 0.140),
+      S1 = (sin 45, 0, cos 45), S2 = (sin 30, 0, cos 30), chi = (1, 0.85).
     Returns (names, cells)."""
-    names = ("orbit_4", "case_II_orbit_2", "case_II_orbit_1")
-    c = np.zeros((3, NFIELDS))
-    rows = ((10.0, 0.274, 1.0, (np.sin(1.0), 0, np.cos(1.0)), (np.sin(1.325), 0, np.cos(1.325)), 1.0),
-            (10.14, 0.365, 1.0, (0.13036, 0.262852, -0.955989), (0.118966, -0.13459, -0.983734), 1.0),
-            (20.0, 0.2461, 1.0 / 3.0, (np.sin(np.pi / 3), 0, 0.5), (np.sqrt(0.5), 0, np.sqrt(0.5)), 0.75))
-    for k, (x0, py, beta, s1, s2, chi) in enumerate(rows):
+    names = ("orbit_4", "case_II_orbit_2", "case_II_orbit_1", "orbit_3")
+    c = np.zeros((len(names), NFIELDS))
+    rows = ((10.0, 0.274, 1.0, (np.sin(1.0), 0, np.cos(1.0)), (np.sin(1.325), 0, np.cos(1.325)), 1.0, 1.0),
+            (10.14, 0.365, 1.0, (0.13036, 0.262852, -0.955989), (0.118966, -0.13459, -0.983734), 1.0, 1.0),
+            (20.0, 0.2461, 1.0 / 3.0, (np.sin(np.pi / 3), 0, 0.5), (np.sqrt(0.5), 0, np.sqrt(0.5)), 0.75, 0.75),
+            (50.0, 0.140, 1.0, (np.sqrt(0.5), 0, np.sqrt(0.5)), (0.5, 0, np.sqrt(0.75)), 1.0, 0.85))
+    for k, (x0, py, beta, s1, s2, chi1, chi2) in enumerate(rows):
         c[k, X0] = x0
         c[k, PFAC] = py * np.sqrt(x0)
         c[k, TH1], c[k, PH1] = _polar(s1)
         c[k, TH2], c[k, PH2] = _polar(s2)
         c[k, BETA] = beta
-        c[k, CHI1] = c[k, CHI2] = chi
+        c[k, CHI1] = chi1
+        c[k, CHI2] = chi2
         c[k, KAP1] = c[k, KAP2] = 1.0
     return names, c
 

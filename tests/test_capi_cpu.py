@@ -58,6 +58,7 @@ def test_params_default_values(pn):
     assert p.newton_tol == 1e-10 and p.newton_max == 50 and p.newton_det_min == 1e-5
     assert p.fli_d0 == 1e-9 and p.fli_renorm_steps == 100 and p.fli_thresh == 6.0
     assert p.r_merge == 6.0 and p.r_escape == 1e3
+    assert (p.radiation_reaction, p.rr_gauge_a, p.rr_gauge_b) == (0, 4.0, 5.0)
     assert ctypes.sizeof(pn.ScanParams) == ctypes.sizeof(p)
 
 
@@ -84,6 +85,16 @@ def test_bad_arguments_are_rejected_before_any_device_work(pn):
         p.n = 4
         setattr(p, field, bad)
         assert L.scan_create(ctypes.byref(p), ctypes.byref(h)) == pn.ERR_ARG, (field, bad)
+    # radiation reaction: a flag, finite gauge constants, the static schedule only
+    for fields in (dict(radiation_reaction=2), dict(radiation_reaction=1, schedule=2),
+                   dict(radiation_reaction=1, schedule=3), dict(radiation_reaction=1, schedule=4),
+                   dict(radiation_reaction=1, rr_gauge_a=float("nan")),
+                   dict(radiation_reaction=1, rr_gauge_b=float("inf"))):
+        p = pn.scan_params_default()
+        p.n = 4
+        for k, v in fields.items():
+            setattr(p, k, v)
+        assert L.scan_create(ctypes.byref(p), ctypes.byref(h)) == pn.ERR_ARG, fields
     assert h.value is None
     assert L.scan_run(None, None, 1.0, 1.0) == pn.ERR_ARG
     assert L.scan_read(None, None, None, None, None, None) == pn.ERR_ARG

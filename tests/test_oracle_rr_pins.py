@@ -15,6 +15,9 @@ oracle uses the leading-order two-parameter gauge family of Iyer & Will
 - the extended RK4 and fifth-order steps converge at orders 4 and 5;
 - with the correction, H and |J| equal the evolving reference values.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -167,16 +170,24 @@ def test_extended_steps_converge_at_their_order(rk_order, slope):
     assert slope - 0.4 < order < slope + 0.6, (errs, order)
 
 
+def golden_orbit(name):
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_orbits.json")) as f:
+        g = json.load(f)[name]
+    beta = g["beta"]
+    m1, m2 = beta / (1 + beta), 1 / (1 + beta)
+    y = np.r_[g["r"], g["p"], g["chi1"] * m1 * m1 * np.array(g["S1_hat"]),
+              g["chi2"] * m2 * m2 * np.array(g["S2_hat"])].astype(float)
+    return beta, y
+
+
 @pytest.mark.parametrize("rk_order", (4, 5))
 def test_correction_holds_the_evolving_reference_values(rk_order):
-    # orbit 3 of Sec. 3B (beta, r, p) = (1, 50, 0.140), S1 = (sin 45, 0, cos 45),
-    # S2 = (sin 30, 0, cos 30), chi = (1, 0.85), with radiation reaction
-    s = orc.system(1.0, pn_order=2)
-    cell = np.array([[50.0, 0.140 * np.sqrt(50.0), np.pi / 4, 0.0, np.pi / 6, 0.0, 1.0, 1.0, 0.85]])
-    y0 = orc.setup_cells(cell)[0]
+    # orbit 3 of Sec. 3B with radiation reaction
+    beta, y0 = golden_orbit("orbit_3")
+    s = orc.system(beta, pn_order=2)
     I0 = orc.integrals(s, y0)
     cfg = orc.config(rr=1, rk_order=rk_order, fli_renorm=100)
-    out = orc.scan(y0[None], 1.0, 2.0, 3000, cfg=cfg)
+    out = orc.scan(y0[None], beta, 2.0, 3000, cfg=cfg)
     assert out["status"][0] == orc.DONE
     E0, E, J0, J = out["integrals"][0, :4]
     assert E0 < I0[0] and J0 < I0[1]               # the references moved (energy radiated)
@@ -184,6 +195,27 @@ def test_correction_holds_the_evolving_reference_values(rk_order):
     assert abs(J - J0) <= 1e-13 * J0
     # without the correction the same run drifts off the references
     cfg0 = orc.config(rr=1, rk_order=rk_order, correct=0, fli_renorm=100)
-    out0 = orc.scan(y0[None], 1.0, 2.0, 3000, cfg=cfg0)
+    out0 = orc.scan(y0[None], beta, 2.0, 3000, cfg=cfg0)
     E0u, Eu = out0["integrals"][0, :2]
     assert abs(Eu - E0u) > 10 * abs(E - E0)
+
+
+def test_orbit3_spirals_in_with_its_energy_on_the_reference():
+    """Fig. 5 (soft): orbit 3 decays until the merger cut; with the correction
+    the energy stays on the integral-invariant reference at every sample
+    (no secular growth, Fig. 5a); uncorrected RK5 drifts off it."""
+    beta, y0 = golden_orbit("orbit_3")
+    errs, errs0, binding = [], [], []
+    for T in (25_000, 50_000, 100_000):
+        out = orc.scan(y0[None], beta, 2.0, T // 2, orc.config(rr=1, rk_order=5, r_escape=0))
+        out0 = orc.scan(y0[None], beta, 2.0, T // 2, orc.config(rr=1, rk_order=5, r_escape=0, correct=0))
+        E0, E = out["integrals"][0, :2]
+        errs.append(abs(E - E0) / abs(E0))
+        E0u, Eu = out0["integrals"][0, :2]
+        errs0.append(abs(Eu - E0u) / abs(E0u))
+        binding.append(abs(E0))
+    assert max(errs) <= 1e-14
+    assert errs0[-1] > 1e3 * max(errs)
+    assert binding[0] < binding[1] < binding[2]    # |E| grows: the binary hardens
+    out = orc.scan(y0[None], beta, 2.0, 200_000, orc.config(rr=1, rk_order=5, r_escape=0))
+    assert out["status"][0] == orc.MERGED and 2.0e5 < out["t_stop"][0] < 3.5e5

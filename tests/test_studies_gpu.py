@@ -92,3 +92,38 @@ def test_fli_curves_of_the_paper_case_II_orbits():
     o = oracle.scan(oracle.setup_cells(cells[pick, :9]), cells[pick, W.BETA], 1.0, 100_000,
                     oracle.config(r_merge=0, r_escape=0))
     assert (o["fli"] > 5.8).tolist() == [False, True]
+
+
+def test_orbit3_inspiral_study():
+    """Fig. 5 with the 2.5PN radiation reaction: orbit 3 spirals in to the
+    merger cut at the oracle's step (t = 268,498 at h = 2); the corrected
+    energy stays on its integral-invariant reference at every sample
+    (Fig. 5a), the uncorrected one drifts off it."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_00147_gb300 import build
+    build.build()
+    from paper_1802_00147_gb300 import studies
+    r = studies.paper_orbit3(t_end=3.0e5, every=5000.0, h=2.0)
+    c, u = r["corrected"], r["uncorrected"]
+    assert c["status"] == 2 and c["t_stop"] == 268498.0
+    assert c["r_first"] > 40.0 and c["r_last"] < 6.0
+    assert c["dE_rel_max"] <= 1e-13
+    assert u["dE_rel_max"] > 1e3 * c["dE_rel_max"]
+
+
+def test_dissipative_waveforms_are_short():
+    """Fig. 10, lower panels: with radiation reaction orbit 4 and case II
+    orbit 2 reach the merger cut within about one orbit (the oracle stops
+    them at t = 56 and 67)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_00147_gb300 import build
+    build.build()
+    from paper_1802_00147_gb300 import studies
+    r = studies.paper_waveforms(t_end=1000.0, dissipative=True)
+    assert r["orbit_4"]["duration"] == 56.0
+    assert r["case_II_orbit_2"]["duration"] == 67.0
+    assert r["orbit_4"]["h_plus_max"] > 0.0
