@@ -9,8 +9,9 @@ synthetic cells, h = 1, t_end = 2e4.
 
 The same JSON line also carries: the end-to-end rate through the C ABI with
 host buffers, the roofline of the integrator, the CPU oracle's rate on the
-host cores, the uneven 1e5-orbit batch and the surrogate-adaptive
-1024 x 1024 map against integrating every cell (rank 0).
+host cores, the uneven 1e5-orbit batch, the same scan with the 2.5PN
+radiation reaction, and the surrogate-adaptive 1024 x 1024 map against
+integrating every cell (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -47,6 +48,11 @@ H_STEP = 1.0
 FLOPS_PER_TRAJ_STEP = 4 * 217 + 171 + 138 + 43
 FLOPS_PER_NEWTON_ITER = 73
 FLOPS_PER_ORBIT_STEP_EXTRA = 5 + 1.75
+# With the 2.5PN radiation reaction each RK stage adds (rhs_rr): r.p, p.p,
+# (n.p)^2, the A and B polynomials, the two scale factors, a = sr r + sp p and
+# its addition to dp/dt, (dr/dt).a, L, J, J.L, |J|^-1 and the product (74), and
+# the two reference-value updates (4): 78 per stage.
+FLOPS_PER_RR_STAGE = 78
 # Algorithmic DRAM bytes per orbit and run: the SoA state read once (main and
 # shadow 2 x 12, reference integrals 8, FLI accumulator, t, beta, kappa1,
 # kappa2: 37 doubles; nstep, status, Newton and skip counters, last kind:
@@ -63,13 +69,13 @@ FP64_PEAK_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # these files differs from the recorded SHA-256.
 TRAFFIC_SOURCES = {
     "paper_1802_00147_gb300/csrc/pn_device.cuh": "1ba3eb6333bd1e411f267c0bc37fa71ffb149ce0d367828de1004ef0516033f3",
-    "paper_1802_00147_gb300/csrc/pn_kernels.cu": "45bae6b12ac35b639d46354b6f0b2b4e2f8eabd095bcf913bed6e7b7f721cb44",
-    "paper_1802_00147_gb300/csrc/pn_kernels.cuh": "7962d1432c8bd6d20fa134782863dabd69c74602b06873194821e338d18d5b7e",
+    "paper_1802_00147_gb300/csrc/pn_kernels.cu": "1ae1f3a5e8a08bc0f0c68ef98329ff67e4675d0dc3c0861f6c75bd0d4a0aa284",
+    "paper_1802_00147_gb300/csrc/pn_kernels.cuh": "740b9de0a7629524f7fb1a3c839e77b619c018ea71f44cd8fd6cd2529266a08a",
 }
 # ncu --cache-control none, as the bench runs: the set-up kernels leave the
 # state in L2 right before the run.
-TRAFFIC_BYTES_PER_RUN = {2: 4443136 + 36443392,      # work-queue schedule, chunk 125
-                         3: 5604352 + 15642368}      # compacting schedule, chunk 62 (7 epochs)
+TRAFFIC_BYTES_PER_RUN = {2: 4336896 + 38163712,      # work-queue schedule, chunk 125
+                         3: 5761792 + 15303936}      # compacting schedule, chunk 62 (7 epochs)
 
 
 def traffic_per_run(schedule):
@@ -345,6 +351,38 @@ def run_uneven(n=100_000, t_end=2.0e4):
             "tflops_algorithmic": algorithmic_flops(summ["orbit_steps"], summ["newton_iters"]) / (ms * 1e-3) / 1e12}
 
 
+# ------------------------------------------------------ radiation reaction
+def run_dissipative(t_end=5.0e3):
+    """The 314 x 314 scan with the 2.5PN radiation reaction (Eq. 6; the
+    reference E and |J| carried by their integral-invariant relations,
+    Sec. 3B), autotuned schedule: one timed run after a warm-up.  Close
+    binaries merge early, so the batch is uneven."""
+    import torch
+    import paper_1802_00147_gb300 as pn
+    cells = workload(0)
+    n = cells.shape[0]
+    cd = torch.as_tensor(np.ascontiguousarray(cells[:, :9]), device="cuda")
+    with pn.Scan(None, device=True, n=n, radiation_reaction=1) as s:
+        s.setup(cd)
+        shape = s.autotune(1000)
+        for _ in range(2):                      # warm-up (and graph capture), then timed
+            s.setup(cd)
+            s.run(t_end, H_STEP)
+            summ = s.summary()
+        ms, _ = s.last_run_timing()
+    flops = (summ["orbit_steps"] * (2 * (FLOPS_PER_TRAJ_STEP + 4 * FLOPS_PER_RR_STAGE) + FLOPS_PER_ORBIT_STEP_EXTRA)
+             + max(0, summ["newton_iters"] - 2 * summ["orbit_steps"]) * FLOPS_PER_NEWTON_ITER)
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"workload": "314x314 scan (as the headline) with the 2.5PN radiation reaction, harmonic gauge, "
+                        "RK4 h=1 to t_end=5e3, merger cut r<6",
+            "schedule": shape, "kernel_ms": ms,
+            "orbit_steps": summ["orbit_steps"], "value": summ["orbit_steps"] / (ms * 1e-3), "unit": UNIT,
+            "status_count": summ["status_count"],
+            "newton_iters_per_orbit_step": summ["newton_iters"] / max(1, summ["orbit_steps"]),
+            "tflops_algorithmic": achieved, "frac": achieved / FP64_PEAK_NOMINAL_TFLOPS,
+            "max_dE_vs_reference": summ["max_dE"]}
+
+
 # -------------------------------------------------------------------- ours
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -367,6 +405,8 @@ def run_ours(args, rank, world, local_rank):
 
     sched_code = {"auto": 0, "static": 1, "queue": 2, "compact": 3, "pair": 4}[args.schedule]
     prof_opts = dict(schedule=sched_code, chunk_steps=args.chunk, block_size=args.block) if args.profile else {}
+    if args.profile and args.dissipative:
+        prof_opts["radiation_reaction"] = 1
     scan = pn.Scan(cells_h[:, W.BETA], device=True, **prof_opts)
     scan.setup(cells_d)
     if args.profile:
@@ -449,6 +489,7 @@ def run_ours(args, rank, world, local_rank):
     d2h = sum(a.nbytes for a in out.values()) * world
 
     uneven = run_uneven() if (rank == 0 and args.adaptive) else None
+    dissipative = run_dissipative() if (rank == 0 and args.adaptive) else None
     adaptive = None
     if args.adaptive and rank == 0:
         fli_full = scan.read()["fli"]
@@ -489,6 +530,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk.summary(),
         "adaptive": adaptive,
         "uneven": uneven,
+        "dissipative": dissipative,
         "scan": {k: summ[k] for k in ("n_chaotic", "status_count", "max_dE", "max_dJ", "max_dJ_all",
                                       "n_final_fallback", "max_dS", "fli_mean", "newton_iters",
                                       "n_skip", "orbit_steps")},
@@ -514,6 +556,8 @@ def main():
     ap.add_argument("--chunk", type=int, default=0, help="steps per task for --profile runs (0: 500)")
     ap.add_argument("--profile", action="store_true",
                     help="time the device path only (no autotune, e2e or CPU leg) for ncu runs")
+    ap.add_argument("--dissipative", action="store_true",
+                    help="--profile runs with the 2.5PN radiation reaction")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

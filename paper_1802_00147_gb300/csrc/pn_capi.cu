@@ -173,7 +173,7 @@ int reset_queue(scan_handle* h, cudaStream_t st)
 
 int queue_grid(scan_handle* h, int block, int bps, int minb)
 {
-    int occ = queue_blocks_per_sm(block, h->base.flags.use_qm != 0, minb, h->base.rk_order);
+    int occ = queue_blocks_per_sm(block, h->base.flags.use_qm != 0, minb, h->base.rk_order, h->base.rr != 0);
     if (occ <= 0) occ = 1;
     if (bps <= 0 || bps > occ) bps = occ;
     return h->num_sms * bps;
@@ -348,8 +348,7 @@ int scan_create(const scan_params* p, scan_handle** out)
     if ((p->alloc_fn == nullptr) != (p->free_fn == nullptr)) return PNSCAN_ERR_ARG;
     if (p->radiation_reaction != 0 && p->radiation_reaction != 1) return PNSCAN_ERR_ARG;
     if (p->radiation_reaction &&
-        ((p->schedule != PNSCAN_SCHED_AUTO && p->schedule != PNSCAN_SCHED_STATIC) ||
-         !std::isfinite(p->rr_gauge_a) || !std::isfinite(p->rr_gauge_b)))
+        (p->schedule == PNSCAN_SCHED_PAIR || !std::isfinite(p->rr_gauge_a) || !std::isfinite(p->rr_gauge_b)))
         return PNSCAN_ERR_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -456,12 +455,8 @@ int scan_create(const scan_params* p, scan_handle** out)
         h->sched = n <= (int64_t)32 * 4 * h->num_sms ? PNSCAN_SCHED_PAIR : PNSCAN_SCHED_STATIC;
         if (!p->block_size) h->block = 32;
     }
-    // radiation reaction: the static integrator, one-warp blocks while they
-    // all fit in one resident wave
-    if (p->radiation_reaction) {
-        h->sched = PNSCAN_SCHED_STATIC;
-        if (!p->block_size) h->block = n <= (int64_t)32 * 8 * h->num_sms ? 32 : 128;
-    }
+    // radiation reaction has no paired kernel: the static one instead
+    if (p->radiation_reaction && h->sched == PNSCAN_SCHED_PAIR) h->sched = PNSCAN_SCHED_STATIC;
     h->chunk = p->chunk_steps ? p->chunk_steps : 500;
     h->bps = p->blocks_per_sm;
     h->minb = p->register_variant >= 2 ? p->register_variant : 4;
@@ -632,18 +627,16 @@ int scan_autotune(scan_handle* h, int steps, int* schedule, int* block_size, int
         struct Cand { int sched, block, chunk, bps, minb; };
         std::vector<Cand> cands;
         for (int blk_sz : {32, 64, 128}) cands.push_back({PNSCAN_SCHED_STATIC, blk_sz, 0, 0, 2});
-        // radiation reaction runs on the static integrator alone
-        const bool static_only = h->base.rr != 0;
-        if (!static_only)
+        // radiation reaction: no paired kernel, one (rolled) queue variant
+        const bool rr = h->base.rr != 0;
+        if (!rr)
         for (int blk_sz : {32, 64}) cands.push_back({PNSCAN_SCHED_PAIR, blk_sz, 0, 0, 2});
-        if (!static_only)
         for (int ch : {steps / 32, steps / 16, steps / 8})
             if (ch >= 1) cands.push_back({PNSCAN_SCHED_COMPACT, 128, ch, 0, 4});
-        if (!static_only && steps / 16 >= 1) cands.push_back({PNSCAN_SCHED_COMPACT, 128, steps / 16, 0, 2});
-        if (!static_only)
+        if (!rr && steps / 16 >= 1) cands.push_back({PNSCAN_SCHED_COMPACT, 128, steps / 16, 0, 2});
         for (int minb : {2, 3, 4})
             for (int ch : {steps / 16, steps / 8, steps / 4}) {
-                if (ch < 1) continue;
+                if (ch < 1 || (rr && minb != 4)) continue;
                 cands.push_back({PNSCAN_SCHED_QUEUE, 128, ch, 0, minb});
                 if (minb == 2) cands.push_back({PNSCAN_SCHED_QUEUE, 128, ch, 1, minb});
                 if (minb == 3) cands.push_back({PNSCAN_SCHED_QUEUE, 64, ch, 0, minb});

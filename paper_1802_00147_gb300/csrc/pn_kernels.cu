@@ -446,10 +446,11 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
 
 // SMEM: keep the per-orbit constants in shared memory (one plane per constant)
 // instead of registers, which is what lets MINB = 3 blocks fit without spills.
-template <bool QM, int MINB, bool SMEM, int RK, bool ROLLED = false>
+template <bool QM, int MINB, bool SMEM, int RK, bool ROLLED = false, bool RR = false>
 __global__ void __launch_bounds__(128, MINB) k_integrate_queue(DevState S, RunCfg rc, QueueState q, int chunk,
                                                                 int use_order)
 {
+    static_assert(!RR || (ROLLED && !SMEM), "radiation reaction: rolled variant with register constants");
     __shared__ double scoef[SMEM ? NCOEF * 128 : 1];
     __shared__ double hab[(RK == 5 && ROLLED) ? 36 : 1];
     if (RK == 5 && ROLLED) {
@@ -503,10 +504,19 @@ __global__ void __launch_bounds__(128, MINB) k_integrate_queue(DevState S, RunCf
                     advance<QM, RK, CoefShared, ROLLED>(rc, cs, o, end, hab);
                 } else {
                     const Coef cf = load_coef<true>(S, i, rc.flags);
-                    advance<QM, RK, Coef, ROLLED>(rc, cf, o, end, hab);
+                    double k8eta = 0.0;
+                    if (RR) {
+                        const double beta = __ldcg(S.beta + i);
+                        k8eta = 1.6 * (beta / ((1.0 + beta) * (1.0 + beta)));
+                    }
+                    advance<QM, RK, Coef, ROLLED, RR>(rc, cf, o, end, hab, k8eta);
                 }
                 if (o.status == ORBIT_RUNNING && o.nstep == end_run) o.status = ORBIT_DONE;
                 store_orbit(S, i, o);
+                if (RR) {
+                    S.ref[0 * S.ld + i] = o.ref.E;
+                    S.ref[1 * S.ld + i] = o.ref.J;
+                }
             }
         }
         __threadfence();
@@ -753,19 +763,19 @@ cudaError_t launch_integrate_static(DevState S, RunCfg rc, int block, cudaStream
     return cudaGetLastError();
 }
 
-template <int MINB, bool SMEM, int RK, bool ROLLED = false>
+template <int MINB, bool SMEM, int RK, bool ROLLED = false, bool RR = false>
 static int occupancy_queue(int block, bool qm)
 {
     const size_t sm = RK == 5 ? rk5_smem_bytes(block) : 0;
     int nb = 0;
     if (sm > 48 * 1024) {
-        cudaFuncSetAttribute(k_integrate_queue<true, MINB, SMEM, RK, ROLLED>,
+        cudaFuncSetAttribute(k_integrate_queue<true, MINB, SMEM, RK, ROLLED, RR>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_integrate_queue<false, MINB, SMEM, RK, ROLLED>,
+        cudaFuncSetAttribute(k_integrate_queue<false, MINB, SMEM, RK, ROLLED, RR>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     }
-    if (qm) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<true, MINB, SMEM, RK, ROLLED>, block, sm);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<false, MINB, SMEM, RK, ROLLED>, block, sm);
+    if (qm) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<true, MINB, SMEM, RK, ROLLED, RR>, block, sm);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_integrate_queue<false, MINB, SMEM, RK, ROLLED, RR>, block, sm);
     return nb;
 }
 
@@ -773,8 +783,10 @@ static int occupancy_queue(int block, bool qm)
 // registers, 2 blocks per SM (2); in shared memory, 3 blocks per SM (3); in
 // registers with the stage and trajectory loops rolled (4).  RK5 with the
 // constants in registers, loops unrolled (2, 3) or rolled (4).
-int queue_blocks_per_sm(int block, bool qm, int minb, int rk_order)
+int queue_blocks_per_sm(int block, bool qm, int minb, int rk_order, bool rr)
 {
+    if (rr) return rk_order == 5 ? occupancy_queue<2, false, 5, true, true>(block, qm)
+                                 : occupancy_queue<2, false, 4, true, true>(block, qm);
     if (rk_order == 5)
         return minb == 4 ? occupancy_queue<2, false, 5, true>(block, qm) : occupancy_queue<2, false, 5>(block, qm);
     if (minb == 3) return occupancy_queue<3, true, 4, true>(block, qm);
@@ -782,24 +794,26 @@ int queue_blocks_per_sm(int block, bool qm, int minb, int rk_order)
     return occupancy_queue<2, false, 4>(block, qm);
 }
 
-template <int MINB, bool SMEM, int RK, bool ROLLED = false>
+template <int MINB, bool SMEM, int RK, bool ROLLED = false, bool RR = false>
 static void launch_queue(DevState S, RunCfg rc, QueueState q, int block, int grid, int chunk, int use_order,
                          cudaStream_t st)
 {
     const size_t sm = RK == 5 ? rk5_smem_bytes(block) : 0;
     if (rc.flags.use_qm)
-        k_integrate_queue<true, MINB, SMEM, RK, ROLLED><<<grid, block, sm, st>>>(S, rc, q, chunk, use_order);
+        k_integrate_queue<true, MINB, SMEM, RK, ROLLED, RR><<<grid, block, sm, st>>>(S, rc, q, chunk, use_order);
     else
-        k_integrate_queue<false, MINB, SMEM, RK, ROLLED><<<grid, block, sm, st>>>(S, rc, q, chunk, use_order);
+        k_integrate_queue<false, MINB, SMEM, RK, ROLLED, RR><<<grid, block, sm, st>>>(S, rc, q, chunk, use_order);
 }
 
 cudaError_t launch_integrate_queue(DevState S, RunCfg rc, QueueState q, int block, int grid,
                                    int chunk, int minb, int use_order, cudaStream_t st)
 {
-    if (rc.rr) return cudaErrorInvalidValue;
     if (S.n == 0 || rc.nsteps <= 0) return cudaSuccess;
     if (block <= 0 || block > 128 || block % 32 || grid <= 0 || chunk <= 0) return cudaErrorInvalidValue;
-    if (rc.rk_order == 5 && minb == 4) launch_queue<2, false, 5, true>(S, rc, q, block, grid, chunk, use_order, st);
+    // radiation reaction: the default (rolled) variant, whatever minb
+    if (rc.rr && rc.rk_order == 5) launch_queue<2, false, 5, true, true>(S, rc, q, block, grid, chunk, use_order, st);
+    else if (rc.rr) launch_queue<2, false, 4, true, true>(S, rc, q, block, grid, chunk, use_order, st);
+    else if (rc.rk_order == 5 && minb == 4) launch_queue<2, false, 5, true>(S, rc, q, block, grid, chunk, use_order, st);
     else if (rc.rk_order == 5) launch_queue<2, false, 5>(S, rc, q, block, grid, chunk, use_order, st);
     else if (minb == 3) launch_queue<3, true, 4, true>(S, rc, q, block, grid, chunk, use_order, st);
     else if (minb == 4) launch_queue<2, false, 4, true>(S, rc, q, block, grid, chunk, use_order, st);

@@ -47,7 +47,7 @@ struct RunCfg {
     NewtonCfg newton;
     int correct;           // apply the manifold correction each step
     int rk_order;          // 4: classical RK4; 5: Dormand-Prince fifth order
-    int rr;                // 2.5PN radiation reaction (static integrator only)
+    int rr;                // 2.5PN radiation reaction (static and work-queue integrators)
     RRCoef rrc;            // its gauge constants
     double h;              // step size
     double d0;             // FLI separation
@@ -97,15 +97,17 @@ cudaError_t launch_setup_cells(const double* cells_aos, int64_t n, DevState S, i
                                cudaStream_t st);
 cudaError_t launch_load_states(const double* states_aos, int64_t n, DevState S, cudaStream_t st);
 cudaError_t launch_init(DevState S, RunCfg rc, cudaStream_t st);
-// One orbit per thread; the only integrator with radiation reaction (rc.rr).
+// One orbit per thread.
 cudaError_t launch_integrate_static(DevState S, RunCfg rc, int block, cudaStream_t st);
-// Two lanes per orbit (main / shadow trajectory), one pass over the batch.
+// Two lanes per orbit (main / shadow trajectory), one pass over the batch
+// (conservative only: refuses rc.rr).
 cudaError_t launch_integrate_pair(DevState S, RunCfg rc, int block, cudaStream_t st);
 // minb: variant of the queue kernel: 2 -- two resident 128-thread blocks per
 // SM, per-orbit constants in registers (up to 255 per thread); 3 -- three,
 // constants in shared memory (168 registers); 4 -- as 2 with the RK stage
-// and trajectory loops rolled (the default)
-int queue_blocks_per_sm(int block, bool qm, int minb, int rk_order);
+// and trajectory loops rolled (the default; with radiation reaction the
+// only variant, whatever minb)
+int queue_blocks_per_sm(int block, bool qm, int minb, int rk_order, bool rr);
 cudaError_t launch_integrate_queue(DevState S, RunCfg rc, QueueState q, int block, int grid,
                                    int chunk, int minb, int use_order, cudaStream_t st);
 // Compacting schedule: order_next <- running orbits of order (or of all
