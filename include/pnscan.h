@@ -139,9 +139,9 @@ typedef struct scan_params {
     int radiation_reaction;  /* 1: add the leading-order 2.5PN radiation reaction a_2.5PN to dp/dt
                                 (Eq. 6) and correct toward reference E and |J| carried by their
                                 integral-invariant relations dE/dt = (dH/dp).a, d|J|/dt =
-                                J.(r x a)/|J| (Sec. 3B, orbit 3).  Every schedule but PAIR
-                                (AUTO takes STATIC where it would take PAIR; the queue kernel
-                                runs its default variant whatever register_variant) (default 0) */
+                                J.(r x a)/|J| (Sec. 3B, orbit 3).  Every schedule; the queue
+                                kernel runs its default variant whatever register_variant
+                                (default 0) */
     double rr_gauge_a;       /* gauge constants of the force, Iyer & Will (1993) family:      */
     double rr_gauge_b;       /* a = (8/5) eta u^3 [A (n.p) n - B p], A = 3 (1 + b) p^2 +
                                 (23 + 6 a - 9 b) u / 3 - 5 b (n.p)^2, B = (2 + a) p^2 + (2 - a) u

@@ -347,8 +347,7 @@ int scan_create(const scan_params* p, scan_handle** out)
     if (p->correct < 0 || p->correct > 3) return PNSCAN_ERR_ARG;
     if ((p->alloc_fn == nullptr) != (p->free_fn == nullptr)) return PNSCAN_ERR_ARG;
     if (p->radiation_reaction != 0 && p->radiation_reaction != 1) return PNSCAN_ERR_ARG;
-    if (p->radiation_reaction &&
-        (p->schedule == PNSCAN_SCHED_PAIR || !std::isfinite(p->rr_gauge_a) || !std::isfinite(p->rr_gauge_b)))
+    if (p->radiation_reaction && (!std::isfinite(p->rr_gauge_a) || !std::isfinite(p->rr_gauge_b)))
         return PNSCAN_ERR_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -455,8 +454,6 @@ int scan_create(const scan_params* p, scan_handle** out)
         h->sched = n <= (int64_t)32 * 4 * h->num_sms ? PNSCAN_SCHED_PAIR : PNSCAN_SCHED_STATIC;
         if (!p->block_size) h->block = 32;
     }
-    // radiation reaction has no paired kernel: the static one instead
-    if (p->radiation_reaction && h->sched == PNSCAN_SCHED_PAIR) h->sched = PNSCAN_SCHED_STATIC;
     h->chunk = p->chunk_steps ? p->chunk_steps : 500;
     h->bps = p->blocks_per_sm;
     h->minb = p->register_variant >= 2 ? p->register_variant : 4;
@@ -627,9 +624,8 @@ int scan_autotune(scan_handle* h, int steps, int* schedule, int* block_size, int
         struct Cand { int sched, block, chunk, bps, minb; };
         std::vector<Cand> cands;
         for (int blk_sz : {32, 64, 128}) cands.push_back({PNSCAN_SCHED_STATIC, blk_sz, 0, 0, 2});
-        // radiation reaction: no paired kernel, one (rolled) queue variant
+        // radiation reaction: one (rolled) queue variant
         const bool rr = h->base.rr != 0;
-        if (!rr)
         for (int blk_sz : {32, 64}) cands.push_back({PNSCAN_SCHED_PAIR, blk_sz, 0, 0, 2});
         for (int ch : {steps / 32, steps / 16, steps / 8})
             if (ch >= 1) cands.push_back({PNSCAN_SCHED_COMPACT, 128, ch, 0, 4});

@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(128) k_integrate_static(DevState S, RunCfg rc)
 // state; the main lane the new distance).  Shuffles are masked to the pair,
 // whose lanes always take the same branches.  The operations and their order
 // per trajectory are those of advance(): results are bit-identical.
-template <bool QM, int RK>
+template <bool QM, int RK, bool RR = false>
 __global__ void __launch_bounds__(128) k_integrate_pair(DevState S, RunCfg rc)
 {
     __shared__ double hab[RK == 5 ? 36 : 1];
@@ -340,6 +340,11 @@ __global__ void __launch_bounds__(128) k_integrate_pair(DevState S, RunCfg rc)
     ref.J = S.ref[(rb + 1) * n + i];
     ref.S1 = S.ref[(rb + 2) * n + i];
     ref.S2 = S.ref[(rb + 3) * n + i];
+    double k8eta = 0.0;
+    if (RR) {
+        const double beta = S.beta[i];
+        k8eta = 1.6 * (beta / ((1.0 + beta) * (1.0 + beta)));
+    }
     double acc = S.fli_acc[i];
     const double t0 = S.t[i];
     const int32_t n0 = S.nstep[i];
@@ -348,8 +353,14 @@ __global__ void __launch_bounds__(128) k_integrate_pair(DevState S, RunCfg rc)
     const int32_t step_end = rc.nstep_base + rc.nsteps;
     double* yv = &y.r[0];
     while (nstep < step_end) {
-        if (RK == 5) rk5_step_rolled<QM, Coef>(c, y, hab, kst, kstride);
-        else rk4_step_rolled<QM, Coef>(c, y, rc.h);
+        if (RR) {
+            if (RK == 5) rk5_step_rr<QM, Coef>(c, rc.rrc, k8eta, y, ref, hab, kst, kstride);
+            else rk4_step_rr<QM, Coef>(c, rc.rrc, k8eta, y, ref, rc.h);
+        } else if (RK == 5) {
+            rk5_step_rolled<QM, Coef>(c, y, hab, kst, kstride);
+        } else {
+            rk4_step_rolled<QM, Coef>(c, y, rc.h);
+        }
         if (rc.correct) {
             int kind;
             iters += correct<QM, Coef>(c, y, ref, rc.newton, &kind);
@@ -406,6 +417,10 @@ __global__ void __launch_bounds__(128) k_integrate_pair(DevState S, RunCfg rc)
         S.ref[7 * n + i] = ref.S2;
     } else {
         store12(S.y, n, i, y);
+        if (RR) {
+            S.ref[0 * n + i] = ref.E;
+            S.ref[1 * n + i] = ref.J;
+        }
         S.fli_acc[i] = acc;
         S.t[i] = t0 + (double)(nstep - n0) * rc.h;
         S.nstep[i] = nstep;
@@ -726,26 +741,30 @@ static void launch_static(DevState S, RunCfg rc, int block, cudaStream_t st)
     else k_integrate_static<false, RK, RR><<<grid_for(S.n, block), block, sm, st>>>(S, rc);
 }
 
-template <int RK>
+template <int RK, bool RR>
 static void launch_pair(DevState S, RunCfg rc, int block, cudaStream_t st)
 {
     const size_t sm = RK == 5 ? rk5_smem_bytes(block) : 0;
     if (sm > 48 * 1024) {
-        cudaFuncSetAttribute(k_integrate_pair<true, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_integrate_pair<false, RK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_integrate_pair<true, RK, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_integrate_pair<false, RK, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     }
     const unsigned grid = grid_for(2 * S.n, block);
-    if (rc.flags.use_qm) k_integrate_pair<true, RK><<<grid, block, sm, st>>>(S, rc);
-    else k_integrate_pair<false, RK><<<grid, block, sm, st>>>(S, rc);
+    if (rc.flags.use_qm) k_integrate_pair<true, RK, RR><<<grid, block, sm, st>>>(S, rc);
+    else k_integrate_pair<false, RK, RR><<<grid, block, sm, st>>>(S, rc);
 }
 
 cudaError_t launch_integrate_pair(DevState S, RunCfg rc, int block, cudaStream_t st)
 {
-    if (rc.rr) return cudaErrorInvalidValue;
     if (S.n == 0 || rc.nsteps <= 0) return cudaSuccess;
     if (block <= 0 || block > 128 || block % 32) return cudaErrorInvalidValue;
-    if (rc.rk_order == 5) launch_pair<5>(S, rc, block, st);
-    else launch_pair<4>(S, rc, block, st);
+    if (rc.rr) {
+        if (rc.rk_order == 5) launch_pair<5, true>(S, rc, block, st);
+        else launch_pair<4, true>(S, rc, block, st);
+    } else {
+        if (rc.rk_order == 5) launch_pair<5, false>(S, rc, block, st);
+        else launch_pair<4, false>(S, rc, block, st);
+    }
     return cudaGetLastError();
 }
 

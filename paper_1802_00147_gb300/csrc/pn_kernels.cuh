@@ -47,7 +47,7 @@ struct RunCfg {
     NewtonCfg newton;
     int correct;           // apply the manifold correction each step
     int rk_order;          // 4: classical RK4; 5: Dormand-Prince fifth order
-    int rr;                // 2.5PN radiation reaction (static and work-queue integrators)
+    int rr;                // 2.5PN radiation reaction
     RRCoef rrc;            // its gauge constants
     double h;              // step size
     double d0;             // FLI separation
@@ -99,8 +99,7 @@ cudaError_t launch_load_states(const double* states_aos, int64_t n, DevState S, 
 cudaError_t launch_init(DevState S, RunCfg rc, cudaStream_t st);
 // One orbit per thread.
 cudaError_t launch_integrate_static(DevState S, RunCfg rc, int block, cudaStream_t st);
-// Two lanes per orbit (main / shadow trajectory), one pass over the batch
-// (conservative only: refuses rc.rr).
+// Two lanes per orbit (main / shadow trajectory), one pass over the batch.
 cudaError_t launch_integrate_pair(DevState S, RunCfg rc, int block, cudaStream_t st);
 // minb: variant of the queue kernel: 2 -- two resident 128-thread blocks per
 // SM, per-orbit constants in registers (up to 255 per thread); 3 -- three,

@@ -85,8 +85,8 @@ def test_bad_arguments_are_rejected_before_any_device_work(pn):
         p.n = 4
         setattr(p, field, bad)
         assert L.scan_create(ctypes.byref(p), ctypes.byref(h)) == pn.ERR_ARG, (field, bad)
-    # radiation reaction: a flag, finite gauge constants, no paired schedule
-    for fields in (dict(radiation_reaction=2), dict(radiation_reaction=1, schedule=4),
+    # radiation reaction: a flag, finite gauge constants
+    for fields in (dict(radiation_reaction=2),
                    dict(radiation_reaction=1, rr_gauge_a=float("nan")),
                    dict(radiation_reaction=1, rr_gauge_b=float("inf"))):
         p = pn.scan_params_default()

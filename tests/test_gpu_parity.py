@@ -401,7 +401,8 @@ def test_checkpoint_restore_continues_bit_identically(pn, schedule):
 # ------------------------------------------------ 2.5PN radiation reaction
 @pytest.mark.parametrize("opts", [dict(), dict(rk_order=5), dict(use_qm=1), dict(correct=0),
                                   dict(rr_gauge_a=0.0, rr_gauge_b=0.0), dict(rk_order=5, use_qm=1, block_size=64),
-                                  dict(schedule=3, chunk_steps=64), dict(rk_order=5, schedule=2, chunk_steps=100)])
+                                  dict(schedule=3, chunk_steps=64), dict(rk_order=5, schedule=2, chunk_steps=100),
+                                  dict(rk_order=5, use_qm=1, schedule=4)])
 def test_radiation_reaction_parity(pn, opts):
     """Eq. 6 with a_2.5PN and the integral-invariant reference values
     (Sec. 3B) against the oracle: states, the evolving E and |J| references,
@@ -462,7 +463,7 @@ def test_radiation_reaction_checkpoint_restore_continues_bit_identically(pn):
 
 
 def test_radiation_reaction_schedules_are_bit_identical(pn):
-    """With radiation reaction the static, work-queue and compacting
+    """With radiation reaction the static, paired, work-queue and compacting
     schedules (any block size, chunking, graph replay or not, several runs)
     give the same bits; the autotuner picks among them."""
     cells = W.grid_cells(12, 16, 9.0, 30.0, seed=44)          # 192 orbits, many merge
@@ -470,14 +471,15 @@ def test_radiation_reaction_schedules_are_bit_identical(pn):
     assert (ref["status"] == pn.ORBIT_MERGED).mean() > 0.2
     for opts in (dict(schedule=1, block_size=32), dict(schedule=2, chunk_steps=64),
                  dict(schedule=2, chunk_steps=600, use_graph=0), dict(schedule=3, chunk_steps=50),
-                 dict(schedule=3, chunk_steps=40, register_variant=2), dict(schedule=0)):
+                 dict(schedule=3, chunk_steps=40, register_variant=2), dict(schedule=0),
+                 dict(schedule=4, block_size=32), dict(schedule=4, block_size=128)):
         g = gpu_run(pn, cells, 600, radiation_reaction=1, read_diag=True, chunks=3, **opts)
         for k in ("states", "integrals", "fli", "status", "t_stop", "newton_iters", "n_skip"):
             np.testing.assert_array_equal(g[k], ref[k], err_msg="%s %s" % (opts, k))
     s = pn.Scan(cells[:, W.BETA], radiation_reaction=1)
     s.setup(cells)
     tuned = s.autotune(100)
-    assert tuned["schedule"] in (pn.SCHED_STATIC, pn.SCHED_QUEUE, pn.SCHED_COMPACT)
+    assert tuned["schedule"] in (pn.SCHED_STATIC, pn.SCHED_QUEUE, pn.SCHED_COMPACT, pn.SCHED_PAIR)
     s.run(600.0, 1.0)
     out = s.read()
     s.close()
