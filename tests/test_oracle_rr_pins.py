@@ -219,3 +219,34 @@ def test_orbit3_spirals_in_with_its_energy_on_the_reference():
     assert binding[0] < binding[1] < binding[2]    # |E| grows: the binary hardens
     out = orc.scan(y0[None], beta, 2.0, 200_000, orc.config(rr=1, rk_order=5, r_escape=0))
     assert out["status"][0] == orc.MERGED and 2.0e5 < out["t_stop"][0] < 3.5e5
+
+
+def test_scalar_J_reference_matches_the_vector_form():
+    # d|J|/dt = J.(r x a)/|J| integrated as a scalar (the oracle) against the
+    # vector dJ/dt = r x a integrated beside it by a plain RK4 of this test,
+    # on the same RK4 stages of the full spinning Hamiltonian: the norms agree
+    # to the integration error
+    s = orc.system(0.7, kappa1=2.0, kappa2=4.0, pn_order=2, use_qm=1)
+    y = orc.setup_cells(np.array([[18.0, 1.0, 0.6, 0.2, 2.3, 1.7, 0.7, 0.8, 0.6]]))[0]
+    I0 = orc.integrals(s, y)
+    y14 = np.concatenate([y, I0[:2]])
+    Jv = I0[4:7].copy()
+    h = 0.5
+
+    def f(z14, jv):
+        d = orc.rhs_rr(s, z14)
+        a = orc.rr_accel(s, z14[:12])
+        return d, np.cross(z14[0:3], a)
+
+    for _ in range(1200):
+        k1, j1 = f(y14, Jv)
+        k2, j2 = f(y14 + 0.5 * h * k1, Jv)
+        k3, j3 = f(y14 + 0.5 * h * k2, Jv)
+        k4, j4 = f(y14 + h * k3, Jv)
+        y_next = orc.rk_step_rr(s, y14, h)
+        Jv = Jv + h * (j1 + 2 * j2 + 2 * j3 + j4) / 6.0
+        y14 = y_next
+    assert abs(np.linalg.norm(Jv) - y14[13]) <= 1e-10 * y14[13]
+    assert abs(y14[13] - I0[1]) > 1e-3 * I0[1]          # |J| did change
+    # and the vector reference stays on J(y) of the state
+    np.testing.assert_allclose(Jv, orc.integrals(s, y14[:12])[4:7], rtol=1e-9, atol=1e-9 * I0[1])
