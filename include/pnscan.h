@@ -158,7 +158,8 @@ typedef struct scan_summary_t {
     int64_t newton_iters;       /* Newton iterations, all orbits, both trajectories */
     int64_t n_skip;             /* corrections whose scaling was skipped */
     int64_t orbit_steps;        /* sum over orbits of steps taken since the initial state */
-    double max_dE;              /* max |E - E0| / |E0| over DONE orbits */
+    double max_dE;              /* max |E - E0| / |E0| over DONE orbits (E0: the reference at t
+                                   with radiation_reaction) */
     double max_dJ;              /* max ||J| - J0| / J0 over DONE orbits whose last step was dual-scaled */
     double max_dJ_all;          /* the same over all DONE orbits */
     int64_t n_final_fallback;   /* DONE orbits whose last step fell where the dual scaling is
@@ -199,7 +200,9 @@ int scan_run(scan_handle *h, const double *initial_states, double t_end, double 
 
 /* Copy results out (synchronises the stream).  Any output pointer may be NULL.
  *   states    n x 12  main trajectory at t_stop (or t_end)
- *   integrals n x 6   (E0, E, J0, |J|, |S1|, |S2|) of the main trajectory
+ *   integrals n x 6   (E0, E, J0, |J|, |S1|, |S2|) of the main trajectory; with
+ *                     radiation_reaction, E0 and J0 are the references at t_stop
+ *                     (integral-invariant relations, Sec. 3B)
  *   fli       n       FLI = sum_k log10(d_k/d0) + log10(d(t)/d0)
  *   status    n       PNSCAN_ORBIT_*
  *   t_stop    n       time at which the orbit stopped (t_end if DONE)
