@@ -410,6 +410,46 @@ def test_radiation_reaction_parity(pn, opts):
     check(pn, W.small_scan(seed=1)[::2], 1000, radiation_reaction=1, **opts)
 
 
+@pytest.mark.parametrize("opts", [dict(correct=2), dict(correct=3), dict(pn_order=1),
+                                  dict(pn_order=0, use_so=0, use_ss=0), dict(use_qm=1, rk_order=5, schedule=3,
+                                                                          chunk_steps=50)])
+def test_radiation_reaction_variants_parity(pn, opts):
+    """Radiation reaction with the ablation corrections, lower PN orders and
+    RK5 + QM on the compacting schedule, over the uneven batch (about half
+    the orbits merge)."""
+    check(pn, W.uneven_batch(n=96, seed=12), 400, radiation_reaction=1, **opts)
+
+
+def test_radiation_reaction_random_orientation_parity(pn):
+    """Random planes, spin directions, mass ratios and kappas (QM on), with
+    radiation reaction and an escape cut: merged, escaped and finished
+    orbits; the oracle's spread over one-ulp moves of all 12 components."""
+    y0, beta, k1, k2 = W.random_states(160, seed=31)
+    s = pn.Scan(beta, kappa1=k1, kappa2=k2, use_qm=1, radiation_reaction=1, r_escape=38.0)
+    s.run(400.0, 1.0, initial_states=y0)
+    g = s.read()
+    g.update(s.read_diag())
+    s.close()
+    cfg = oracle.config(use_qm=1, rr=1, r_escape=38.0)
+    o = oracle.scan(y0, beta, 1.0, 400, cfg, kappa1=k1, kappa2=k2)
+    counts = np.bincount(o["status"], minlength=6)
+    assert counts[oracle.MERGED] > 0 and counts[oracle.ESCAPED] > 0 and counts[oracle.DONE] > 0
+    s_state = np.zeros(y0.shape[0])
+    s_fli = np.zeros(y0.shape[0])
+    s_int = np.zeros((y0.shape[0], 6))
+    for comp in range(12):
+        y1 = y0.copy()
+        y1[:, comp] = np.nextafter(y1[:, comp], np.inf)
+        o1 = oracle.scan(y1, beta, 1.0, 400, cfg, kappa1=k1, kappa2=k2)
+        same = o1["status"] == o["status"]
+        s_state = np.maximum(s_state, np.where(same, block_relerr(o1["y"], o["y"]), 0.0))
+        s_fli = np.maximum(s_fli, np.where(same, np.abs(o1["fli"] - o["fli"]), 0.0))
+        s_int = np.maximum(s_int, np.where(same[:, None], np.abs(o1["integrals"] - o["integrals"]), 0.0))
+    o["s_integrals"] = s_int
+    o["integ_floor"] = 4 * 400 * 2.0 ** -52
+    assert_parity(g, o, s_state, s_fli, 400)
+
+
 def test_radiation_reaction_inspirals_merge_at_the_oracle_step(pn):
     """Close binaries spiral in: most reach the merger cut within the run,
     at the same step as in the oracle."""
