@@ -212,7 +212,8 @@ def paper_waveforms(t_end=1.0e4, every=2.0, out_dir=None, dissipative=False):
     """Fig. 10: orbit 4 (regular) and case II orbit 2 (chaotic), corrected
     RK5, h = 1, P = x, Q = y, N = z, R = 1.  Conservative (upper panels), or
     with the 2.5PN radiation reaction until the merger cut r < 6 (lower
-    panels; samples after an orbit stopped repeat its last state)."""
+    panels, sampled at least every 1 M since they last about one orbit; the
+    series written and summarised end where each orbit stopped)."""
     import os
     names, cells = W.paper_orbit_cells()
     names, cells = names[:2], cells[:2]
