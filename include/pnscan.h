@@ -169,11 +169,13 @@ typedef struct scan_summary_t {
     double fli_mean;            /* mean FLI over DONE orbits */
 } scan_summary_t;
 
-/* Fill *p with the defaults listed above (n = 0, no arrays).  Returns
- * PNSCAN_ERR_ARG if p is NULL. */
+/* Fill *p with the defaults listed above (n = 0, no arrays): the model and
+ * method parameters of Secs. 2-3 (Newton tolerance 1e-10 of Sec. 3A, FLI
+ * threshold of Sec. 3C).  Returns PNSCAN_ERR_ARG if p is NULL. */
 int scan_params_default(scan_params *p);
 
-/* Validate *p, copy the per-orbit parameters to the device and allocate the
+/* Validate *p, copy the per-orbit parameters (Sec. 2: mass ratio m1/m2 <= 1,
+ * quadrupole-monopole multipliers of Eqs. 4-5) to the device and allocate the
  * structure-of-arrays orbit state (about 330 bytes per orbit).  On success
  * *out receives a new handle; on failure *out is NULL.  Errors: ARG (bad
  * sizes, flags or beta_m outside (0,1]), OOM, CUDA, NODEVICE. */
@@ -190,7 +192,10 @@ int scan_setup(scan_handle *h, const double *cells);
 
 /* Integrate every running orbit from its current time to t_end with step
  * h_step (number of steps = round((t_end - t) / h_step), t the handle's
- * current time).  If initial_states (n x 12 row-major) is not NULL it first
+ * current time).  Each step is the loop of Sec. 3A / Fig. 1 for both FLI
+ * trajectories: an RK step of Eqs. 6-9, the spin lengths (Eq. 10), the dual
+ * scaling (Eqs. 11-13); then the termination tests and, every
+ * fli_renorm_steps, the FLI renormalisation (Secs. 3B-3C).  If initial_states (n x 12 row-major) is not NULL it first
  * replaces the state and resets as scan_setup does; if it is NULL the run
  * continues from the device-resident state (chunked runs reproduce one long
  * run exactly).  Errors: ARG (t_end < t, h_step <= 0 or too many steps),
@@ -210,19 +215,24 @@ int scan_run(scan_handle *h, const double *initial_states, double t_end, double 
 int scan_read(scan_handle *h, double *states, double *integrals, double *fli,
               int32_t *status, double *t_stop);
 
-/* Diagnostics (synchronises).  shadow n x 12 (shadow trajectory),
- * newton_iters n (Newton iterations of both trajectories), n_skip n (steps
- * of either trajectory whose dual scaling was singular or did not converge),
- * last_kind n (correction of the main trajectory's last step: 0 dual
- * scaling, 2 velocity scaling of p alone, 1 none).  Any pointer may be NULL. */
+/* Diagnostics of the correction (synchronises).  shadow n x 12 (the second
+ * FLI trajectory, Sec. 3B), newton_iters n (Newton iterations of Eq. 13, both
+ * trajectories), n_skip n (steps of either trajectory whose dual scaling was
+ * singular or did not converge), last_kind n (correction of the main
+ * trajectory's last step: 0 dual scaling, 2 velocity scaling of p alone as
+ * in the method Sec. 1 cites, 1 none).  Any pointer may be NULL.
+ * Errors: STATE, CUDA, KERNEL, TIMEOUT. */
 int scan_read_diag(scan_handle *h, double *shadow, int32_t *newton_iters, int32_t *n_skip,
                    int32_t *last_kind);
 
-/* Scan-level reduction on the device: chaotic count, integral drifts, status
- * histogram (synchronises; *out is a host struct).  Errors: ARG, STATE, CUDA. */
+/* Scan-level reduction on the device (synchronises; *out is a host struct):
+ * the chaotic count at the FLI threshold (the scan outcome of Sec. 3C), the
+ * integral errors (Table 2's measure of the correction) and the status
+ * histogram.  Errors: ARG, STATE, CUDA. */
 int scan_summary(scan_handle *h, scan_summary_t *out);
 
-/* Pick the integrator schedule, block size, chunk length, blocks per SM and
+/* Not in the paper (its launch shape is fixed, Sec. 3A).  Pick the
+ * integrator schedule, block size, chunk length, blocks per SM and
  * register variant by timing candidate launches on a copy of the handle's current state for
  * `steps` steps (the state itself is left unchanged).  The choice is kept in
  * the handle and used by later scan_run calls with schedule AUTO; it is also
@@ -265,17 +275,18 @@ int scan_restore(scan_handle *h, const void *buf, size_t bytes);
  * positive and finite, non-finite P or Q), STATE (no state), CUDA. */
 int scan_waveform(scan_handle *h, double R, const double *P, const double *Q, double *hplus, double *hcross);
 
-/* Device time of the integrator launches of the last scan_run (CUDA events
- * on the handle's stream; synchronises) and the number of kernels that run
- * launched: 1 for the static and work-queue schedules, 2 per epoch for the
- * compacting schedule (integrator + compaction).  *ms and *launches may be
- * NULL. */
+/* Device time of the integrator launches of the last scan_run (the elapsed
+ * time that Tables 2-3 report, here from CUDA events on the handle's stream;
+ * synchronises) and the number of kernels that run launched: 1 for the
+ * static, paired and work-queue schedules, 2 per epoch for the compacting
+ * schedule (integrator + compaction).  *ms and *launches may be NULL; 0 ms
+ * if the last scan_run launched nothing.  Errors: ARG, CUDA. */
 int scan_last_run_timing(scan_handle *h, double *ms, int *launches);
 
-/* Time iters x 8 x (256 threads on every SM) DFMA -- 8 independent chains
- * per thread -- on the handle's stream and return the achieved FP64 rate
- * (TFLOP/s, 2 flops per DFMA).  Used to measure the FP64 pipe's peak.
- * Errors: ARG, OOM, CUDA. */
+/* Not in the paper: the measured denominator of the integrator's FP64
+ * roofline.  Time iters x 8 x (256 threads on every SM) DFMA -- 8
+ * independent chains per thread -- on the handle's stream and return the
+ * achieved FP64 rate (TFLOP/s, 2 flops per DFMA).  Errors: ARG, OOM, CUDA. */
 int scan_fp64_peak(scan_handle *h, int iters, double *tflops);
 
 /* ---- reduction without run-time allocation ----
@@ -329,23 +340,29 @@ int scan_summary_noalloc(int64_t n, const int32_t *status, const double *fli,
 #define MLP_BATCH 128
 typedef struct mlp_handle mlp_handle;
 
-/* Xavier-uniform weights from seed (SplitMix64), zero biases and moments.
- * center/scale: host float[4].  members in 1..64.  Errors: ARG, OOM, CUDA, NODEVICE. */
+/* Surrogate (not in the paper).  Xavier-uniform weights from seed
+ * (SplitMix64), zero biases and moments.  center/scale: host float[4], scale
+ * nonzero.  members in 1..64.  Errors: ARG, OOM, CUDA, NODEVICE. */
 int mlp_create(int members, uint64_t seed, const float *center, const float *scale, void *cuda_stream,
                mlp_handle **out);
-/* Copy all members' parameters out / in ([members][MLP_PARAMS] floats);
- * mlp_set_params also clears the Adam moments. */
+/* Surrogate (not in the paper).  Copy all members' parameters out / in
+ * ([members][MLP_PARAMS] floats, device); mlp_set_params also clears the
+ * Adam moments.  Errors: ARG (NULL pointer), CUDA. */
 int mlp_get_params(mlp_handle *h, float *params);
 int mlp_set_params(mlp_handle *h, const float *params);
-/* `steps` Adam steps of minibatch MSE training on (X [n][4], y [n]); each
- * step draws MLP_BATCH rows with replacement from SplitMix64(seed, member,
- * step, row).  loss_hist [members][steps] (nullable) gets each step's loss. */
+/* Surrogate (not in the paper).  `steps` Adam steps of minibatch MSE
+ * training on (X [n][4], y [n]); each step draws MLP_BATCH rows with
+ * replacement from SplitMix64(seed, member, step, row).  loss_hist
+ * [members][steps] (nullable) gets each step's loss.  Errors: ARG (NULL
+ * X or y, n < 1, steps < 0, lr not positive), CUDA. */
 int mlp_train(mlp_handle *h, const float *X, const float *y, int64_t n, int steps, float lr, uint64_t seed,
               float *loss_hist);
-/* Loss and gradient of every member on exactly MLP_BATCH rows (X [128][4],
- * y [128]): grad [members][MLP_PARAMS], loss [members].  No update. */
+/* Surrogate (not in the paper).  Loss and gradient of every member on
+ * exactly MLP_BATCH rows (X [128][4], y [128]): grad [members][MLP_PARAMS],
+ * loss [members].  No update.  Errors: ARG (NULL pointer), CUDA. */
 int mlp_gradient(mlp_handle *h, const float *X, const float *y, float *grad, float *loss);
-/* Ensemble mean and spread (max - min over members) for X [n][4]. */
+/* Surrogate (not in the paper).  Ensemble mean and spread (max - min over
+ * members) for X [n][4].  Errors: ARG (n < 0, NULL arrays with n > 0), CUDA. */
 int mlp_predict(mlp_handle *h, const float *X, int64_t n, float *mean, float *spread);
 void mlp_destroy(mlp_handle *h);
 
@@ -369,13 +386,16 @@ int adaptive_select(const float *mean, const float *spread, int64_t n, float thr
 int adaptive_merge(const float *mean, int64_t n, float thr, const int32_t *idx, int64_t count,
                    const double *fli_sel, const int32_t *status_sel, int8_t *cls, void *cuda_stream);
 
-/* Free the handle's device buffers and the handle (NULL is a no-op). */
+/* Library utility (not in the paper): free the handle's device buffers and
+ * the handle (NULL is a no-op; no error is reported). */
 void scan_destroy(scan_handle *h);
 
-/* Static description of an error code. */
+/* Library utility (not in the paper): static description of an error code
+ * (an unknown code gets a generic string; never NULL). */
 const char *scan_strerror(int code);
 
-/* Library version string. */
+/* Library utility (not in the paper): version string; static, never NULL,
+ * names the build's target architecture (sm_103a). */
 const char *scan_version(void);
 
 #ifdef __cplusplus
