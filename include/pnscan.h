@@ -248,7 +248,7 @@ int scan_autotune(scan_handle *h, int steps, int *schedule, int *block_size, int
  * Newton settings, RK order, FLI and termination settings).  Restored into
  * a handle created with the same n and configuration, the next scan_run
  * continues exactly where the checkpointed handle stood: the results are
- * bit-identical to an uninterrupted run.  The paper has no counterpart.
+ * bit-identical to an uninterrupted run.  Not in the paper.
  *
  * scan_checkpoint_size: bytes of a checkpoint of h (0 for a NULL handle).
  * scan_checkpoint: write it to buf, HOST memory of at least that many bytes
@@ -391,11 +391,11 @@ int adaptive_merge(const float *mean, int64_t n, float thr, const int32_t *idx, 
 void scan_destroy(scan_handle *h);
 
 /* Library utility (not in the paper): static description of an error code
- * (an unknown code gets a generic string; never NULL). */
+ * (an unknown code gets a generic string; never NULL, no error). */
 const char *scan_strerror(int code);
 
 /* Library utility (not in the paper): version string; static, never NULL,
- * names the build's target architecture (sm_103a). */
+ * no error; names the build's target architecture (sm_103a). */
 const char *scan_version(void);
 
 #ifdef __cplusplus

@@ -40,6 +40,22 @@ def test_header_declares_the_boundary():
         assert required in names, names
 
 
+def test_every_declaration_cites_its_passage_and_errors():
+    """Each entry point of include/*.h sits under a comment that cites the
+    paper's passage (or says it is not in the paper) and states its errors."""
+    bad = []
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        pat = r"(/\*(?:(?!\*/).)*\*/)\s*\n((?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\([^;]*\);)"
+        for m in re.finditer(pat, text, flags=re.S):
+            com, name = m.group(1), m.group(3)
+            if not re.search(r"Sec\.|Eqs?\.|Table|Fig\.|not in the paper|Not in the paper", com):
+                bad.append((name, "no citation"))
+            if not re.search(r"Errors?|ERR_|Returns|returns|no error", com):
+                bad.append((name, "no error behaviour"))
+    assert not bad, bad
+
+
 def test_library_exports_every_declared_symbol(pn):
     L = ctypes.CDLL(pn.library_path)
     missing = [n for n in declared_functions() if not hasattr(L, n)]
