@@ -12,8 +12,10 @@ each a call into libpnscan:
    class elsewhere.
 
 The surrogate is trained (``Surrogate.train``) on FLI values the integrator
-itself produced for other scans.  PyTorch provides device memory and the
-stream only.
+itself produced for other scans.  Keyword options of ``training_set``,
+``adaptive_map`` and ``full_map`` are ``Scan`` options (``rk_order``,
+``use_qm``, ``radiation_reaction``, ...), passed to every integration.
+PyTorch provides device memory and the stream only.
 """
 import time
 
@@ -50,14 +52,14 @@ def classes(fli, status, thr):
     return (ok & (fli > thr)).to(torch.int8)
 
 
-def training_set(cell_sets, t_ends, h=1.0):
+def training_set(cell_sets, t_ends, h=1.0, **opts):
     """Surrogate training data from integrator runs: X (m x 4 float32) and the
     FLI (m float32) of every cell that did not become non-finite."""
     torch = _torch()
     Xs, ys = [], []
     for cells, t_end in zip(cell_sets, t_ends):
         cd = torch.as_tensor(np.ascontiguousarray(cells[:, :9]), device="cuda")
-        out = integrate_cells(cd, t_end, h)
+        out = integrate_cells(cd, t_end, h, **opts)
         keep = out["status"] != ORBIT_NONFINITE
         Xs.append(adaptive_features(cd)[keep])
         ys.append(out["fli"][keep].float())
@@ -70,7 +72,7 @@ def train_surrogate(X, y, members=5, steps=4000, lr=3e-3, seed=1):
     return sur, hist
 
 
-def adaptive_map(sur, cells_d, t_end, h=1.0, thr=6.0, band=1.0, spread_max=0.5):
+def adaptive_map(sur, cells_d, t_end, h=1.0, thr=6.0, band=1.0, spread_max=0.5, **opts):
     """Class map of the grid cells_d (n x 9 float64, CUDA) and its cost."""
     torch = _torch()
     torch.cuda.synchronize()
@@ -79,7 +81,7 @@ def adaptive_map(sur, cells_d, t_end, h=1.0, thr=6.0, band=1.0, spread_max=0.5):
     mean, spread = sur.predict(X)
     idx, sel = adaptive_select(mean, spread, thr, band, spread_max, cells=cells_d)
     t1 = time.perf_counter()
-    out = integrate_cells(sel, t_end, h)
+    out = integrate_cells(sel, t_end, h, **opts)
     cls = adaptive_merge(mean, thr, idx, out["fli"], out["status"])
     torch.cuda.synchronize()
     t2 = time.perf_counter()
@@ -87,12 +89,12 @@ def adaptive_map(sur, cells_d, t_end, h=1.0, thr=6.0, band=1.0, spread_max=0.5):
                 n_marked=int(idx.shape[0]), seconds=t2 - t0, seconds_surrogate=t1 - t0)
 
 
-def full_map(cells_d, t_end, h=1.0, thr=6.0):
+def full_map(cells_d, t_end, h=1.0, thr=6.0, **opts):
     """Class map from integrating every cell, and its cost."""
     torch = _torch()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    out = integrate_cells(cells_d, t_end, h)
+    out = integrate_cells(cells_d, t_end, h, **opts)
     cls = classes(out["fli"], out["status"], thr)
     torch.cuda.synchronize()
     return dict(cls=cls, fli=out["fli"], status=out["status"], seconds=time.perf_counter() - t0)

@@ -80,3 +80,28 @@ def test_training_is_what_saves_the_work(env):
     assert trained["n_marked"] < 0.5 * raw["n_marked"], (trained["n_marked"], raw["n_marked"])
     for res in (raw, trained):
         assert (res["cls"] != full["cls"]).float().mean().item() <= 0.005
+
+
+def test_scan_options_reach_every_integration(env):
+    """With radiation reaction and RK5 passed through, the cells the adaptive
+    scan integrates carry exactly the values of integrating the whole grid
+    with the same options, and of a direct Scan of those cells."""
+    import torch
+    import paper_1802_00147_gb300 as pn
+    A, sur, hist, cells_d = env
+    opts = dict(radiation_reaction=1, rk_order=5)
+    t_end = 500.0
+    full = A.full_map(cells_d, t_end, thr=2.0, **opts)
+    plain = A.full_map(cells_d, t_end, thr=2.0)
+    assert not torch.equal(full["fli"], plain["fli"])          # the options changed the run
+    res = A.adaptive_map(sur, cells_d, t_end, thr=2.0, band=0.5, spread_max=0.25, **opts)
+    idx = res["idx"].long()
+    assert res["n_marked"] > 0
+    assert torch.equal(res["fli_sel"], full["fli"][idx])
+    assert torch.equal(res["status_sel"], full["status"][idx])
+    sel = cells_d[idx].cpu().numpy()
+    with pn.Scan(sel[:, 6], **opts) as s:
+        s.setup(sel)
+        s.run(t_end, 1.0)
+        direct = s.read()
+    np.testing.assert_array_equal(direct["fli"], res["fli_sel"].cpu().numpy())
