@@ -160,7 +160,9 @@ int orc_scan(int64_t n, const double *y0, const double *beta,
              int32_t *n_skip, int32_t *last_kind, int nthreads);
 
 /* Same integrator without the shadow trajectory, recording the state after
- * every `every` steps into trace[(nsteps/every) * 12] (single orbit). */
+ * every `every` steps into trace[(nsteps/every) * 12] (single orbit).  With
+ * cfg->rr the reference E and |J| advance with the state (not recorded), and
+ * there is no termination test: stop before the orbit plunges. */
 int orc_trace(const double y0[12], double beta, double kappa1, double kappa2,
               const orc_config *cfg, double h, int64_t nsteps, int64_t every,
               double *trace);
