@@ -1,8 +1,9 @@
 """Out-of-bounds writes, caught without a sanitizer: every device buffer the
 library allocates comes from a test allocator (the alloc_fn / free_fn hooks
 of scan_params) that surrounds it with 4 KiB of canary bytes on each side.
-After runs through every schedule and every reading call, and at each free,
-the canaries must be intact."""
+After runs through every schedule (and, with the 2.5PN radiation reaction,
+the static, compacting and paired ones) and every reading call, and at each
+free, the canaries must be intact."""
 import ctypes
 
 import numpy as np
@@ -60,8 +61,8 @@ class GuardedAllocator:
             self.check_one(ptr)
 
 
-@pytest.mark.parametrize("schedule", [1, 2, 3, 4])
-def test_no_write_outside_the_library_buffers(pn, schedule):
+@pytest.mark.parametrize("schedule,rr", [(1, 0), (2, 0), (3, 0), (4, 0), (1, 1), (3, 1), (4, 1)])
+def test_no_write_outside_the_library_buffers(pn, schedule, rr):
     import torch
     from paper_1802_00147_gb300 import workloads as W
     cells = W.uneven_batch(n=1000, seed=17)
@@ -73,6 +74,7 @@ def test_no_write_outside_the_library_buffers(pn, schedule):
     p.schedule = schedule
     p.chunk_steps = 40
     p.fli_cap = 12.0
+    p.radiation_reaction = rr
     p.alloc_fn, p.free_fn = ga.cb
     h = pn.scan_create(p)
     try:
