@@ -171,7 +171,8 @@ class ClockSampler:
 # ------------------------------------------------------------ CPU oracle
 def cpu_oracle_rate(cells, target_s=15.0, steps_cap=20000):
     """Time the CPU oracle (OpenMP over orbits, all host cores) on a bounded
-    sample of the workload; returns (orbit-steps/s, sample description, cores)."""
+    sample of the workload to the benchmark's t_end; returns (orbit-steps/s,
+    sample description, cores, seconds, (sample indices, oracle outputs))."""
     import oracle
     from paper_1802_00147_gb300 import workloads as W
     cores = oracle.max_threads()
@@ -184,14 +185,27 @@ def cpu_oracle_rate(cells, target_s=15.0, steps_cap=20000):
     nsteps = steps_cap
     m = int(max(cores, min(cells.shape[0], rate0 * target_s / nsteps)))
     m = max(cores, (m // cores) * cores)
-    sub, _ = W.subset(cells, m, seed=32)
+    sub, idx = W.subset(cells, m, seed=32)
     y0 = oracle.setup_cells(sub[:, :9])
     t0 = time.perf_counter()
     o = oracle.scan(y0, sub[:, W.BETA], H_STEP, nsteps, oracle.config())
     dt = time.perf_counter() - t0
     steps_done = float(o["t_stop"].sum() / H_STEP)
     return (steps_done / dt, "%d seeded orbits of the 314x314 scan to t_end=%g (%d orbit-steps, %.1f s)"
-            % (m, nsteps * H_STEP, steps_done, dt), cores, dt)
+            % (m, nsteps * H_STEP, steps_done, dt), cores, dt, (idx, o))
+
+
+def oracle_agreement(g_status, g_fli, o_status, o_fli, thr=6.0):
+    """The timed run against the oracle on the same orbits (the CPU-baseline
+    sample, integrated to the same t_end): fraction of equal statuses, and
+    among the orbits both finished, fraction of equal classes (FLI > thr)."""
+    g_status, o_status = np.asarray(g_status), np.asarray(o_status)
+    same = g_status == o_status
+    done = same & (o_status == 1)                # DONE in both numberings
+    cls = (np.asarray(g_fli)[done] > thr) == (np.asarray(o_fli)[done] > thr)
+    return {"orbits": int(o_status.size), "status_agree": float(same.mean()) if same.size else None,
+            "class_orbits": int(cls.size), "class_agree": float(cls.mean()) if cls.size else None,
+            "threshold": thr}
 
 
 def cpu_oracle_rate_single_core(cells, m=64, nsteps=20000):
@@ -213,7 +227,7 @@ def run_reference(args, rank, world):
         return
     cells = workload()
     # calibrate once; every step is the same bounded sample
-    rate, sample, cores, dt = cpu_oracle_rate(cells, target_s=8.0)
+    rate, sample, cores, dt, _ = cpu_oracle_rate(cells, target_s=8.0)
     import oracle
     from paper_1802_00147_gb300 import workloads as W
     m = int(sample.split()[0])
@@ -501,7 +515,14 @@ def run_ours(args, rank, world, local_rank):
     flops = algorithmic_flops(summ["orbit_steps"], summ["newton_iters"])
     achieved = flops / (ms_kernel * 1e-3) / 1e12
     traffic = traffic_per_run(shape["schedule"])
-    cpu_rate, cpu_sample, cores, _ = cpu_oracle_rate(cells_h, target_s=15.0)
+    cpu_rate, cpu_sample, cores, _, (cpu_idx, cpu_out) = cpu_oracle_rate(cells_h, target_s=15.0)
+    try:
+        final = scan.read()
+        host = {k: (v.cpu().numpy() if hasattr(v, "cpu") else np.asarray(v)) for k, v in final.items()}
+        agreement = oracle_agreement(host["status"][cpu_idx], host["fli"][cpu_idx],
+                                     cpu_out["status"], cpu_out["fli"])
+    except Exception as e:          # a diagnostic must not cost the benchmark line
+        agreement = {"error": repr(e)}
     cpu_rate_1 = cpu_oracle_rate_single_core(cells_h)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -520,7 +541,8 @@ def run_ours(args, rank, world, local_rank):
                      "peak_measured_dfma": fp64_measured,
                      "frac_of_measured": achieved / fp64_measured},
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": cpu_sample, "single_core_value": cpu_rate_1,
+                         "sample": cpu_sample, "agreement_with_this_run": agreement,
+                         "single_core_value": cpu_rate_1,
                          "single_core_sample": "64 seeded orbits of the 314x314 scan to t_end=2e4 on one core"},
         "e2e": {"value": e2e_steps / e2e_dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},

@@ -41,3 +41,17 @@ def test_traffic_stays_below_the_algorithmic_bytes():
     n = 314 * 314
     for nbytes in bench.TRAFFIC_BYTES_PER_RUN.values():
         assert 0 < nbytes <= n * bench.STATE_BYTES_PER_ORBIT
+
+
+def test_oracle_agreement_counts_statuses_and_classes():
+    import numpy as np
+    g_status = np.array([1, 1, 1, 2, 1, 3])
+    o_status = np.array([1, 1, 1, 2, 2, 3])
+    g_fli = np.array([7.0, 2.0, 6.5, 9.0, 1.0, 0.0])
+    o_fli = np.array([7.2, 2.1, 5.9, 9.0, 1.0, 0.0])
+    a = bench.oracle_agreement(g_status, g_fli, o_status, o_fli, thr=6.0)
+    assert a["orbits"] == 6 and a["status_agree"] == 5 / 6
+    # finished in both: orbits 0, 1, 2; orbit 2 sits on opposite sides of 6
+    assert a["class_orbits"] == 3 and a["class_agree"] == 2 / 3
+    empty = bench.oracle_agreement([], [], [], [])
+    assert empty["orbits"] == 0 and empty["status_agree"] is None and empty["class_agree"] is None
