@@ -195,6 +195,32 @@ def cpu_oracle_rate(cells, target_s=15.0, steps_cap=20000):
             % (m, nsteps * H_STEP, steps_done, dt), cores, dt, (idx, o))
 
 
+# The integrator each tuned shape runs (conservative, RK4), as the kernel
+# symbols ptxas reports: k_integrate_queue<QM, MINB, SMEM, RK, ROLLED, RR>
+# per register_variant, k_integrate_static<QM, RK, RR>, k_integrate_pair<QM, RK, RR>.
+_QUEUE_VARIANT = {4: "k_integrate_queueILb0ELi2ELb0ELi4ELb1ELb0E", 2: "k_integrate_queueILb0ELi2ELb0ELi4ELb0ELb0E",
+                  3: "k_integrate_queueILb0ELi3ELb1ELi4ELb1ELb0E"}
+
+
+def register_occupancy(shape, registers):
+    """Registers per thread of the integrator a tuned shape runs (from the
+    build's ptxas report) and the resident blocks and warps per SM they allow
+    (65,536 registers per SM, allocated per warp in units of 256)."""
+    sched, block = shape.get("schedule"), shape.get("block_size") or 128
+    if sched in (2, 3):
+        key = _QUEUE_VARIANT.get(shape.get("register_variant") or 4)
+    else:
+        key = {1: "k_integrate_staticILb0ELi4ELb0E", 4: "k_integrate_pairILb0ELi4ELb0E"}.get(sched)
+    found = [v for k, v in registers.items() if key and key in k]
+    if len(found) != 1:
+        return None
+    regs = found[0]
+    per_warp = -(-regs * 32 // 256) * 256
+    blocks = min(32, 65536 // (per_warp * (block // 32)))
+    return {"kernel": key.split("I")[0], "registers_per_thread": regs, "block_size": block,
+            "blocks_per_sm": blocks, "warps_per_sm": blocks * block // 32}
+
+
 def oracle_agreement(g_status, g_fli, o_status, o_fli, thr=6.0):
     """The timed run against the oracle on the same orbits (the CPU-baseline
     sample, integrated to the same t_end): fraction of equal statuses, and
@@ -516,6 +542,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = flops / (ms_kernel * 1e-3) / 1e12
     traffic = traffic_per_run(shape["schedule"])
     cpu_rate, cpu_sample, cores, _, (cpu_idx, cpu_out) = cpu_oracle_rate(cells_h, target_s=15.0)
+    occupancy = register_occupancy(shape, pnbuild.kernel_registers())
     try:
         final = scan.read()
         host = {k: (v.cpu().numpy() if hasattr(v, "cpu") else np.asarray(v)) for k, v in final.items()}
@@ -539,7 +566,8 @@ def run_ours(args, rank, world, local_rank):
                      "flops_per_run": flops,
                      "traffic_algorithmic_bytes": int(n * STATE_BYTES_PER_ORBIT),
                      "peak_measured_dfma": fp64_measured,
-                     "frac_of_measured": achieved / fp64_measured},
+                     "frac_of_measured": achieved / fp64_measured,
+                     "occupancy": occupancy},
         "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": cpu_sample, "agreement_with_this_run": agreement,
                          "single_core_value": cpu_rate_1,

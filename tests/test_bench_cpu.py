@@ -55,3 +55,30 @@ def test_oracle_agreement_counts_statuses_and_classes():
     assert a["class_orbits"] == 3 and a["class_agree"] == 2 / 3
     empty = bench.oracle_agreement([], [], [], [])
     assert empty["orbits"] == 0 and empty["status_agree"] is None and empty["class_agree"] is None
+
+
+def test_register_occupancy_arithmetic():
+    regs = {"_ZN6pnscan17k_integrate_queueILb0ELi2ELb0ELi4ELb1ELb0EEEvX": 253,
+            "_ZN6pnscan17k_integrate_queueILb1ELi2ELb0ELi4ELb1ELb0EEEvX": 250,
+            "_ZN6pnscan18k_integrate_staticILb0ELi4ELb0EEEvX": 210,
+            "_ZN6pnscan16k_integrate_pairILb0ELi4ELb0EEEvX": 164}
+    q = bench.register_occupancy({"schedule": 3, "block_size": 128, "register_variant": 4}, regs)
+    # 253 -> 8,192 registers per warp: two 128-thread blocks, 8 warps per SM
+    assert q == {"kernel": "k_integrate_queue", "registers_per_thread": 253, "block_size": 128,
+                 "blocks_per_sm": 2, "warps_per_sm": 8}
+    st = bench.register_occupancy({"schedule": 1, "block_size": 32}, regs)
+    assert st["registers_per_thread"] == 210 and st["blocks_per_sm"] == 9 and st["warps_per_sm"] == 9
+    pr = bench.register_occupancy({"schedule": 4, "block_size": 32}, regs)
+    assert pr["registers_per_thread"] == 164 and pr["blocks_per_sm"] == 12
+    assert bench.register_occupancy({"schedule": 2, "block_size": 128, "register_variant": 3}, regs) is None
+    assert bench.register_occupancy({"schedule": 3}, {}) is None
+
+
+def test_build_records_the_timed_kernels_registers():
+    from paper_1802_00147_gb300 import build
+    build.build()
+    if not build.kernel_registers():
+        build.build(force=True)
+    regs = build.kernel_registers()
+    q = bench.register_occupancy({"schedule": 3, "block_size": 128, "register_variant": 4}, regs)
+    assert q is not None and 128 <= q["registers_per_thread"] <= 255 and q["blocks_per_sm"] >= 1
