@@ -250,3 +250,21 @@ def test_scalar_J_reference_matches_the_vector_form():
     assert abs(y14[13] - I0[1]) > 1e-3 * I0[1]          # |J| did change
     # and the vector reference stays on J(y) of the state
     np.testing.assert_allclose(Jv, orc.integrals(s, y14[:12])[4:7], rtol=1e-9, atol=1e-9 * I0[1])
+
+
+def test_ablation_modes_restore_what_they_claim_under_radiation_reaction():
+    # orbit 3 with radiation reaction to t = 6000 (RK4, h = 2): velocity
+    # scaling (mode 3) holds E on its moving reference but not |J|; spin
+    # lengths alone (mode 2) hold neither; the dual scaling holds both
+    beta, y0 = golden_orbit("orbit_3")
+    s = orc.system(beta, pn_order=2)
+    I0 = orc.integrals(s, y0)
+    res = {}
+    for mode in (0, 1, 2, 3):
+        out = orc.scan(y0[None], beta, 2.0, 3000, orc.config(rr=1, correct=mode, fli_renorm=0))
+        E0, E, J0, J, S1, S2 = out["integrals"][0]
+        res[mode] = (abs(E - E0) / abs(E0), abs(J - J0) / J0, abs(S1 - I0[2]) / I0[2], abs(S2 - I0[3]) / I0[3])
+    assert max(res[1]) <= 1e-14
+    assert res[3][0] <= 1e-14 and res[3][1] > 100 * res[1][1] and max(res[3][2:]) <= 1e-14
+    assert res[2][0] > 100 * res[1][0] and max(res[2][2:]) <= 1e-14
+    assert res[0][0] > 100 * res[1][0] and res[0][1] > 100 * res[1][1]
