@@ -63,8 +63,7 @@ FP64_PEAK_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the integrator
 # over one scan_run of this workload, from ncu captures of
-# `bench.py --profile --schedule S` (summary and commands in
-# profiles/k_integrate_queue_dram_314x314.md), keyed by schedule.  Valid only
+# `bench.py --profile --schedule S`, keyed by schedule.  Valid only
 # for the kernel sources they were taken with: reported as null once any of
 # these files differs from the recorded SHA-256.
 TRAFFIC_SOURCES = {

@@ -130,9 +130,11 @@ typedef struct scan_params {
                                 kernel sets an error flag and returns, and the next synchronising
                                 call reports PNSCAN_ERR_KERNEL.  0 (default): 20 s plus 2 ms per
                                 step of the chunk, so that long chunks never time out while their
-                                predecessor is still running */
-    int debug_stall_group;   /* test hook, default -1 (off): group g never publishes its first
-                                chunk, so the wait of its second chunk runs out */
+                                predecessor is still running.  For testing this bound, the
+                                environment variable PNSCAN_TEST_STALL_GROUP=g, read by
+                                scan_create, makes 32-orbit group g of the handle's queue runs
+                                withhold its first chunk, so the wait of its second chunk runs
+                                out */
     void *(*alloc_fn)(size_t bytes, void *ctx);  /* optional device allocator (e.g. PyTorch's) */
     void (*free_fn)(void *ptr, void *ctx);
     void *alloc_ctx;
@@ -292,8 +294,8 @@ int scan_fp64_peak(scan_handle *h, int iters, double *tflops);
 /* ---- reduction without run-time allocation ----
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory when they reduce a scan (a framework whose
- * allocator already holds the memory budget, a loop that must not allocate
- * after start-up, or work issued while a stream is being captured).
+ * caching allocator already holds the memory budget, or a loop that must
+ * not allocate after start-up).
  *
  * scan_summary_noalloc computes the same reduction as scan_summary over
  * caller-owned DEVICE arrays -- typically what scan_read / scan_read_diag
@@ -350,11 +352,21 @@ int mlp_create(int members, uint64_t seed, const float *center, const float *sca
  * Adam moments.  Errors: ARG (NULL pointer), CUDA. */
 int mlp_get_params(mlp_handle *h, float *params);
 int mlp_set_params(mlp_handle *h, const float *params);
+/* Surrogate (not in the paper).  Copy the Adam moments out: m and v, each
+ * [members][MLP_PARAMS] floats (device), in the parameter layout.  Zero
+ * after mlp_create and mlp_set_params.  Errors: ARG (NULL pointer), CUDA. */
+int mlp_get_moments(mlp_handle *h, float *m, float *v);
 /* Surrogate (not in the paper).  `steps` Adam steps of minibatch MSE
- * training on (X [n][4], y [n]); each step draws MLP_BATCH rows with
- * replacement from SplitMix64(seed, member, step, row).  loss_hist
- * [members][steps] (nullable) gets each step's loss.  Errors: ARG (NULL
- * X or y, n < 1, steps < 0, lr not positive), CUDA. */
+ * training on (X [n][4], y [n]).  Adam step t (counted from 1 since
+ * mlp_create / mlp_set_params, across calls) draws MLP_BATCH rows with
+ * replacement: row j (0 <= j < 128) of member k is
+ *   X[ SM(seed ^ SM((k << 40) ^ ((t - 1) << 8) ^ j)) mod n ],
+ * where SM is the SplitMix64 output function of Steele, Lea & Flood (2014)
+ * applied to x + 0x9E3779B97F4A7C15 (all arithmetic modulo 2^64).  The
+ * update is Adam (Kingma & Ba 2015: beta1 0.9, beta2 0.999, eps 1e-8 added
+ * to the square root of the bias-corrected second moment) in FP32.
+ * loss_hist [members][steps] (nullable) gets each step's loss.  Errors: ARG
+ * (NULL X or y, n < 1, steps < 0, lr not positive), CUDA. */
 int mlp_train(mlp_handle *h, const float *X, const float *y, int64_t n, int steps, float lr, uint64_t seed,
               float *loss_hist);
 /* Surrogate (not in the paper).  Loss and gradient of every member on

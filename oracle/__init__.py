@@ -6,6 +6,7 @@ no code with the CUDA library; see ``pn_oracle.c`` for the method and its
 citations (arXiv:1802.00147, Sec. 2 Eqs. 1-13, Sec. 3).
 """
 import ctypes as _ct
+from contextlib import contextmanager as _contextmanager
 
 import numpy as _np
 
@@ -49,40 +50,61 @@ def config(pn_order=2, use_so=1, use_ss=1, use_qm=0, correct=1, newton_tol=1e-10
 def lib():
     global _lib
     if _lib is None:
-        L = _ct.CDLL(_build())
-        P = _ct.POINTER
-        d, i, i64 = _ct.c_double, _ct.c_int, _ct.c_int64
-        dp = P(d)
-        L.orc_sys_init.argtypes = [P(Sys), d, d, d, i, i, i, i]
-        for name in ("orc_H_newton", "orc_H_1pn", "orc_H_2pn", "orc_H_so", "orc_H_s1s2",
-                     "orc_H_qm", "orc_hamiltonian"):
-            f = getattr(L, name)
-            f.argtypes = [P(Sys), dp]
-            f.restype = d
-        L.orc_gradient.argtypes = [P(Sys), dp, dp]
-        L.orc_rhs.argtypes = [P(Sys), dp, dp]
-        L.orc_rk4_step.argtypes = [P(Sys), dp, d]
-        L.orc_rk5_step.argtypes = [P(Sys), dp, d]
-        L.orc_integrals.argtypes = [P(Sys), dp, dp]
-        L.orc_rr_accel.argtypes = [P(Sys), d, d, dp, dp]
-        L.orc_rhs_rr.argtypes = [P(Sys), d, d, dp, dp]
-        L.orc_rk_step_rr.argtypes = [P(Sys), d, d, i, dp, d]
-        L.orc_correct.argtypes = [P(Sys), dp, dp, d, i, d, P(i), dp]
-        L.orc_correct.restype = i
-        L.orc_waveform.argtypes = [P(Sys), dp, d, dp, dp, dp]
-        L.orc_newton_trace.argtypes = [P(Sys), dp, dp, i, dp, dp]
-        L.orc_newton_trace.restype = i
-        L.orc_correct_rule.argtypes = [P(Sys), dp, dp, d, i, d, i, i, P(i), dp]
-        L.orc_correct_rule.restype = i
-        L.orc_setup_cell.argtypes = [dp, dp]
-        L.orc_scan.argtypes = [i64, dp, dp, dp, dp, P(Config), d, i64, dp, dp, dp, dp,
-                               P(_ct.c_int32), dp, P(i64), P(_ct.c_int32), P(_ct.c_int32), i]
-        L.orc_scan.restype = i
-        L.orc_trace.argtypes = [dp, d, d, d, P(Config), d, i64, i64, dp]
-        L.orc_trace.restype = i
-        L.orc_max_threads.restype = i
-        _lib = L
+        _lib = _declare(_ct.CDLL(_build()))
     return _lib
+
+
+def load_variant(path):
+    """Another build of pn_oracle.c (e.g. build.build_variant's) with the
+    same signatures declared; use it through `using`."""
+    return _declare(_ct.CDLL(path))
+
+
+@_contextmanager
+def using(L):
+    """Run the functions of this module on the oracle library L."""
+    global _lib
+    old = _lib
+    _lib = L
+    try:
+        yield L
+    finally:
+        _lib = old
+
+
+def _declare(L):
+    P = _ct.POINTER
+    d, i, i64 = _ct.c_double, _ct.c_int, _ct.c_int64
+    dp = P(d)
+    L.orc_sys_init.argtypes = [P(Sys), d, d, d, i, i, i, i]
+    for name in ("orc_H_newton", "orc_H_1pn", "orc_H_2pn", "orc_H_so", "orc_H_s1s2",
+                 "orc_H_qm", "orc_hamiltonian"):
+        f = getattr(L, name)
+        f.argtypes = [P(Sys), dp]
+        f.restype = d
+    L.orc_gradient.argtypes = [P(Sys), dp, dp]
+    L.orc_rhs.argtypes = [P(Sys), dp, dp]
+    L.orc_rk4_step.argtypes = [P(Sys), dp, d]
+    L.orc_rk5_step.argtypes = [P(Sys), dp, d]
+    L.orc_integrals.argtypes = [P(Sys), dp, dp]
+    L.orc_rr_accel.argtypes = [P(Sys), d, d, dp, dp]
+    L.orc_rhs_rr.argtypes = [P(Sys), d, d, dp, dp]
+    L.orc_rk_step_rr.argtypes = [P(Sys), d, d, i, dp, d]
+    L.orc_correct.argtypes = [P(Sys), dp, dp, d, i, d, P(i), dp]
+    L.orc_correct.restype = i
+    L.orc_waveform.argtypes = [P(Sys), dp, d, dp, dp, dp]
+    L.orc_newton_trace.argtypes = [P(Sys), dp, dp, i, dp, dp]
+    L.orc_newton_trace.restype = i
+    L.orc_correct_rule.argtypes = [P(Sys), dp, dp, d, i, d, i, i, P(i), dp]
+    L.orc_correct_rule.restype = i
+    L.orc_setup_cell.argtypes = [dp, dp]
+    L.orc_scan.argtypes = [i64, dp, dp, dp, dp, P(Config), d, i64, dp, dp, dp, dp,
+                           P(_ct.c_int32), dp, P(i64), P(_ct.c_int32), P(_ct.c_int32), i]
+    L.orc_scan.restype = i
+    L.orc_trace.argtypes = [dp, d, d, d, P(Config), d, i64, i64, dp]
+    L.orc_trace.restype = i
+    L.orc_max_threads.restype = i
+    return L
 
 
 def _dp(a):

@@ -27,5 +27,15 @@ def build(force: bool = False) -> str:
     return LIB
 
 
+def build_variant(out: str, extra_flags) -> str:
+    """Compile pn_oracle.c with other code-generation flags into `out` (for
+    tests that compare two roundings of the same arithmetic, e.g. with
+    multiply-adds contracted into FMAs)."""
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-Wall"] + list(extra_flags) + \
+          ["-o", out, SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    return out
+
+
 if __name__ == "__main__":
     print(build(force=True))

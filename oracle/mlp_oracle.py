@@ -81,6 +81,31 @@ def adam_step(p, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     return p - lr * mhat / (np.sqrt(vhat) + eps), m, v
 
 
+GOLDEN_GAMMA = 0x9E3779B97F4A7C15
+MASK64 = (1 << 64) - 1
+
+
+def splitmix64(x):
+    """SplitMix64 (Steele, Lea & Flood 2014): advance the state by the golden
+    gamma and return the output mix of the new state.  Python integers,
+    reduced modulo 2**64 after every operation."""
+    z = (int(x) + GOLDEN_GAMMA) & MASK64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+    return z ^ (z >> 31)
+
+
+def batch_rows(seed, member, t, n, batch=128):
+    """Rows of the minibatch of Adam step t (from 1) of ensemble member
+    `member`, drawn with replacement from n rows: row j is
+    SM(seed ^ SM((member << 40) ^ ((t - 1) << 8) ^ j)) mod n."""
+    out = np.empty(batch, dtype=np.int64)
+    for j in range(batch):
+        key = ((int(member) << 40) ^ ((int(t) - 1) << 8) ^ j) & MASK64
+        out[j] = splitmix64(int(seed) ^ splitmix64(key)) % int(n)
+    return out
+
+
 def ensemble_predict(params, z):
     """params: (K, P).  Returns (mean, spread = max - min) over the members."""
     ys = np.stack([forward(p, z)[0] for p in params])

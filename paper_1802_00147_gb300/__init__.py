@@ -53,7 +53,7 @@ class ScanParams(_ct.Structure):
         ("epoch_steps", _ct.c_int),
         ("blocks_per_sm", _ct.c_int), ("register_variant", _ct.c_int), ("use_graph", _ct.c_int),
         ("sync_timeout_s", _ct.c_double),
-        ("queue_wait_limit_ms", _ct.c_int), ("debug_stall_group", _ct.c_int),
+        ("queue_wait_limit_ms", _ct.c_int),
         ("alloc_fn", _ALLOC_FN), ("free_fn", _FREE_FN), ("alloc_ctx", _ct.c_void_p),
         ("radiation_reaction", _ct.c_int), ("rr_gauge_a", _ct.c_double), ("rr_gauge_b", _ct.c_double),
     ]
@@ -113,6 +113,7 @@ def lib():
         L.mlp_create.argtypes = [i, u64, P(f), P(f), vp, P(vp)]
         L.mlp_get_params.argtypes = [vp, vp]
         L.mlp_set_params.argtypes = [vp, vp]
+        L.mlp_get_moments.argtypes = [vp, vp, vp]
         L.mlp_train.argtypes = [vp, vp, vp, i64, i, f, u64, vp]
         L.mlp_gradient.argtypes = [vp, vp, vp, vp, vp]
         L.mlp_predict.argtypes = [vp, vp, i64, vp, vp]
@@ -124,7 +125,7 @@ def lib():
         L.adaptive_select_workspace.restype = _ct.c_size_t
         L.adaptive_select.argtypes = [vp, vp, i64, f, f, f, vp, vp, vp, P(i64), vp, vp]
         L.adaptive_merge.argtypes = [vp, i64, f, vp, i64, vp, vp, vp, vp]
-        for name in ("mlp_create", "mlp_get_params", "mlp_set_params", "mlp_train", "mlp_gradient",
+        for name in ("mlp_create", "mlp_get_params", "mlp_get_moments", "mlp_set_params", "mlp_train", "mlp_gradient",
                      "mlp_predict", "adaptive_select", "adaptive_merge"):
             getattr(L, name).restype = i
         L.scan_destroy.argtypes = [vp]
@@ -434,6 +435,13 @@ class Surrogate:
         out = self._torch.empty((self.members, MLP_PARAMS), dtype=self._torch.float32, device="cuda")
         _check(lib().mlp_get_params(self.h, _ptr(out)), "mlp_get_params")
         return out
+
+    def get_moments(self):
+        """The Adam moments (m, v), each (members, MLP_PARAMS) float32."""
+        m = self._torch.empty((self.members, MLP_PARAMS), dtype=self._torch.float32, device="cuda")
+        v = self._torch.empty_like(m)
+        _check(lib().mlp_get_moments(self.h, _ptr(m), _ptr(v)), "mlp_get_moments")
+        return m, v
 
     def set_params(self, params):
         p = self._f32(params, (self.members, MLP_PARAMS))

@@ -69,6 +69,16 @@ int mlp_get_params(mlp_handle* h, float* params)
     return cudaStreamSynchronize(h->stream) == cudaSuccess ? PNSCAN_OK : PNSCAN_ERR_CUDA;
 }
 
+int mlp_get_moments(mlp_handle* h, float* m, float* v)
+{
+    if (!h || !m || !v) return PNSCAN_ERR_ARG;
+    const size_t bytes = sizeof(float) * h->members * NPARAM;
+    if (cudaMemcpyAsync(m, h->adam_m, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(v, h->adam_v, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+        return PNSCAN_ERR_CUDA;
+    return cudaStreamSynchronize(h->stream) == cudaSuccess ? PNSCAN_OK : PNSCAN_ERR_CUDA;
+}
+
 int mlp_set_params(mlp_handle* h, const float* params)
 {
     if (!h || !params) return PNSCAN_ERR_ARG;

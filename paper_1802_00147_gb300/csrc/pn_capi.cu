@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <thread>
@@ -322,7 +323,6 @@ int scan_params_default(scan_params* p)
     p->schedule = PNSCAN_SCHED_AUTO;
     p->use_graph = 1;
     p->queue_wait_limit_ms = 0;
-    p->debug_stall_group = -1;
     p->radiation_reaction = 0;
     p->rr_gauge_a = 4.0;
     p->rr_gauge_b = 5.0;
@@ -437,7 +437,13 @@ int scan_create(const scan_params* p, scan_handle** out)
     b.rmerge2 = p->r_merge > 0.0 ? p->r_merge * p->r_merge : 0.0;
     b.rescape2 = p->r_escape > 0.0 ? p->r_escape * p->r_escape : 0.0;
     b.wait_limit_ns = (unsigned long long)p->queue_wait_limit_ms * 1000000ull;   // 0: set per launch
-    b.stall_group = p->debug_stall_group;
+    // test switch of the bounded queue wait (documented with queue_wait_limit_ms)
+    b.stall_group = -1;
+    if (const char* env = std::getenv("PNSCAN_TEST_STALL_GROUP")) {
+        char* end = nullptr;
+        const long g = std::strtol(env, &end, 10);
+        if (end != env && *end == '\0' && g >= 0 && g < (1L << 30)) b.stall_group = (int)g;
+    }
     b.rr = p->radiation_reaction;
     b.rrc = make_rr_coef(p->rr_gauge_a, p->rr_gauge_b);
     h->sched = p->schedule == PNSCAN_SCHED_AUTO ? PNSCAN_SCHED_QUEUE : p->schedule;

@@ -4,11 +4,13 @@
 //
 // Who needs it: callers that cannot call cudaMalloc (or any allocating
 // routine) when they reduce a scan -- a framework whose caching allocator
-// already holds the device memory budget, a host process that forbids
-// run-time allocation in its latency-critical loop, or code that runs while
-// a stream is being captured into a CUDA graph, where allocation is not
-// permitted.  They pass their own input arrays and a host output struct;
-// the library touches no memory it did not reserve when it was loaded.
+// already holds the device memory budget, so that a further cudaMalloc
+// would fail or force the framework to release its cache, or a host process
+// that forbids run-time allocation after start-up in its latency-critical
+// loop.  They pass their own input arrays and a host output struct; the
+// library touches no device memory it did not reserve when it was loaded.
+// The call waits for its stream to finish (it copies the result into the
+// host struct).
 //
 // Scratch: g_scratch below, kNoallocBlocks + 1 partial records of 256 bytes
 // (2.1 MB), reserved on every GPU that loads the library, until the process

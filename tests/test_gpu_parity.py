@@ -13,15 +13,17 @@ What is compared, and why the tolerances are what they are:
     here: the oracle is re-run with one initial component moved by one ulp,
     which gives its own sensitivity s_i for each orbit.  The test asserts
       median(err) <= 3 median(s) and p99(err) <= 3 p99(s)  (no systematic term),
-      max(err)   <= max(1e-10, 3 max(s))                  (no outlier beyond it),
-      >= 99 % of orbits within 1e-10.
+      >= 99 % of orbits within 1e-10,
+    and, orbit by orbit, err_i <= max(1e-10, 3 s_i).
     Near-singular Newton steps amplify rounding by up to 1/det_min = 1e5, and
     orbits about to merge are strongly unstable, so s_i itself reaches a few
     1e-10 for a handful of orbits; for the rest, err is ~1e-12.
   * FLI: log10 of the distance of two trajectories 1e-9 apart, so a one-ulp
-    change moves it by ~1e-2 (up to ~1) after 1000 M.  Asserted: median and
-    max of |dFLI| within 3x the oracle's own one-ulp spread (plus 1e-3), and
-    the regular/chaotic class (FLI > 6) agrees for >= 99.5 % of the orbits.
+    change moves it by ~1e-2 (up to ~1) after 1000 M.  Asserted: the median
+    of |dFLI| within 3x the median one-ulp spread (plus 1e-3); orbit by
+    orbit, |dFLI_i| within 3x that orbit's spread over all 24 one-ulp moves
+    (each component up and down; see ulp_spreads) plus 1e-3; and the
+    regular/chaotic class (FLI > 6) agrees for >= 99.5 % of the orbits.
 """
 import numpy as np
 import pytest
@@ -88,26 +90,50 @@ def block_relerr(a, b):
     return w
 
 
+def ulp_spreads(run, y0, o, calibration):
+    """The oracle against itself with one initial component moved by one ulp,
+    up and down, for each of the 12 components (24 runs; `run(y1)` integrates
+    from y1).  Returns per-orbit maxima of the state, FLI and integral
+    differences over the `calibration` moves (components moved up), and the
+    FLI maximum over all 24 moves.
+
+    A single one-ulp move leaves most of a run's later rounding decisions
+    correlated with the unmoved run's, so a few moves underestimate how far a
+    program that rounds differently at every operation (FMA against separate
+    multiply and add) lands from the oracle.  Measured with the oracle itself
+    compiled with and without FMA contraction: over 3 moves up to 20 of 774
+    orbits' FLI differences exceed 3x the spread (ratio up to 9); over all 24
+    moves none do (ratio <= 2.1)."""
+    n = y0.shape[0]
+    s_state, s_fli, s_fli_all = np.zeros(n), np.zeros(n), np.zeros(n)
+    s_integ = np.zeros((n, 6))
+    for comp in range(12):
+        for up in (True, False):
+            y1 = y0.copy()
+            y1[:, comp] = np.nextafter(y1[:, comp], np.inf if up else -np.inf)
+            o1 = run(y1)
+            same = o1["status"] == o["status"]
+            dfli = np.where(same, np.abs(o1["fli"] - o["fli"]), 0.0)
+            s_fli_all = np.maximum(s_fli_all, dfli)
+            if up and comp in calibration:
+                s_state = np.maximum(s_state, np.where(same, block_relerr(o1["y"], o["y"]), 0.0))
+                s_fli = np.maximum(s_fli, dfli)
+                s_integ = np.maximum(s_integ, np.where(same[:, None],
+                                                       np.abs(o1["integrals"] - o["integrals"]), 0.0))
+    o["s_fli_all"] = s_fli_all
+    return s_state, s_fli, s_integ
+
+
 def oracle_sensitivity(cells, nsteps, h=1.0, **cfg):
-    """The oracle against itself with one initial component moved by one ulp
-    (largest over three components): per-orbit state and FLI spread."""
+    """The oracle's own per-orbit state and FLI spread under one-ulp moves of
+    the initial state (ulp_spreads): the state's over three components, or all
+    twelve with radiation reaction (there the reference integrals carry the
+    trajectory's sensitivity, for which three components can be 6x short)."""
     cfg = {ORC_KEYS.get(k, k): v for k, v in cfg.items()}
     o = orc_run(cells, nsteps, h, **cfg)
     y0 = oracle.setup_cells(cells[:, :9])
-    s_state = np.zeros(cells.shape[0])
-    s_fli = np.zeros(cells.shape[0])
-    s_integ = np.zeros((cells.shape[0], 6))
-    # with radiation reaction the reference integrals carry the trajectory's
-    # sensitivity, for which three components can be 6x short: all twelve
-    for comp in (range(12) if cfg.get("rr") else (0, 4, 6)):
-        y1 = y0.copy()
-        y1[:, comp] = np.nextafter(y1[:, comp], np.inf)
-        o1 = orc_run(cells, nsteps, h, y0=y1, **cfg)
-        same = o1["status"] == o["status"]
-        e = block_relerr(o1["y"], o["y"])
-        s_state = np.maximum(s_state, np.where(same, e, 0.0))
-        s_fli = np.maximum(s_fli, np.where(same, np.abs(o1["fli"] - o["fli"]), 0.0))
-        s_integ = np.maximum(s_integ, np.where(same[:, None], np.abs(o1["integrals"] - o["integrals"]), 0.0))
+    calibration = range(12) if cfg.get("rr") else (0, 4, 6)
+    s_state, s_fli, s_integ = ulp_spreads(lambda y1: orc_run(cells, nsteps, h, y0=y1, **cfg), y0, o, calibration)
     # the integrals' own spread: at rounding level for a conservative run,
     # where they are restored every step; with radiation reaction the
     # reference E and |J| are integrals along the trajectory (Sec. 3B) and
@@ -135,7 +161,10 @@ def assert_parity(g, o, s_state, s_fli, nsteps):
     if err.size:
         assert np.median(err) <= 3 * np.median(s) + floor, (np.median(err), np.median(s))
         assert np.quantile(err, 0.99) <= 3 * np.quantile(s, 0.99) + floor
-        assert err.max() <= max(STATE_TOL, 3 * s.max()), (err.max(), s.max())
+        # per orbit: within 1e-10, or within 3x that orbit's own one-ulp spread
+        bound = np.maximum(STATE_TOL, 3 * s)
+        bad = np.flatnonzero(err > bound)
+        assert bad.size == 0, ("state", bad.size, err[bad][:5], s[bad][:5])
         # >= 99 % within 1e-10, not counting orbits that the oracle itself
         # cannot reproduce to 1e-10 within a factor 3 under a one-ulp move
         assert np.mean((err <= STATE_TOL) | (s >= STATE_TOL / 3)) >= 0.99
@@ -152,7 +181,11 @@ def assert_parity(g, o, s_state, s_fli, nsteps):
         df = np.abs(g["fli"][done] - o["fli"][done])
         sf = s_fli[done]
         assert np.median(df) <= 3 * np.median(sf) + 1e-3, (np.median(df), np.median(sf))
-        assert df.max() <= 3 * sf.max() + 1e-3, (df.max(), sf.max())
+        # per orbit: within 3x that orbit's own FLI spread over all 24 one-ulp
+        # moves (+1e-3)
+        sfa = o["s_fli_all"][done] if "s_fli_all" in o else sf
+        bad = np.flatnonzero(df > 3 * sfa + 1e-3)
+        assert bad.size == 0, ("fli", bad.size, df[bad][:5], sf[bad][:5])
         agree = (g["fli"][done] > FLI_THRESH) == (o["fli"][done] > FLI_THRESH)
         assert agree.mean() >= 0.995
     return float(err.max()) if err.size else 0.0
@@ -291,17 +324,11 @@ def test_random_orientation_states_parity(pn, schedule):
     g.update(s.read_diag())
     s.close()
     o = oracle.scan(y0, beta, 1.0, 400, oracle.config(use_qm=1), kappa1=k1, kappa2=k2)
-    s_state = np.zeros(y0.shape[0])
-    s_fli = np.zeros(y0.shape[0])
     # every component moved by one ulp: in random orientations the spread over
     # all 12 is up to 3x the spread over (x, p_y, S1_x) that grid states need
-    for comp in range(12):
-        y1 = y0.copy()
-        y1[:, comp] = np.nextafter(y1[:, comp], np.inf)
-        o1 = oracle.scan(y1, beta, 1.0, 400, oracle.config(use_qm=1), kappa1=k1, kappa2=k2)
-        same = o1["status"] == o["status"]
-        s_state = np.maximum(s_state, np.where(same, block_relerr(o1["y"], o["y"]), 0.0))
-        s_fli = np.maximum(s_fli, np.where(same, np.abs(o1["fli"] - o["fli"]), 0.0))
+    s_state, s_fli, _ = ulp_spreads(
+        lambda y1: oracle.scan(y1, beta, 1.0, 400, oracle.config(use_qm=1), kappa1=k1, kappa2=k2),
+        y0, o, range(12))
     assert_parity(g, o, s_state, s_fli, 400)
 
 
@@ -434,17 +461,8 @@ def test_radiation_reaction_random_orientation_parity(pn):
     o = oracle.scan(y0, beta, 1.0, 400, cfg, kappa1=k1, kappa2=k2)
     counts = np.bincount(o["status"], minlength=6)
     assert counts[oracle.MERGED] > 0 and counts[oracle.ESCAPED] > 0 and counts[oracle.DONE] > 0
-    s_state = np.zeros(y0.shape[0])
-    s_fli = np.zeros(y0.shape[0])
-    s_int = np.zeros((y0.shape[0], 6))
-    for comp in range(12):
-        y1 = y0.copy()
-        y1[:, comp] = np.nextafter(y1[:, comp], np.inf)
-        o1 = oracle.scan(y1, beta, 1.0, 400, cfg, kappa1=k1, kappa2=k2)
-        same = o1["status"] == o["status"]
-        s_state = np.maximum(s_state, np.where(same, block_relerr(o1["y"], o["y"]), 0.0))
-        s_fli = np.maximum(s_fli, np.where(same, np.abs(o1["fli"] - o["fli"]), 0.0))
-        s_int = np.maximum(s_int, np.where(same[:, None], np.abs(o1["integrals"] - o["integrals"]), 0.0))
+    s_state, s_fli, s_int = ulp_spreads(lambda y1: oracle.scan(y1, beta, 1.0, 400, cfg, kappa1=k1, kappa2=k2),
+                                        y0, o, range(12))
     o["s_integrals"] = s_int
     o["integ_floor"] = 4 * 400 * 2.0 ** -52
     assert_parity(g, o, s_state, s_fli, 400)
@@ -585,14 +603,18 @@ def test_single_orbit_and_nonfinite_input(pn):
 
 
 def test_bounded_queue_wait_reports_an_error_and_the_device_stays_usable(pn):
-    """A work-queue task whose predecessor never reports (test hook: group 0
+    """A work-queue task whose predecessor never reports (PNSCAN_TEST_STALL_GROUP: group 0
     withholds its first chunk) waits at most queue_wait_limit_ms, sets the
     kernel's error flag and returns; the host reads PNSCAN_ERR_KERNEL and the
     next run on the same handle works."""
+    import os
     import time
     cells = W.uneven_batch(n=4096, seed=14)
-    s = pn.Scan(cells[:, W.BETA], schedule=2, chunk_steps=50, use_graph=0, queue_wait_limit_ms=300,
-                debug_stall_group=0)
+    os.environ["PNSCAN_TEST_STALL_GROUP"] = "0"
+    try:
+        s = pn.Scan(cells[:, W.BETA], schedule=2, chunk_steps=50, use_graph=0, queue_wait_limit_ms=300)
+    finally:
+        del os.environ["PNSCAN_TEST_STALL_GROUP"]
     s.setup(cells)
     t0 = time.perf_counter()
     s.run(150.0, 1.0)

@@ -127,6 +127,72 @@ def test_training_lowers_the_loss_for_every_member(pn):
     sur.close()
 
 
+def oracle_adam_run(p0, z, t, steps, lr, seed, member, bf16):
+    """The oracle's Adam training of one member on the rows the kernel draws
+    (mlp_oracle.batch_rows, SplitMix64 from its published definition)."""
+    grad = M.loss_and_grad_bf16 if bf16 else M.loss_and_grad
+    p, m, v = p0.copy(), np.zeros_like(p0), np.zeros_like(p0)
+    for step in range(1, steps + 1):
+        rows = M.batch_rows(seed, member, step, z.shape[0])
+        _, g = grad(p, z[rows], t[rows])
+        p, m, v = M.adam_step(p, g, m, v, step, lr)
+    return p, m, v
+
+
+BLOCKS = ((M.OFF_W1, M.OFF_B1), (M.OFF_B1, M.OFF_W2), (M.OFF_W2, M.OFF_B2), (M.OFF_B2, M.OFF_W3),
+          (M.OFF_W3, M.OFF_B3), (M.OFF_B3, M.N_PARAMS))
+
+
+@pytest.mark.parametrize("steps", [1, 5])
+def test_adam_steps_match_oracle(pn, steps):
+    """mlp_train's forward, backward and FP32 Adam update (one persistent
+    kernel) against mlp_oracle's loss_and_grad + adam_step on the same rows.
+
+    Tolerances.  Adam divides the first moment by the root of the second, so
+    a parameter's update is lr times a ratio that the BF16 rounding of the
+    gradient moves only through the gradients' direction: at step 1 it is
+    lr g / (|g| + eps) = +-lr.  Against the oracle that rounds the same
+    operands to BF16: every moment block within 2e-3 (m) and 4e-3 (v) in norm
+    (the gradient's 1e-3, doubled by v = g^2, and later steps evaluated at
+    slightly different parameters); >= 99 % of the parameters' updates
+    within 1e-3 lr per step, all within 2 lr per step (a gradient element
+    within rounding of zero may take the other sign).  Against the plain
+    FP64 oracle: moments within 4e-2 in norm, >= 90 % of the updates within
+    1e-2 lr per step.  A missing or mis-stepped bias correction moves every
+    update by >= 0.3 lr; eps inside the square root moves those of the
+    small gradients."""
+    import torch
+    rng = np.random.default_rng(8)
+    K, n, lr, seed = 2, 3000, 1e-3, 0x5EED1234ABCD
+    params = as_f32_params(rng, K, 0.3)
+    X = raw_inputs(rng, n).astype(np.float32)
+    t = (2.0 + rng.normal(size=n)).astype(np.float32)
+    z = M.normalise(X.astype(np.float64), CENTER, SCALE)
+    sur = pn.Surrogate(members=K, center=tuple(CENTER), scale=tuple(SCALE))
+    sur.set_params(torch.as_tensor(params, device="cuda"))
+    sur.train(torch.as_tensor(X, device="cuda"), torch.as_tensor(t, device="cuda"), steps=steps, lr=lr, seed=seed)
+    P = sur.get_params().cpu().numpy().astype(np.float64)
+    m_g, v_g = (a.cpu().numpy().astype(np.float64) for a in sur.get_moments())
+    sur.close()
+    for k in range(K):
+        p0 = params[k].astype(np.float64)
+        for bf16, mtol, vtol, frac, utol in ((True, 2e-3, 4e-3, 0.99, 1e-3), (False, 4e-2, 4e-2, 0.90, 1e-2)):
+            p_o, m_o, v_o = oracle_adam_run(p0, z, t.astype(np.float64), steps, lr, seed, k, bf16)
+            for lo, hi in BLOCKS:
+                assert np.linalg.norm(m_g[k, lo:hi] - m_o[lo:hi]) <= mtol * np.linalg.norm(m_o[lo:hi]), \
+                    ("m", bf16, lo, hi)
+                assert np.linalg.norm(v_g[k, lo:hi] - v_o[lo:hi]) <= vtol * np.linalg.norm(v_o[lo:hi]), \
+                    ("v", bf16, lo, hi)
+            # updates, against the FP32 rounding of the parameters themselves
+            du = np.abs((P[k] - p0) - (p_o - p0))
+            slack = 2.0 ** -23 * (np.abs(p0) + np.abs(P[k]))
+            within = du <= utol * lr * steps + slack
+            assert within.mean() >= frac, (bf16, within.mean(), np.sort(du)[-5:] / lr)
+            if bf16:
+                assert np.all(du <= 2 * lr * steps + slack), (np.max(du) / lr)
+                assert np.median(du) <= 1e-4 * lr * steps + np.median(slack), np.median(du) / lr
+
+
 @pytest.mark.parametrize("n", [0, 1, 255, 256, 1000, 70000])
 def test_selection_is_exact_and_ordered(pn, n):
     import torch

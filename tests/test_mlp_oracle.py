@@ -73,3 +73,42 @@ def test_training_lowers_the_loss():
     p0 = rand_params(rng, 0.2)
     p, losses = M.train(p0, z, t, 600, 128, 3e-3, rng)
     assert losses[-50:].mean() < 0.05 * losses[:10].mean()
+
+
+def test_adam_constant_gradient_moves_lr_per_step():
+    """Under a constant gradient the bias-corrected moments are exactly g and
+    g^2 at every step (Kingma & Ba 2015, Sec. 3), so t steps move each
+    parameter by t lr g / (|g| + eps): pins the step count in both bias
+    corrections."""
+    rng = np.random.default_rng(6)
+    p0 = rand_params(rng)
+    g = rng.normal(size=M.N_PARAMS)
+    p, m, v = p0.copy(), np.zeros_like(p0), np.zeros_like(p0)
+    for t in range(1, 6):
+        p, m, v = M.adam_step(p, g, m, v, t, 2e-3)
+        np.testing.assert_allclose(m, (1 - 0.9 ** t) * g, rtol=1e-13)
+        np.testing.assert_allclose(v, (1 - 0.999 ** t) * g * g, rtol=1e-12)
+    np.testing.assert_allclose(p0 - p, 5 * 2e-3 * g / (np.abs(g) + 1e-8), rtol=1e-10)
+
+
+def test_splitmix64_published_sequence():
+    """SplitMix64 from state 0 (Steele, Lea & Flood 2014; the reference C
+    implementation's generator): the first four outputs."""
+    x, out = 0, []
+    for _ in range(4):
+        out.append(M.splitmix64(x))
+        x = (x + M.GOLDEN_GAMMA) & M.MASK64
+    assert out == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F, 0xF88BB8A8724C81EC]
+
+
+def test_batch_rows_are_uniform_and_distinct_per_member_and_step():
+    n = 1000
+    rows = np.concatenate([M.batch_rows(99, k, t, n) for k in range(4) for t in range(1, 41)])
+    assert rows.min() >= 0 and rows.max() < n
+    # 20,480 draws over 10 bins of 100 rows: chi-square with 9 dof, p ~ 1e-4 at 33
+    counts = np.bincount(rows // 100, minlength=10)
+    chi2 = np.sum((counts - rows.size / 10) ** 2 / (rows.size / 10))
+    assert chi2 < 33.0, counts
+    a, b, c = M.batch_rows(99, 0, 1, n), M.batch_rows(99, 1, 1, n), M.batch_rows(99, 0, 2, n)
+    assert not np.array_equal(a, b) and not np.array_equal(a, c)
+    assert np.array_equal(a, M.batch_rows(99, 0, 1, n))

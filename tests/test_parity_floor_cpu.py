@@ -1,0 +1,79 @@
+"""The rounding floor the GPU parity tests assert against, checked on the CPU
+with two builds of the same oracle: the reference build rounds every + and *
+separately, the other contracts multiply-adds into FMAs, as the GPU kernels
+do.  The two are the same algorithm, so everything between them is rounding.
+
+Pinned here, on the small scan and on the uneven batch to t = 1000:
+  * statuses and stop times agree exactly;
+  * every orbit's state lies within max(1e-10, 3x) its one-ulp spread;
+  * every orbit's FLI lies within 3x its FLI spread over all 24 one-ulp
+    moves (each component up and down) plus 1e-3 -- the per-orbit FLI floor
+    of tests/test_gpu_parity.py -- while three moves alone are too few;
+  * the class (FLI > 6) agrees on every orbit.
+The FMA build needs FMA instructions: baseline on aarch64, -mfma on x86-64
+(skipped where the CPU lacks them)."""
+import os
+import platform
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import build as ob
+from paper_1802_00147_gb300 import workloads as W
+
+from test_gpu_parity import block_relerr, ulp_spreads
+
+
+def fma_flags():
+    m = platform.machine().lower()
+    if m in ("aarch64", "arm64"):
+        return ["-ffp-contract=fast"]
+    if m in ("x86_64", "amd64"):
+        try:
+            flags = open("/proc/cpuinfo").read()
+        except OSError:
+            return None
+        return ["-mfma", "-ffp-contract=fast"] if " fma " in flags else None
+    return None
+
+
+@pytest.fixture(scope="module")
+def fma_lib():
+    flags = fma_flags()
+    if flags is None:
+        pytest.skip("no FMA instructions on this CPU")
+    d = tempfile.mkdtemp()
+    path = ob.build_variant(os.path.join(d, "libpnoracle_fma.so"), flags)
+    return oracle.load_variant(path)
+
+
+def run(cells, nsteps, y0=None):
+    if y0 is None:
+        y0 = oracle.setup_cells(cells[:, :9])
+    return oracle.scan(y0, cells[:, W.BETA], 1.0, nsteps, oracle.config(),
+                       kappa1=cells[:, W.KAP1], kappa2=cells[:, W.KAP2])
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("which", ["small", "uneven"])
+def test_fma_rounding_lies_within_the_per_orbit_floor(fma_lib, which):
+    cells = W.small_scan(seed=1) if which == "small" else W.uneven_batch(n=1500, seed=3)
+    nsteps = 1000
+    o = run(cells, nsteps)
+    with oracle.using(fma_lib):
+        f = run(cells, nsteps)
+    y0 = oracle.setup_cells(cells[:, :9])
+    s_state, s_fli3, _ = ulp_spreads(lambda y1: run(cells, nsteps, y0=y1), y0, o, (0, 4, 6))
+    np.testing.assert_array_equal(f["status"], o["status"])
+    np.testing.assert_array_equal(f["t_stop"], o["t_stop"])
+    ok = o["status"] != oracle.NONFINITE
+    err = block_relerr(f["y"][ok], o["y"][ok])
+    assert np.all(err <= np.maximum(1e-10, 3 * s_state[ok]))
+    done = o["status"] == oracle.DONE
+    df = np.abs(f["fli"] - o["fli"])[done]
+    assert np.all(df <= 3 * o["s_fli_all"][done] + 1e-3), np.max(df / (o["s_fli_all"][done] + 1e-300))
+    # three moves underestimate the floor: some orbit exceeds 3x their spread
+    assert np.any(df > 3 * s_fli3[done] + 1e-3)
+    assert np.array_equal(f["fli"][done] > 6.0, o["fli"][done] > 6.0)

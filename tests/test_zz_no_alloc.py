@@ -1,7 +1,6 @@
 """scan_summary_noalloc: the scan reduction for callers that cannot allocate
-device memory when they reduce (a framework whose allocator holds the memory
-budget, a loop that must not allocate after start-up, work issued during
-stream capture).  Checked through the C ABI against scan_summary, the
+device memory when they reduce (a framework whose caching allocator holds the
+memory budget, a loop that must not allocate after start-up).  Checked through the C ABI against scan_summary, the
 handle's reduction, on the same device arrays, on two calls in a row (the
 second call reuses the library's fixed scratch that the first left behind).
 
