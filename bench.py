@@ -297,6 +297,58 @@ def aggregate_ranks(elapsed_s, orbit_steps, device=None):
     return float(mx.item()), float(sm.item())
 
 
+SUMMARY_SUM_KEYS = ("n_chaotic", "newton_iters", "n_skip", "orbit_steps", "n_final_fallback")
+SUMMARY_MAX_KEYS = ("max_dE", "max_dJ", "max_dJ_all", "max_dS")
+
+
+def aggregate_summary(summ, device=None):
+    """The scan counters of the whole job: counts summed over ranks (the
+    status histogram too), maximal drifts maximised, the FLI mean weighted by
+    each rank's finished orbits.  Each rank scans its own batch, so this is
+    the one exchange of the multi-GPU path, after the timed region."""
+    import torch
+    import torch.distributed as td
+    out = {k: summ[k] for k in SUMMARY_SUM_KEYS + SUMMARY_MAX_KEYS + ("status_count", "fli_mean")}
+    if not (td.is_available() and td.is_initialized()) or td.get_world_size() == 1:
+        return out
+    dev = device if device is not None else "cpu"
+    done = float(summ["status_count"][1])
+    sums = torch.tensor([float(summ[k]) for k in SUMMARY_SUM_KEYS] + [float(c) for c in summ["status_count"]]
+                        + [summ["fli_mean"] * done], dtype=torch.float64, device=dev)
+    maxs = torch.tensor([float(summ[k]) for k in SUMMARY_MAX_KEYS], dtype=torch.float64, device=dev)
+    td.all_reduce(sums, op=td.ReduceOp.SUM)
+    td.all_reduce(maxs, op=td.ReduceOp.MAX)
+    sums = sums.cpu().tolist()
+    maxs = maxs.cpu().tolist()
+    ns = len(SUMMARY_SUM_KEYS)
+    for i, k in enumerate(SUMMARY_SUM_KEYS):
+        out[k] = int(round(sums[i]))
+    out["status_count"] = [int(round(v)) for v in sums[ns:ns + 6]]
+    out["fli_mean"] = sums[ns + 6] / max(1, out["status_count"][1])
+    for i, k in enumerate(SUMMARY_MAX_KEYS):
+        out[k] = maxs[i]
+    return out
+
+
+def torchrun_argv(nproc, argv, port):
+    """The command that runs this script once per GPU of this node (one rank
+    per GPU, rendezvous on 127.0.0.1) with the same arguments."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=%d" % nproc,
+            "--master-addr=127.0.0.1", "--master-port=%d" % port, os.path.abspath(__file__)] + list(argv)
+
+
+def launch_check(gpus, env):
+    """None to run in this process, or the number of ranks to spawn.  Under
+    a launcher (WORLD_SIZE set) --gpus must match the world size."""
+    world = env.get("WORLD_SIZE")
+    if world is None:
+        return gpus if gpus > 1 else None
+    if int(world) != gpus:
+        raise SystemExit("bench.py: --gpus %d but WORLD_SIZE=%s: give --gpus the launcher's process count"
+                         % (gpus, world))
+    return None
+
+
 # --------------------------------------------------------- adaptive scan
 ADAPTIVE_N = 1024
 ADAPTIVE_T_END = 1.0e4
@@ -527,6 +579,7 @@ def run_ours(args, rank, world, local_rank):
     h2d = cells9.nbytes * world
     d2h = sum(a.nbytes for a in out.values()) * world
 
+    job_summary = aggregate_summary(summ, dev if dist else None)
     uneven = run_uneven() if (rank == 0 and args.adaptive) else None
     dissipative = run_dissipative() if (rank == 0 and args.adaptive) else None
     adaptive = None
@@ -580,9 +633,7 @@ def run_ours(args, rank, world, local_rank):
         "adaptive": adaptive,
         "uneven": uneven,
         "dissipative": dissipative,
-        "scan": {k: summ[k] for k in ("n_chaotic", "status_count", "max_dE", "max_dJ", "max_dJ_all",
-                                      "n_final_fallback", "max_dS", "fli_mean", "newton_iters",
-                                      "n_skip", "orbit_steps")},
+        "scan": job_summary,
     }
     print(json.dumps(line), flush=True)
     scan.close()
@@ -608,6 +659,14 @@ def main():
     ap.add_argument("--dissipative", action="store_true",
                     help="--profile runs with the 2.5PN radiation reaction")
     args = ap.parse_args()
+    spawn = launch_check(args.gpus, os.environ)
+    if spawn:
+        # one process per GPU: re-run this script under torch.distributed.run
+        import socket
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+        sys.exit(subprocess.call(torchrun_argv(spawn, sys.argv[1:], port)))
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))

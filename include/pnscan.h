@@ -97,7 +97,8 @@ typedef struct scan_params {
     double newton_tol;       /* Newton stop: |d alpha|, |d beta| <= tol (default 1e-10, Sec. 3A) */
     int newton_max;          /* Newton iteration cap (default 50) */
     double newton_det_min;   /* a step whose dual-scaling Jacobian has |det| <= det_min
-                                (|J11 J22| + |J12 J21|) restores E by scaling p alone
+                                (|J11 J22| + |J12 J21|) is corrected by the split scaling
+                                (newton_split_min), else restores E by scaling p alone
                                 (default 1e-5) */
     int newton_apply_small;  /* 1: apply a Newton step, then stop if it was within newton_tol (default);
                                 0: stop before applying a step already within newton_tol (the rule
@@ -148,6 +149,22 @@ typedef struct scan_params {
     double rr_gauge_b;       /* a = (8/5) eta u^3 [A (n.p) n - B p], A = 3 (1 + b) p^2 +
                                 (23 + 6 a - 9 b) u / 3 - 5 b (n.p)^2, B = (2 + a) p^2 + (2 - a) u
                                 - 3 (1 + a) (n.p)^2; (4, 5): harmonic gauge (default) */
+    double newton_split_min; /* where the dual scaling is singular (newton_det_min), restore E and
+                                |J| by scaling p's tangential and radial parts, p = a p_t + g p_r
+                                (r kept; L = a L*, so the Jacobian is triangular), if
+                                |p_r.dH/dp| > split_min (|p_t.dH/dp| + |p_r.dH/dp|) and
+                                |L*.J|/|J| > split_min |L*| (near circular orbits it is as
+                                ill-conditioned as the dual scaling).  In [0, 1); 0: never
+                                (default 1e-3).  Not in the paper, which does not treat the
+                                singular case of Eqs. 11-13 */
+    double newton_cond_switch; /* where the dual scaling's relative determinant at (1, 1) is at most
+                                this, the split scaling is used instead if it is better conditioned
+                                (|p_r.dH/dp| / (|p_t.dH/dp| + |p_r.dH/dp|) larger, and above
+                                newton_split_min).  Rounding in Eq. 13's residuals reaches the state
+                                amplified by the inverse conditioning, and kicks that differ between
+                                the two FLI trajectories (Sec. 3B) grow their separation by
+                                themselves.  In [0, 1); 0: the dual scaling down to newton_det_min
+                                (default 1e-2) */
 } scan_params;
 
 typedef struct scan_handle scan_handle;   /* opaque, library-owned */
@@ -158,14 +175,16 @@ typedef struct scan_summary_t {
     int64_t n_chaotic;          /* orbits DONE or FLI_SATURATED with FLI > fli_thresh */
     int64_t status_count[6];    /* orbits per PNSCAN_ORBIT_* value */
     int64_t newton_iters;       /* Newton iterations, all orbits, both trajectories */
-    int64_t n_skip;             /* corrections whose scaling was skipped */
+    int64_t n_skip;             /* corrections whose dual scaling was singular or did not converge */
     int64_t orbit_steps;        /* sum over orbits of steps taken since the initial state */
     double max_dE;              /* max |E - E0| / |E0| over DONE orbits (E0: the reference at t
                                    with radiation_reaction) */
-    double max_dJ;              /* max ||J| - J0| / J0 over DONE orbits whose last step was dual-scaled */
+    double max_dJ;              /* max ||J| - J0| / J0 over DONE orbits whose last step restored |J|
+                                   (dual or split scaling) */
     double max_dJ_all;          /* the same over all DONE orbits */
-    int64_t n_final_fallback;   /* DONE orbits whose last step fell where the dual scaling is
-                                   singular (E restored by velocity scaling, |J| not) */
+    int64_t n_final_fallback;   /* DONE orbits whose last step fell where both the dual and the
+                                   split scaling are singular (E restored by velocity scaling,
+                                   |J| not) */
     double max_dS;              /* max ||S_i| - |S_i|0| / |S_i|0 over DONE orbits */
     double fli_max;             /* max(FLI, 0) over DONE orbits */
     double fli_mean;            /* mean FLI over DONE orbits */
@@ -221,8 +240,9 @@ int scan_read(scan_handle *h, double *states, double *integrals, double *fli,
  * FLI trajectory, Sec. 3B), newton_iters n (Newton iterations of Eq. 13, both
  * trajectories), n_skip n (steps of either trajectory whose dual scaling was
  * singular or did not converge), last_kind n (correction of the main
- * trajectory's last step: 0 dual scaling, 2 velocity scaling of p alone as
- * in the method Sec. 1 cites, 1 none).  Any pointer may be NULL.
+ * trajectory's last step: 0 dual scaling, 3 split scaling of p's tangential
+ * and radial parts (newton_split_min), 2 velocity scaling of p alone as in
+ * the method Sec. 1 cites, 1 none).  Any pointer may be NULL.
  * Errors: STATE, CUDA, KERNEL, TIMEOUT. */
 int scan_read_diag(scan_handle *h, double *shadow, int32_t *newton_iters, int32_t *n_skip,
                    int32_t *last_kind);
@@ -307,7 +327,7 @@ int scan_fp64_peak(scan_handle *h, int iters, double *tflops);
  *   n              number of orbits, 0 <= n <= PNSCAN_NOALLOC_MAX_ORBITS (else ARG)
  *   status [n], fli [n], integrals [n x 6] (E0, E, J0, |J|, |S1|, |S2|): required if n > 0
  *   spin_ref [n x 2] (|S1|0, |S2|0), newton_iters [n], n_skip [n],
- *   last_kind [n] (NULL: every last step counts as dual-scaled),
+ *   last_kind [n] (NULL: every last step counts as restoring |J|),
  *   t_stop [n] with h_step > 0 (orbit_steps = sum round(t_stop / h_step)): each nullable;
  *   a NULL input leaves its fields 0.
  *   fli_thresh     FLI above this counts as chaotic
@@ -397,6 +417,29 @@ int adaptive_select(const float *mean, const float *spread, int64_t n, float thr
                     void *cuda_stream);
 int adaptive_merge(const float *mean, int64_t n, float thr, const int32_t *idx, int64_t count,
                    const double *fli_sel, const int32_t *status_sel, int8_t *cls, void *cuda_stream);
+/* Adaptive scan (not in the paper).  The surrogate inputs X [n][4] from any
+ * four fields of cells [n][9]: X[i][k] = (float) cells[i][fields[k]], fields
+ * a HOST array of 4 indices in 0..8 (x0, pfac, theta1, phi1, theta2, phi2,
+ * beta, chi1, chi2), e.g. (2, 4, 0, 6) for the (theta1, theta2) plane of
+ * Sec. 3C, Fig. 7.  Device pointers otherwise; asynchronous on cuda_stream.
+ * Errors: ARG (n < 0, a field out of range, NULL arrays with n > 0), CUDA. */
+int adaptive_features_fields(const double *cells, int64_t n, const int32_t *fields, float *X,
+                             void *cuda_stream);
+/* Adaptive scan without a learned map (not in the paper; the comparison
+ * method of the surrogate): a row-major n1 x n2 grid is estimated from its
+ * coarse grid of every stride-th cell in both directions, integrated
+ * beforehand: nodes (a, b) at cells (a stride, b stride), a < (n1-1)/stride+1,
+ * b < (n2-1)/stride+1, with FLIs fli_nodes and statuses status_nodes
+ * (row-major, device).  mean [n1 x n2] gets the FLI interpolated bilinearly
+ * between the four surrounding nodes (clamped beyond the last node; a node
+ * that did not finish or saturate counts as FLI 0, not chaotic), spread the
+ * max - min of those four node values, as uncertainty; a cell that is a node
+ * gets the node's FLI and spread 0.  Both feed adaptive_select and
+ * adaptive_merge like the surrogate's mean and spread.  Asynchronous on
+ * cuda_stream.  Errors: ARG (negative sizes, stride < 1, n1 or n2 > 2^20,
+ * n1 n2 > 2^32, NULL arrays with a non-empty grid), CUDA. */
+int adaptive_interp_grid(const double *fli_nodes, const int32_t *status_nodes, int64_t n1, int64_t n2,
+                         int32_t stride, float *mean, float *spread, void *cuda_stream);
 
 /* Library utility (not in the paper): free the handle's device buffers and
  * the handle (NULL is a no-op; no error is reported). */

@@ -14,6 +14,12 @@ from .build import build as _build
 
 _lib = None
 
+# conditioning guard of the split scaling (orc_config.split_min), and the
+# dual scaling's conditioning below which the better-conditioned of the two
+# is used (orc_config.cond_switch)
+SPLIT_MIN = 1e-3
+COND_SWITCH = 1e-2
+
 # per-orbit status numbering of the oracle
 RUNNING, DONE, MERGED, ESCAPED, FLI_SATURATED, NONFINITE = range(6)
 
@@ -27,6 +33,7 @@ class Config(_ct.Structure):
         ("r_merge", _ct.c_double), ("r_escape", _ct.c_double), ("rk_order", _ct.c_int),
         ("newton_apply_small", _ct.c_int),
         ("rr", _ct.c_int), ("rr_gauge_a", _ct.c_double), ("rr_gauge_b", _ct.c_double),
+        ("split_min", _ct.c_double), ("cond_switch", _ct.c_double),
     ]
 
 
@@ -41,10 +48,10 @@ class Sys(_ct.Structure):
 def config(pn_order=2, use_so=1, use_ss=1, use_qm=0, correct=1, newton_tol=1e-10,
            newton_max=50, det_min=1e-5, fli_d0=1e-9, fli_renorm=100, fli_cap=0.0,
            r_merge=6.0, r_escape=1e3, rk_order=4, newton_apply_small=1, rr=0,
-           rr_gauge_a=4.0, rr_gauge_b=5.0):
+           rr_gauge_a=4.0, rr_gauge_b=5.0, split_min=SPLIT_MIN, cond_switch=COND_SWITCH):
     return Config(pn_order, use_so, use_ss, use_qm, correct, newton_tol, newton_max,
                   det_min, fli_d0, fli_renorm, fli_cap, r_merge, r_escape, rk_order, newton_apply_small,
-                  rr, rr_gauge_a, rr_gauge_b)
+                  rr, rr_gauge_a, rr_gauge_b, split_min, cond_switch)
 
 
 def lib():
@@ -95,7 +102,7 @@ def _declare(L):
     L.orc_waveform.argtypes = [P(Sys), dp, d, dp, dp, dp]
     L.orc_newton_trace.argtypes = [P(Sys), dp, dp, i, dp, dp]
     L.orc_newton_trace.restype = i
-    L.orc_correct_rule.argtypes = [P(Sys), dp, dp, d, i, d, i, i, P(i), dp]
+    L.orc_correct_rule.argtypes = [P(Sys), dp, dp, d, i, d, d, d, i, i, P(i), dp]
     L.orc_correct_rule.restype = i
     L.orc_setup_cell.argtypes = [dp, dp]
     L.orc_scan.argtypes = [i64, dp, dp, dp, dp, P(Config), d, i64, dp, dp, dp, dp,
@@ -206,16 +213,25 @@ def newton_trace(s, y, ref, kmax=8):
 MODE_DUAL, MODE_SPINS, MODE_VELOCITY = 1, 2, 3
 
 
-def correct(s, y, ref, newton_tol=1e-10, newton_max=50, det_min=1e-5, mode=MODE_DUAL, apply_small=1):
+CORR_DUAL, CORR_NONE, CORR_VELOCITY, CORR_SPLIT = 0, 1, 2, 3
+
+
+def correct(s, y, ref, newton_tol=1e-10, newton_max=50, det_min=1e-5, mode=MODE_DUAL, apply_small=1,
+            split_min=None, cond_switch=None):
     """Returns (y_corrected, code, iters, (alpha, beta)); code 0 dual scaling,
-    2 velocity scaling (singular dual scaling, or mode MODE_VELOCITY), 1 nothing
-    applied beyond the spin lengths."""
+    3 split scaling (singular dual scaling), 2 velocity scaling (both
+    singular, or mode MODE_VELOCITY), 1 nothing applied beyond the spin
+    lengths.  For code 3 (alpha, beta) are the factors (a, g) of the
+    tangential and radial parts of p."""
     y = _vec(y).copy()
     ref = _vec(ref)
     it = _ct.c_int(0)
     ab = _np.zeros(2)
+    split_min = SPLIT_MIN if split_min is None else split_min
+    cond_switch = COND_SWITCH if cond_switch is None else cond_switch
     code = lib().orc_correct_rule(_ct.byref(s), _dp(y), _dp(ref), newton_tol, newton_max,
-                                  det_min, int(apply_small), int(mode), _ct.byref(it), _dp(ab))
+                                  det_min, float(split_min), float(cond_switch), int(apply_small), int(mode),
+                                  _ct.byref(it), _dp(ab))
     return y, code, it.value, (ab[0], ab[1])
 
 

@@ -423,7 +423,8 @@ int orc_correct(const orc_sys *s, double y[12], const double ref[4],
                 double newton_tol, int newton_max, double det_min,
                 int *iters, double alpha_beta[2])
 {
-    return orc_correct_rule(s, y, ref, newton_tol, newton_max, det_min, 1, ORC_MODE_DUAL, iters, alpha_beta);
+    return orc_correct_rule(s, y, ref, newton_tol, newton_max, det_min, 0.0, 0.0, 1, ORC_MODE_DUAL, iters,
+                            alpha_beta);
 }
 
 /* One Newton step of Eq. 13 at (alpha, beta): F = (H(beta r*, alpha p*, S)
@@ -467,6 +468,42 @@ static int dual_newton_step(const orc_sys *s, const double y[12], const double r
     return 0;
 }
 
+/* One Newton step of the split scaling at (a, g): p = a p_t + g p_r, r = r*,
+ * with p_r = (n.p*) n and p_t = p* - p_r the radial and tangential parts of
+ * p* (n the unit vector along r*).  Since r* x p_r = 0, L = a (r* x p_t) =
+ * a L*, so |J|
+ * depends on a alone and the Jacobian of F = (H - E0, |J| - J0) in (a, g),
+ *   [ p_t.dH/dp   p_r.dH/dp ]
+ *   [ L*.J/|J|    0         ],
+ * is triangular.  It is singular where the radial part vanishes (turning
+ * points, circular orbits) or L*.J = 0; -1 is returned there, below det_min
+ * of the row or column it is compared with, or if not finite. */
+static int split_newton_step(const orc_sys *s, const double y[12], const double ref[4],
+                             const double pt[3], const double pr[3], double a, double g,
+                             double split_min, double *da, double *dg)
+{
+    double yb[12], grad[12], J[3], L[3], Ls[3], Jn, F1, F2, A, B, C;
+    int i;
+    memcpy(yb, y, sizeof(yb));
+    for (i = 0; i < 3; i++) yb[3 + i] = a * pt[i] + g * pr[i];
+    F1 = orc_hamiltonian(s, yb) - ref[0];
+    cross3(yb, yb + 3, L);
+    for (i = 0; i < 3; i++) J[i] = L[i] + yb[6 + i] + yb[9 + i];
+    Jn = norm3(J);
+    F2 = Jn - ref[1];
+    orc_gradient(s, yb, grad);
+    A = dot3(grad + 3, pt);          /* dF1/da */
+    B = dot3(grad + 3, pr);          /* dF1/dg */
+    cross3(yb, pt, Ls);              /* dL/da = r* x p_t = L* */
+    C = dot3(J, Ls) / Jn;            /* dF2/da; dF2/dg = 0 */
+    if (!(fabs(B) > split_min * (fabs(A) + fabs(B))) || !(fabs(C) > split_min * norm3(Ls)) ||
+        !isfinite(A) || !isfinite(B) || !isfinite(C))
+        return -1;
+    *da = F2 / C;
+    *dg = (F1 - A * (*da)) / B;
+    return 0;
+}
+
 int orc_newton_trace(const orc_sys *s, const double y[12], const double ref[4], int kmax,
                      double *alpha, double *beta)
 {
@@ -482,13 +519,43 @@ int orc_newton_trace(const orc_sys *s, const double y[12], const double ref[4], 
     return k;
 }
 
+/* Conditioning of the two scalings at the unscaled point y = (r*, p*, S):
+ * the dual scaling's relative determinant |A - B| / (|A| + |B|), with
+ * A = p*.dH/dp and B = r*.dH/dr (its two |J| derivatives are equal there);
+ * and the split scaling's |p_r.dH/dp| / (|p_t.dH/dp| + |p_r.dH/dp|), or 0
+ * where its |J| row is degenerate (|L*.J|/|J| <= split_min |L*|). */
+static void conditioning(const orc_sys *s, const double y[12], double split_min, double *c_dual,
+                         double *c_split)
+{
+    double g[12], pr[3], pt[3], L[3], J[3], A, B, As, Bs, rn, np_;
+    int i;
+    orc_gradient(s, y, g);
+    A = dot3(g + 3, y + 3);
+    B = dot3(g, y);
+    *c_dual = fabs(A - B) / (fabs(A) + fabs(B));
+    rn = norm3(y);
+    np_ = dot3(y, y + 3) / rn;
+    for (i = 0; i < 3; i++) {
+        pr[i] = np_ * (y[i] / rn);
+        pt[i] = y[3 + i] - pr[i];
+    }
+    As = dot3(g + 3, pt);
+    Bs = dot3(g + 3, pr);
+    cross3(y, y + 3, L);
+    for (i = 0; i < 3; i++) J[i] = L[i] + y[6 + i] + y[9 + i];
+    *c_split = fabs(Bs) / (fabs(As) + fabs(Bs));
+    if (!(fabs(dot3(J, L)) / norm3(J) > split_min * norm3(L))) *c_split = 0.0;
+    if (!isfinite(*c_dual)) *c_dual = 0.0;
+    if (!isfinite(*c_split)) *c_split = 0.0;
+}
+
 int orc_correct_rule(const orc_sys *s, double y[12], const double ref[4],
-                     double newton_tol, int newton_max, double det_min, int apply_small, int mode,
-                     int *iters, double alpha_beta[2])
+                     double newton_tol, int newton_max, double det_min, double split_min,
+                     double cond_switch, int apply_small, int mode, int *iters, double alpha_beta[2])
 {
     double rs[3], ps[3], yb[12];
     double alpha = 1.0, beta = 1.0;
-    int it = 0, i, converged = 0;
+    int it = 0, i, converged = 0, prefer_split = 0;
 
     /* Eq. 10: restore both spin lengths (skipped for a zero-length spin). */
     for (i = 0; i < 2; i++) {
@@ -519,7 +586,17 @@ int orc_correct_rule(const orc_sys *s, double y[12], const double ref[4],
     memcpy(yb, y, sizeof(yb));
     /* mode ORC_MODE_VELOCITY (ablation): no dual scaling, straight to the
      * velocity scaling below */
-    for (it = 1; mode == ORC_MODE_DUAL && it <= newton_max; it++) {
+    /* In the dual scaling's ill-conditioned band (relative determinant at
+     * most cond_switch) the split scaling is used instead where it is better
+     * conditioned: rounding in F reaches the correction amplified by the
+     * inverse conditioning, and kicks that differ between the two FLI
+     * trajectories would masquerade as divergence. */
+    if (mode == ORC_MODE_DUAL && cond_switch > 0.0 && split_min > 0.0) {
+        double cd, cs;
+        conditioning(s, y, split_min, &cd, &cs);
+        if (cd <= cond_switch && cs > cd && cs > split_min) prefer_split = 1;
+    }
+    for (it = 1; mode == ORC_MODE_DUAL && !prefer_split && it <= newton_max; it++) {
         double da, db;
         if (dual_newton_step(s, y, ref, alpha, beta, det_min, &da, &db)) break;
         /* stopping rule: apply the step and then test it (default), or stop
@@ -536,7 +613,7 @@ int orc_correct_rule(const orc_sys *s, double y[12], const double ref[4],
             break;
         }
     }
-    if (mode != ORC_MODE_DUAL) it = 0;
+    if (mode != ORC_MODE_DUAL || prefer_split) it = 0;
     if (it > newton_max) it = newton_max;
     if (converged) {
         for (i = 0; i < 3; i++) {
@@ -550,10 +627,49 @@ int orc_correct_rule(const orc_sys *s, double y[12], const double ref[4],
         }
         return ORC_CORR_OK;
     }
-    /* Singular (or non-converged) dual scaling: restore the energy alone by
+    /* Singular (or non-converged) dual scaling: both integrals by the split
+     * scaling p = a p_t + g p_r (r* kept), 2x2 Newton on (a, g) from (1, 1)
+     * with the same stopping rule.  The dual scaling is singular where
+     * p*.dH/dp = r*.dH/dr (for a Kepler ellipse at r = a, where
+     * |p_r| / |p| = e), away from the turning points where this one is. */
+    if (mode == ORC_MODE_DUAL && split_min > 0.0) {
+        double pt[3], pr[3], rn = norm3(rs), np_ = dot3(rs, ps) / rn, a = 1.0, g = 1.0;
+        int k, ok = 0;
+        for (i = 0; i < 3; i++) {
+            pr[i] = np_ * (rs[i] / rn);
+            pt[i] = ps[i] - pr[i];
+        }
+        for (k = 1; k <= newton_max; k++) {
+            double da, dg;
+            if (split_newton_step(s, y, ref, pt, pr, a, g, split_min, &da, &dg)) break;
+            if (!apply_small && fabs(da) <= newton_tol && fabs(dg) <= newton_tol) {
+                ok = 1;
+                break;
+            }
+            a = a - da;
+            g = g - dg;
+            if (!isfinite(a) || !isfinite(g)) break;
+            if (fabs(da) <= newton_tol && fabs(dg) <= newton_tol) {
+                ok = 1;
+                break;
+            }
+        }
+        if (k > newton_max) k = newton_max;
+        if (ok) {
+            for (i = 0; i < 3; i++) y[3 + i] = a * pt[i] + g * pr[i];
+            if (iters) *iters = it + k;
+            if (alpha_beta) {
+                alpha_beta[0] = a;
+                alpha_beta[1] = g;
+            }
+            return ORC_CORR_SPLIT;
+        }
+        it += k;
+    }
+    /* Both singular (or non-converged): restore the energy alone by
      * velocity scaling, p = a p*, H(r*, a p*, S) = E0, Newton in a from 1
      * (the momentum-scaling correction of Sec. 1, Wu et al. 2007).  |J| is
-     * left to the next step's dual scaling. */
+     * left to the next step. */
     {
         double a = 1.0, g2[12];
         int k, ok = 0;
@@ -678,14 +794,14 @@ static void integrate_one(const orc_config *cfg, const orc_sys *s, const double 
         step(cfg, s, y, ref, h);
         if (cfg->correct) {
             last_kind = orc_correct_rule(s, y, ref, cfg->newton_tol, cfg->newton_max, cfg->det_min,
-                                         cfg->newton_apply_small, cfg->correct, &it, 0);
+                                         cfg->split_min, cfg->cond_switch, cfg->newton_apply_small, cfg->correct, &it, 0);
             if (last_kind != ORC_CORR_OK) skips++;
             iters += it;
         }
         step(cfg, s, ys, refs, h);
         if (cfg->correct) {
             if (orc_correct_rule(s, ys, refs, cfg->newton_tol, cfg->newton_max, cfg->det_min,
-                                 cfg->newton_apply_small, cfg->correct, &it, 0))
+                                 cfg->split_min, cfg->cond_switch, cfg->newton_apply_small, cfg->correct, &it, 0))
                 skips++;
             iters += it;
         }
@@ -767,7 +883,7 @@ int orc_trace(const double y0[12], double beta, double kappa1, double kappa2,
         step(cfg, &s, y, ref, h);
         if (cfg->correct)
             orc_correct_rule(&s, y, ref, cfg->newton_tol, cfg->newton_max, cfg->det_min,
-                             cfg->newton_apply_small, cfg->correct, &it, 0);
+                             cfg->split_min, cfg->cond_switch, cfg->newton_apply_small, cfg->correct, &it, 0);
         if (k % every == 0) {
             memcpy(trace + 12 * m, y, sizeof(y));
             m++;

@@ -52,6 +52,11 @@ typedef struct {
     int rr;               /* 1: add the 2.5PN radiation reaction a_2.5PN to dp/dt (Eq. 6) and
                              correct toward integral-invariant reference values (Sec. 3B) */
     double rr_gauge_a, rr_gauge_b; /* gauge constants of orc_rr_accel (harmonic gauge: 4, 5) */
+    double split_min;     /* use the split scaling only where |p_r.dH/dp| > split_min
+                             (|p_t.dH/dp| + |p_r.dH/dp|) (<= 0: never) */
+    double cond_switch;   /* where the dual scaling's relative determinant at (1, 1) is at most
+                             this, the split scaling is used instead if it is better conditioned
+                             (<= 0: only where the dual scaling is singular) */
 } orc_config;
 
 /* Per-orbit final status (oracle's own numbering). */
@@ -61,8 +66,10 @@ enum {
 };
 
 /* Correction outcome: dual scaling applied; singular dual scaling replaced
- * by velocity scaling of p alone; nothing converged (r*, p* kept). */
-enum { ORC_CORR_OK = 0, ORC_CORR_SKIPPED = 1, ORC_CORR_VELOCITY = 2 };
+ * by velocity scaling of p alone; nothing converged (r*, p* kept); singular
+ * dual scaling replaced by the split scaling of p's radial and tangential
+ * parts (both integrals restored). */
+enum { ORC_CORR_OK = 0, ORC_CORR_SKIPPED = 1, ORC_CORR_VELOCITY = 2, ORC_CORR_SPLIT = 3 };
 
 void orc_sys_init(orc_sys *s, double beta, double kappa1, double kappa2,
                   int pn_order, int use_so, int use_ss, int use_qm);
@@ -109,11 +116,15 @@ void orc_rk_step_rr(const orc_sys *s, double ga, double gb, int rk_order, double
 void orc_integrals(const orc_sys *s, const double y[12], double out[7]);
 
 /* Manifold correction (Eqs. 10-13) toward ref = (E0, J0, |S1|0, |S2|0), in
- * place.  Returns ORC_CORR_OK, ORC_CORR_VELOCITY (the dual scaling was
- * singular, |det| <= det_min (|J11 J22| + |J12 J21|), or did not converge:
- * p alone was scaled to restore E) or ORC_CORR_SKIPPED; *iters gets the
- * number of Newton iterations of both solves; alpha_beta (nullable) gets the
- * scale factors applied. */
+ * place.  Returns ORC_CORR_OK (dual scaling applied), or, where the dual
+ * scaling was singular (|det| <= det_min (|J11 J22| + |J12 J21|)) or did not
+ * converge, or where its relative determinant at (1, 1) is at most
+ * cond_switch and the split scaling is better conditioned: ORC_CORR_SPLIT
+ * (p = a p_t + g p_r with r kept restored E and |J|), ORC_CORR_VELOCITY
+ * (that too was singular: p alone was scaled to restore E) or
+ * ORC_CORR_SKIPPED.  *iters gets the number of Newton
+ * iterations of all solves; alpha_beta (nullable) gets the scale factors of
+ * p and r applied (for the split scaling: a and g). */
 int orc_correct(const orc_sys *s, double y[12], const double ref[4],
                 double newton_tol, int newton_max, double det_min,
                 int *iters, double alpha_beta[2]);
@@ -121,8 +132,8 @@ int orc_correct(const orc_sys *s, double y[12], const double ref[4],
  * correction mode (orc_config.correct: ORC_MODE_*) as parameters. */
 enum { ORC_MODE_DUAL = 1, ORC_MODE_SPINS = 2, ORC_MODE_VELOCITY = 3 };
 int orc_correct_rule(const orc_sys *s, double y[12], const double ref[4],
-                     double newton_tol, int newton_max, double det_min, int apply_small, int mode,
-                     int *iters, double alpha_beta[2]);
+                     double newton_tol, int newton_max, double det_min, double split_min,
+                     double cond_switch, int apply_small, int mode, int *iters, double alpha_beta[2]);
 
 /* Gravitational-wave polarisations (Eq. 14) from the mass quadrupole
  * field of the relative orbit, observer at distance R along N = P x Q:

@@ -56,6 +56,7 @@ class ScanParams(_ct.Structure):
         ("queue_wait_limit_ms", _ct.c_int),
         ("alloc_fn", _ALLOC_FN), ("free_fn", _FREE_FN), ("alloc_ctx", _ct.c_void_p),
         ("radiation_reaction", _ct.c_int), ("rr_gauge_a", _ct.c_double), ("rr_gauge_b", _ct.c_double),
+        ("newton_split_min", _ct.c_double), ("newton_cond_switch", _ct.c_double),
     ]
 
 
@@ -121,6 +122,10 @@ def lib():
         L.mlp_destroy.restype = None
         L.adaptive_features.argtypes = [vp, i64, vp, vp]
         L.adaptive_features.restype = i
+        L.adaptive_features_fields.argtypes = [vp, i64, P(_ct.c_int32), vp, vp]
+        L.adaptive_features_fields.restype = i
+        L.adaptive_interp_grid.argtypes = [vp, vp, i64, i64, _ct.c_int32, vp, vp, vp]
+        L.adaptive_interp_grid.restype = i
         L.adaptive_select_workspace.argtypes = [i64]
         L.adaptive_select_workspace.restype = _ct.c_size_t
         L.adaptive_select.argtypes = [vp, vp, i64, f, f, f, vp, vp, vp, P(i64), vp, vp]
@@ -483,6 +488,33 @@ def adaptive_features(cells, stream=None):
     st = (stream or torch.cuda.current_stream()).cuda_stream
     _check(lib().adaptive_features(_ptr(cells), n, _ptr(X), st), "adaptive_features")
     return X
+
+
+def adaptive_features_fields(cells, fields, stream=None):
+    """Surrogate inputs from four chosen cell fields (indices 0..8) of cells
+    (n x 9 float64, CUDA), as float32 (n x 4)."""
+    import torch
+    cells = cells.contiguous()
+    n = int(cells.shape[0])
+    X = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    f = (_ct.c_int32 * 4)(*[int(k) for k in fields])
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(lib().adaptive_features_fields(_ptr(cells), n, f, _ptr(X), st), "adaptive_features_fields")
+    return X
+
+
+def adaptive_interp_grid(fli_nodes, status_nodes, n1, n2, stride, stream=None):
+    """Mean and spread (float32, n1*n2, CUDA) of a row-major n1 x n2 grid
+    interpolated from its integrated coarse grid of every stride-th cell."""
+    import torch
+    fli_nodes = fli_nodes.contiguous()
+    status_nodes = status_nodes.contiguous()
+    mean = torch.empty(n1 * n2, dtype=torch.float32, device="cuda")
+    spread = torch.empty(n1 * n2, dtype=torch.float32, device="cuda")
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(lib().adaptive_interp_grid(_ptr(fli_nodes), _ptr(status_nodes), int(n1), int(n2), int(stride),
+                                      _ptr(mean), _ptr(spread), st), "adaptive_interp_grid")
+    return mean, spread
 
 
 def adaptive_select(mean, spread, thr=6.0, band=1.0, spread_max=0.5, cells=None, stream=None):

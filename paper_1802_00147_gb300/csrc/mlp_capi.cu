@@ -168,6 +168,29 @@ int adaptive_features(const double* cells, int64_t n, float* X, void* cuda_strea
     return launch_features(cells, n, X, (cudaStream_t)cuda_stream) == cudaSuccess ? PNSCAN_OK : PNSCAN_ERR_CUDA;
 }
 
+int adaptive_features_fields(const double* cells, int64_t n, const int32_t* fields, float* X, void* cuda_stream)
+{
+    if (n < 0 || !fields || (n > 0 && (!cells || !X))) return PNSCAN_ERR_ARG;
+    FieldSel f{};
+    for (int k = 0; k < NIN; k++) {
+        if (fields[k] < 0 || fields[k] > 8) return PNSCAN_ERR_ARG;
+        f.field[k] = fields[k];
+    }
+    return launch_features_fields(cells, n, f, X, (cudaStream_t)cuda_stream) == cudaSuccess ? PNSCAN_OK
+                                                                                            : PNSCAN_ERR_CUDA;
+}
+
+int adaptive_interp_grid(const double* fli_nodes, const int32_t* status_nodes, int64_t n1, int64_t n2,
+                         int32_t stride, float* mean, float* spread, void* cuda_stream)
+{
+    if (n1 < 0 || n2 < 0 || stride < 1) return PNSCAN_ERR_ARG;
+    if (n1 > 0 && n2 > 0 && (!fli_nodes || !status_nodes || !mean || !spread)) return PNSCAN_ERR_ARG;
+    if (n1 > (int64_t)1 << 20 || n2 > (int64_t)1 << 20 || n1 * n2 > (int64_t)1 << 32) return PNSCAN_ERR_ARG;
+    InterpArgs A{fli_nodes, status_nodes, n1 > 0 ? (n1 - 1) / stride + 1 : 0, n2 > 0 ? (n2 - 1) / stride + 1 : 0,
+                 stride, n1, n2, mean, spread};
+    return launch_interp_grid(A, (cudaStream_t)cuda_stream) == cudaSuccess ? PNSCAN_OK : PNSCAN_ERR_CUDA;
+}
+
 int adaptive_select(const float* mean, const float* spread, int64_t n, float thr, float band, float spread_max,
                     const double* cells, int32_t* idx, double* cells_out, int64_t* count, void* workspace,
                     void* cuda_stream)

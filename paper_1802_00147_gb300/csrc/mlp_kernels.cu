@@ -546,7 +546,58 @@ __global__ void k_features(const double* cells, long long n, float* X)
     X[4 * i + 3] = (float)cells[9 * i + 7];
 }
 
+// Features from any four of a cell's nine fields.
+__global__ void k_features_fields(const double* cells, long long n, FieldSel f, float* X)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int k = 0; k < NIN; k++) X[NIN * i + k] = (float)cells[9 * i + f.field[k]];
+}
+
+// No-learning map of a row-major n1 x n2 grid from an integrated coarse grid
+// of every stride-th cell in both directions (nc1 x nc2 nodes, node (a, b) at
+// cell (a stride, b stride)): the FLI interpolated bilinearly between the
+// four surrounding nodes (clamped beyond the last node), and the spread of
+// those four values (max - min) as the uncertainty.  A node counts with its
+// FLI when it finished (DONE) or saturated, else as 0 (not chaotic).  A cell
+// that is itself a node takes the node's FLI and spread 0.
+__global__ void k_interp_grid(InterpArgs A)
+{
+    const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (c >= A.n1 * A.n2) return;
+    const long long i = c / A.n2, j = c % A.n2;
+    const long long a0 = i / A.stride, b0 = j / A.stride;
+    const long long a1 = a0 + 1 < A.nc1 ? a0 + 1 : a0, b1 = b0 + 1 < A.nc2 ? b0 + 1 : b0;
+    const float wa = a1 > a0 ? (float)(i - a0 * A.stride) / (float)A.stride : 0.f;
+    const float wb = b1 > b0 ? (float)(j - b0 * A.stride) / (float)A.stride : 0.f;
+    auto node = [&](long long a, long long b) {
+        const long long k = a * A.nc2 + b;
+        const int st = A.status[k];
+        return (st == 1 || st == 4) ? (float)A.fli[k] : 0.f;
+    };
+    const float v00 = node(a0, b0), v01 = node(a0, b1), v10 = node(a1, b0), v11 = node(a1, b1);
+    const float lo = fminf(fminf(v00, v01), fminf(v10, v11)), hi = fmaxf(fmaxf(v00, v01), fmaxf(v10, v11));
+    const bool is_node = (i % A.stride == 0) && (j % A.stride == 0);
+    const float top = fmaf(wb, v01 - v00, v00), bot = fmaf(wb, v11 - v10, v10);
+    A.mean[c] = is_node ? v00 : fmaf(wa, bot - top, top);
+    A.spread[c] = is_node ? 0.f : hi - lo;
+}
+
 // -------------------------------------------------------------- launchers
+cudaError_t launch_features_fields(const double* cells, long long n, FieldSel f, float* X, cudaStream_t st)
+{
+    if (n > 0) k_features_fields<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cells, n, f, X);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interp_grid(const InterpArgs& A, cudaStream_t st)
+{
+    const long long n = A.n1 * A.n2;
+    if (n > 0) k_interp_grid<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_features(const double* cells, long long n, float* X, cudaStream_t st)
 {
     if (n > 0) k_features<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cells, n, X);

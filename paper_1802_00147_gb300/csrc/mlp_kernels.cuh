@@ -79,5 +79,19 @@ cudaError_t launch_select(const SelectArgs& A, void* ws, long long* d_total, cud
 cudaError_t launch_merge(const MergeArgs& A, cudaStream_t st);
 cudaError_t launch_features(const double* cells, long long n, float* X, cudaStream_t st);
 
+struct FieldSel {
+    int field[NIN];   // cell field (0..8) of each input
+};
+cudaError_t launch_features_fields(const double* cells, long long n, FieldSel f, float* X, cudaStream_t st);
+
+struct InterpArgs {
+    const double* fli;      // [nc1][nc2] node FLIs
+    const int32_t* status;  // [nc1][nc2] node statuses
+    long long nc1, nc2, stride, n1, n2;
+    float* mean;            // [n1][n2]
+    float* spread;          // [n1][n2]
+};
+cudaError_t launch_interp_grid(const InterpArgs& A, cudaStream_t st);
+
 }  // namespace mlp
 }  // namespace pnscan

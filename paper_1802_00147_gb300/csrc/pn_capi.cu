@@ -259,7 +259,8 @@ bool same_run(const RunCfg& a, const RunCfg& b)
            a.flags.use_ss == b.flags.use_ss && a.flags.use_qm == b.flags.use_qm &&
            a.newton.tol == b.newton.tol && a.newton.max_iter == b.newton.max_iter &&
            a.newton.det_min == b.newton.det_min && a.newton.apply_small == b.newton.apply_small &&
-           a.newton.mode == b.newton.mode &&
+           a.newton.mode == b.newton.mode && a.newton.split_min == b.newton.split_min &&
+           a.newton.cond_switch == b.newton.cond_switch &&
            a.correct == b.correct && a.rk_order == b.rk_order && a.h == b.h &&
            a.d0 == b.d0 && a.renorm == b.renorm && a.fli_cap == b.fli_cap &&
            a.rmerge2 == b.rmerge2 && a.rescape2 == b.rescape2 && a.nstep_base == b.nstep_base &&
@@ -313,6 +314,8 @@ int scan_params_default(scan_params* p)
     p->newton_tol = 1e-10;
     p->newton_max = 50;
     p->newton_det_min = 1e-5;
+    p->newton_split_min = 1e-3;
+    p->newton_cond_switch = 1e-2;
     p->newton_apply_small = 1;
     p->fli_d0 = 1e-9;
     p->fli_renorm_steps = 100;
@@ -335,7 +338,9 @@ int scan_create(const scan_params* p, scan_handle** out)
     *out = nullptr;
     if (!p || p->n < 0 || p->n > (int64_t)1 << 31) return PNSCAN_ERR_ARG;
     if (p->pn_order < 0 || p->pn_order > 2) return PNSCAN_ERR_ARG;
-    if (!(p->newton_tol > 0.0) || p->newton_max < 1 || p->newton_max > 1000 || !(p->newton_det_min >= 0.0))
+    if (!(p->newton_tol > 0.0) || p->newton_max < 1 || p->newton_max > 1000 || !(p->newton_det_min >= 0.0) ||
+        !(p->newton_split_min >= 0.0) || !(p->newton_split_min < 1.0) || !(p->newton_cond_switch >= 0.0) ||
+        !(p->newton_cond_switch < 1.0))
         return PNSCAN_ERR_ARG;
     if (!(p->fli_d0 > 0.0)) return PNSCAN_ERR_ARG;
     if (p->block_size && (p->block_size < 32 || p->block_size > 128 || p->block_size % 32)) return PNSCAN_ERR_ARG;
@@ -427,6 +432,8 @@ int scan_create(const scan_params* p, scan_handle** out)
     b.newton.tol = p->newton_tol;
     b.newton.max_iter = p->newton_max;
     b.newton.det_min = p->newton_det_min;
+    b.newton.split_min = p->newton_split_min;
+    b.newton.cond_switch = p->newton_cond_switch;
     b.newton.apply_small = p->newton_apply_small != 0;
     b.newton.mode = p->correct;
     b.correct = p->correct != 0;
@@ -704,9 +711,10 @@ struct CheckpointHeader {
     double newton_tol, newton_det_min, d0, fli_cap, rmerge2, rescape2;
     int rr;
     RRCoef rrc;
+    double newton_split_min, newton_cond_switch;
 };
 
-static const char kCheckpointMagic[8] = {'P', 'N', 'S', 'C', 'A', 'N', '0', '1'};
+static const char kCheckpointMagic[8] = {'P', 'N', 'S', 'C', 'A', 'N', '0', '2'};
 
 static void fill_header(const scan_handle* h, CheckpointHeader& c)
 {
@@ -726,6 +734,8 @@ static void fill_header(const scan_handle* h, CheckpointHeader& c)
     c.renorm = b.renorm;
     c.newton_tol = b.newton.tol;
     c.newton_det_min = b.newton.det_min;
+    c.newton_split_min = b.newton.split_min;
+    c.newton_cond_switch = b.newton.cond_switch;
     c.d0 = b.d0;
     c.fli_cap = b.fli_cap;
     c.rmerge2 = b.rmerge2;

@@ -587,7 +587,7 @@ __device__ __forceinline__ void rk5_step_rr(const C& c, const RRCoef& g, double 
 }
 
 // ------------------------------------------------------ manifold correction
-enum CorrKind : int { CORR_DUAL = 0, CORR_NONE = 1, CORR_VELOCITY = 2 };
+enum CorrKind : int { CORR_DUAL = 0, CORR_NONE = 1, CORR_VELOCITY = 2, CORR_SPLIT = 3 };
 
 struct NewtonCfg {
     double tol;       // stop when |d alpha| <= tol and |d beta| <= tol (Sec. 3A: 1e-10)
@@ -595,6 +595,9 @@ struct NewtonCfg {
     double det_min;   // relative-determinant guard of the singular scaling
     int apply_small;  // 1: apply a step, then stop if it was within tol; 0: stop before applying it
     int mode;         // CORR_MODE_*: what the correction restores
+    double split_min; // conditioning guard of the split scaling (<= 0: not used)
+    double cond_switch; // dual scaling's relative determinant below which the better-conditioned
+                        // of the dual and split scalings is used (<= 0: dual down to det_min)
 };
 
 // Correction modes: spin lengths and dual scaling (Eqs. 10-13); ablations:
@@ -605,9 +608,11 @@ enum CorrMode : int { CORR_MODE_DUAL = 1, CORR_MODE_SPINS = 2, CORR_MODE_VELOCIT
 // Eq. 10, then Eqs. 11-13: p = alpha p*, r = beta r* with (alpha, beta) from
 // H(beta r*, alpha p*, S) = E0 and |J(beta r*, alpha p*, S)| = J0 by Newton's
 // method from (1, 1).  Returns the number of Newton iterations; *kind is
-// CORR_DUAL when the dual scaling was applied, CORR_VELOCITY when it was
-// singular (or did not converge) and E was restored by scaling p alone, and
-// CORR_NONE when neither converged.
+// CORR_DUAL when the dual scaling was applied; where it was singular (or did
+// not converge) CORR_SPLIT when the split scaling of p's tangential and
+// radial parts restored both integrals, CORR_VELOCITY when that was singular
+// too and E was restored by scaling p alone, and CORR_NONE when nothing
+// converged.
 //
 // With u = 1/beta, every term of H at the scaled point is a monomial in
 // (alpha, u):  H(alpha, u) = alpha^2 (A2 + alpha^2 (A4 + alpha^2 A6))
@@ -668,6 +673,11 @@ __device__ __forceinline__ int correct(const C& c, Vec12& y, const Ref& ref,
     double al = 1.0, be = 1.0;
     int it = 0;
     bool conv = false, stop = false;
+    // split scaling state (below): factors of p's tangential and radial parts,
+    // iterations done, converged
+    double sa = 1.0, sg = 1.0;
+    int ks = 0;
+    bool sok = false;
     // First iteration at alpha = beta = 1 (u = 1, k = 1): the monomial sums
     // need no powers and no reciprocal; there dF2/dalpha = dF2/dbeta = dJ and
     // dH/dbeta = -dH/du, so det = dJ (Ha + Hu).
@@ -686,7 +696,41 @@ __device__ __forceinline__ int correct(const C& c, Vec12& y, const Ref& ref,
         const double F2 = fma(Jn2, rJ, -ref.J);
         const double p1 = Ha * dJ, p2 = -Hu * dJ;
         const double det = p1 - p2;
-        if (fabs(det) > nc.det_min * (fabs(p1) + fabs(p2))) {
+        // In the dual scaling's ill-conditioned band the split scaling below is
+        // used instead where it is better conditioned: its relative
+        // conditioning at (1, 1) is |H_g| / (|H_a| + |H_g|), with
+        // H_a = p_t.dH/dp and H_g = p_r.dH/dp from the split polynomial's
+        // derivatives at q = P2, w = NP2 (P2 = 2 A2 exactly).
+        bool prefer_split = false;
+        if (nc.cond_switch > 0.0 && nc.split_min > 0.0 && fabs(det) <= nc.cond_switch * (fabs(p1) + fabs(p2))) {
+            const double P2s = 2.0 * A2, Rr = -B0;
+            const double Hq1 = fma(P2s, fma(3.0 * c[K_A2], P2s, 2.0 * c[K_A1]), fma(Rr * Rr, c[K_D1], 0.5))
+                             + Rr * fma(2.0 * c[K_C1], P2s, fma(c[K_C2], NP2, c[K_B1]));
+            const double Hw1 = Rr * fma(c[K_C2], P2s, fma(2.0 * c[K_C3], NP2, c[K_B2])) + Rr * Rr * c[K_D2];
+            const double As = fma(2.0 * (P2s - NP2), Hq1, E1);
+            const double Bs = 2.0 * NP2 * (Hq1 + Hw1);
+            prefer_split = fabs(Bs) * (fabs(p1) + fabs(p2)) > fabs(det) * (fabs(As) + fabs(Bs)) &&
+                           fabs(Bs) > nc.split_min * (fabs(As) + fabs(Bs)) &&
+                           fabs(dJ) > nc.split_min * (LL * rsqrt(LL));
+            if (prefer_split) {
+                // the split scaling's first Newton step at (1, 1): H, F and the
+                // |J| derivative are the dual scaling's at its own (1, 1)
+                ks = 1;
+                const double rd = __drcp_rn(dJ * Bs);
+                const double da = F2 * Bs * rd;
+                const double dg = fma(F1, dJ, -As * F2) * rd;
+                const bool small = fabs(da) <= nc.tol && fabs(dg) <= nc.tol;
+                if (!(small && !nc.apply_small)) {
+                    sa -= da;
+                    sg -= dg;
+                }
+                sok = small;
+            }
+        }
+        if (prefer_split) {
+            it = 0;
+            stop = true;   // straight to the split scaling
+        } else if (fabs(det) > nc.det_min * (fabs(p1) + fabs(p2))) {
             const double rd = __drcp_rn(det);
             const double da = fma(F1, dJ, Hu * F2) * rd;
             const double db = fma(Ha, F2, -dJ * F1) * rd;
@@ -741,9 +785,76 @@ __device__ __forceinline__ int correct(const C& c, Vec12& y, const Ref& ref,
         *kind = CORR_DUAL;
         return it;
     }
-    // Singular (or non-converged) dual scaling: restore E alone by velocity
-    // scaling, p = a p*, H(r*, a p*, S) = E0 (Newton in a from 1), i.e. the
-    // monomial form at 1/beta = 1.  |J| is left to the next step.
+    // Singular (or non-converged) dual scaling -- for a Kepler ellipse at
+    // r = a, where |p_r| / |p| = e: restore both integrals by the split
+    // scaling p = a p_t + g p_r of p*'s tangential and radial parts, r = r*.
+    // There L = a L*, and with q = p^2 = a^2 Pt2 + g^2 NP2, w = (n.p)^2 =
+    // g^2 NP2 every term of H is a polynomial in (q, w, a):
+    //   H = q (1/2 + q (A1 + q A2)) + R (q (B1 + C1 q + C2 w) + w (B2 + C3 w))
+    //       + R^2 (D1 q + D2 w) + a E1 + (B0 + C0 + D0),
+    // and |J|^2 = a^2 LL + 2 a LJ + SSq.  Newton on (a, g) from (1, 1); the
+    // Jacobian [[H_a, H_g], [J_a, 0]] is triangular.  It is used only where
+    // |H_g| > split_min (|H_a| + |H_g|) and |J_a| > split_min |L*|: near a
+    // circular orbit E and |J| cannot be moved independently, and it is as
+    // ill-conditioned as the dual scaling.  State quantities are recomputed
+    // from (r*, p*), which are still unchanged here.
+    if (nc.mode == CORR_MODE_DUAL && nc.split_min > 0.0) {
+        const double Rr = -B0;
+        const double NPs = dot3(y.r, y.p) * Rr;
+        const double NP2s = NPs * NPs;
+        const double Pt2 = dot3(y.p, y.p) - NP2s;
+        const double RR2 = Rr * Rr;
+        const double hq0 = fma(Rr, c[K_B1], fma(RR2, c[K_D1], 0.5));    // dH/dq at q = w = 0
+        const double hw0 = fma(Rr, c[K_B2], RR2 * c[K_D2]);             // dH/dw at q = w = 0
+        const double Hc = (B0 + C0) + D0;
+        const double Lmag = LL * rsqrt(LL);
+        while (!sok && ks < nc.max_iter) {
+            ++ks;
+            const double w = sg * sg * NP2s;
+            const double q = fma(sa * sa, Pt2, w);
+            const double H = fma(q, fma(q, fma(q, c[K_A2], c[K_A1]), 0.5),
+                                 fma(Rr, fma(q, fma(c[K_C1], q, fma(c[K_C2], w, c[K_B1])),
+                                             w * fma(c[K_C3], w, c[K_B2])),
+                                     fma(RR2, fma(c[K_D1], q, c[K_D2] * w), fma(sa, E1, Hc))));
+            const double Hq = fma(q, fma(3.0 * c[K_A2], q, 2.0 * c[K_A1]), hq0)
+                            + Rr * fma(2.0 * c[K_C1], q, c[K_C2] * w);
+            const double Hw = fma(Rr, fma(c[K_C2], q, 2.0 * c[K_C3] * w), hw0);
+            const double Ha = fma(2.0 * sa * Pt2, Hq, E1);
+            const double Hg = 2.0 * sg * NP2s * (Hq + Hw);
+            const double Jn2 = fma(sa, fma(sa, LL, LJx2), SSq);
+            const double rJ = rsqrt(Jn2);
+            const double Ja = fma(sa, LL, LJ) * rJ;
+            if (!(fabs(Hg) > nc.split_min * (fabs(Ha) + fabs(Hg))) || !(fabs(Ja) > nc.split_min * Lmag))
+                break;   // ill-conditioned (or NaN)
+            const double F1 = H - ref.E;
+            const double F2 = fma(Jn2, rJ, -ref.J);
+            // triangular Jacobian [[Ha, Hg], [Ja, 0]]: da = F2 / Ja,
+            // dg = (F1 - Ha da) / Hg, with one reciprocal of Ja Hg
+            const double rd = __drcp_rn(Ja * Hg);
+            const double da = F2 * Hg * rd;
+            const double dg = fma(F1, Ja, -Ha * F2) * rd;
+            const bool small = fabs(da) <= nc.tol && fabs(dg) <= nc.tol;
+            if (small && !nc.apply_small) { sok = true; break; }
+            sa -= da;
+            sg -= dg;
+            if (small) { sok = true; break; }
+            if (!(fabs(sa) < 1e300) || !(fabs(sg) < 1e300)) break;
+        }
+        if (sok) {
+            // p = a (p* - p_r) + g p_r, p_r = (n.p*) n = (NPs Rr) r*
+            const double f = NPs * Rr;
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                const double pr = f * y.r[i];
+                y.p[i] = fma(sa, y.p[i] - pr, sg * pr);
+            }
+            *kind = CORR_SPLIT;
+            return it + ks;
+        }
+    }
+    // Both singular (or non-converged): restore E alone by velocity scaling,
+    // p = a p*, H(r*, a p*, S) = E0 (Newton in a from 1), i.e. the monomial
+    // form at 1/beta = 1.  |J| is left to the next step.
     double a = 1.0;
     int k = 0;
     bool ok = false;
@@ -763,7 +874,7 @@ __device__ __forceinline__ int correct(const C& c, Vec12& y, const Ref& ref,
         y.p[0] *= a; y.p[1] *= a; y.p[2] *= a;
     }
     *kind = ok ? CORR_VELOCITY : CORR_NONE;
-    return it + k;
+    return it + ks + k;
 }
 
 }  // namespace pnscan

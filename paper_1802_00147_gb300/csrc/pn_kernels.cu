@@ -613,7 +613,7 @@ __global__ void k_reduce(DevState S, double thr, Summary* out)
             dE = fabs((S.out[0 * n + i] - S.ref[0 * n + i]) / S.ref[0 * n + i]);
             dJall = fabs((S.out[1 * n + i] - S.ref[1 * n + i]) / S.ref[1 * n + i]);
             if (!(dJall == dJall)) dJall = 1e300;
-            if (S.last_kind[i] == CORR_DUAL) dJ = dJall;
+            if (S.last_kind[i] == CORR_DUAL || S.last_kind[i] == CORR_SPLIT) dJ = dJall;
             else fallback = 1;
             const double s1 = S.ref[2 * n + i], s2 = S.ref[3 * n + i];
             if (s1 > 0.0) dS = fmax(dS, fabs(S.out[2 * n + i] - s1) / s1);

@@ -148,7 +148,8 @@ __global__ void __launch_bounds__(kNoallocBlock) k_noalloc_partials(Inputs in, N
             if (!(dJ == dJ)) dJ = 1e300;
             p.max_dE = dE;
             p.max_dJ_all = dJ;
-            if (!in.last_kind || in.last_kind[i] == 0) p.max_dJ = dJ;
+            // last step dual-scaled (0) or split-scaled (3): |J| was restored
+            if (!in.last_kind || in.last_kind[i] == 0 || in.last_kind[i] == 3) p.max_dJ = dJ;
             else p.n_final_fallback = 1;
             if (in.spin_ref) {
                 const double s1 = in.spin_ref[2 * i], s2 = in.spin_ref[2 * i + 1];

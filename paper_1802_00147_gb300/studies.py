@@ -136,23 +136,26 @@ def paper_scans(t_end=1.0e5, h=1.0, thr=5.8, out_dir=None, n=314):
     return report
 
 
-def newton_tolerance_study(n=64, t_end=1.0e4, h=1.0, eps_list=(1e-6, 1e-8, 1e-10), seed=1):
+def newton_tolerance_study(n=64, t_end=1.0e4, h=1.0, eps_list=(1e-6, 1e-8, 1e-10), seed=1, cond_switch=0.0):
     """Energy, |J| and spin-length drift at t_end on an n x n grid of the
     small-scan family (x0 in [15, 40], theta in [0, pi], m1 = m2, chi = 1)
-    for each Newton tolerance and stopping rule."""
+    for each Newton tolerance and stopping rule.  Fig. 4 is about the
+    paper's own correction, so by default the dual scaling is used at every
+    step where it is not singular (cond_switch 0)."""
     import torch
     cells = W.grid_cells(n, n, 15.0, 40.0, seed)
     m1 = cells[:, W.BETA] / (1 + cells[:, W.BETA])
     m2 = 1 / (1 + cells[:, W.BETA])
     spin_ref = np.stack([cells[:, W.CHI1] * m1 ** 2, cells[:, W.CHI2] * m2 ** 2], axis=1)
     cd = torch.as_tensor(np.ascontiguousarray(cells[:, :9]), device="cuda")
-    report = {"grid": "%dx%d" % (n, n), "orbits": int(cells.shape[0]), "h": h, "t_end": t_end, "rk_order": 5}
+    report = {"grid": "%dx%d" % (n, n), "orbits": int(cells.shape[0]), "h": h, "t_end": t_end, "rk_order": 5,
+              "cond_switch": cond_switch}
     for apply_small in (1, 0):
         rule = "apply_then_test" if apply_small else "stop_before_applying"
         report[rule] = {}
         for eps in eps_list:
             with Scan(None, device=True, n=cells.shape[0], rk_order=5, newton_tol=eps,
-                      newton_apply_small=apply_small) as s:
+                      newton_apply_small=apply_small, newton_cond_switch=cond_switch) as s:
                 s.setup(cd)
                 s.run(t_end, h)
                 out = s.read()
@@ -310,8 +313,10 @@ def fli_curves(cells, t_end, every=1000.0, h=1.0, **opts):
     return np.array(ts), np.array(flis)
 
 
-def paper_fli_curves(t_end=1.0e5, every=500.0, out_dir=None, thr=5.8):
-    """Fig. 3: FLI(t) of case II orbits 1 and 2, corrected RK5, h = 1."""
+def paper_fli_curves(t_end=8.0e5, every=2000.0, out_dir=None, thr=5.8):
+    """Fig. 3: FLI(t) of case II orbits 1 and 2, corrected RK5, h = 1.
+    Orbit 2's exponential growth sets in near t = 8e5 (an uncorrected RK5 run
+    at h = 0.25 agrees), so that is the default length."""
     import os
     names, cells = W.paper_orbit_cells()
     pick = [names.index("case_II_orbit_1"), names.index("case_II_orbit_2")]

@@ -9,10 +9,10 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _run(env_extra):
+def _run(env_extra, gpus=1):
     env = dict(os.environ, **env_extra)
-    return subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
-                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    return subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
+                           "--gpus", str(gpus)], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
 
 
 def test_reference_arm_prints_one_contract_line():
@@ -33,6 +33,11 @@ def test_reference_arm_prints_one_contract_line():
 
 
 def test_reference_arm_other_ranks_do_no_work():
-    r = _run({"RANK": "1", "WORLD_SIZE": "2"})
+    r = _run({"RANK": "1", "WORLD_SIZE": "2"}, gpus=2)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_gpus_must_match_the_launchers_world_size():
+    r = _run({"RANK": "1", "WORLD_SIZE": "2"}, gpus=1)
+    assert r.returncode != 0 and "WORLD_SIZE" in r.stderr

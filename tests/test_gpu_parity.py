@@ -70,7 +70,8 @@ def gpu_run(pn, cells, nsteps, h=1.0, chunks=1, device=False, read_diag=False, *
     return out
 
 
-ORC_KEYS = {"fli_renorm_steps": "fli_renorm", "newton_det_min": "det_min", "radiation_reaction": "rr"}
+ORC_KEYS = {"fli_renorm_steps": "fli_renorm", "newton_det_min": "det_min", "radiation_reaction": "rr",
+            "newton_split_min": "split_min", "newton_cond_switch": "cond_switch"}
 
 
 def orc_run(cells, nsteps, h=1.0, y0=None, **cfg):
@@ -90,20 +91,38 @@ def block_relerr(a, b):
     return w
 
 
-def ulp_spreads(run, y0, o, calibration):
+def ulp_spreads(run, y0, o, calibration, h, d0=1e-9):
     """The oracle against itself with one initial component moved by one ulp,
-    up and down, for each of the 12 components (24 runs; `run(y1)` integrates
-    from y1).  Returns per-orbit maxima of the state, FLI and integral
-    differences over the `calibration` moves (components moved up), and the
-    FLI maximum over all 24 moves.
+    up and down, for each of the 12 components (24 runs; `run(y1, h, idx,
+    d0)` integrates orbits idx -- None: all -- from y1 with step h and FLI
+    separation d0).  Returns per-orbit maxima of the state, FLI and integral
+    differences over the `calibration` moves (components moved up); the FLI
+    maximum over all 24 moves goes to o["s_fli_all"], and o["refine_fli"](idx)
+    gives a denser estimate of the FLI spread of orbits idx.
 
     A single one-ulp move leaves most of a run's later rounding decisions
     correlated with the unmoved run's, so a few moves underestimate how far a
     program that rounds differently at every operation (FMA against separate
     multiply and add) lands from the oracle.  Measured with the oracle itself
-    compiled with and without FMA contraction: over 3 moves up to 20 of 774
-    orbits' FLI differences exceed 3x the spread (ratio up to 9); over all 24
-    moves none do (ratio <= 2.1)."""
+    compiled with and without FMA contraction (uneven batch, t = 1000): the
+    largest FLI difference is 21x the spread over 3 moves but at most 2.4x
+    the spread over all 24.
+
+    The FLI's rounding noise comes from the correction: a Newton step in the
+    scaling's ill-conditioned band amplifies rounding in F by the inverse
+    conditioning, and kicks that differ between the two trajectories move
+    their 1e-9 separation.  With the dual scaling kept down to its singular
+    guard (amplification up to 1e5) that noise was heavy-tailed: median
+    |dFLI| 6e-3, some orbits at 0.5, and against the GPU a few orbits in a
+    thousand at 3-6x the 24-move spread.  With the split scaling taking that
+    band (cond_switch) the noise is ~50x smaller.  For orbits beyond the
+    24-move estimate refine_fli samples the tail densely: every combination
+    of the initial state (unmoved, or one component one ulp up or down), h
+    moved by 0, 1 or 2 ulp either way and d0 moved by 0 or 1 ulp either way,
+    374 runs besides the unmoved one.  Moving h shifts every rounding
+    decision of the run (the time shift, ~t x 2e-16, is itself a
+    rounding-level perturbation); moving d0 does the same for the FLI's
+    renormalisations."""
     n = y0.shape[0]
     s_state, s_fli, s_fli_all = np.zeros(n), np.zeros(n), np.zeros(n)
     s_integ = np.zeros((n, 6))
@@ -111,7 +130,7 @@ def ulp_spreads(run, y0, o, calibration):
         for up in (True, False):
             y1 = y0.copy()
             y1[:, comp] = np.nextafter(y1[:, comp], np.inf if up else -np.inf)
-            o1 = run(y1)
+            o1 = run(y1, h, None, d0)
             same = o1["status"] == o["status"]
             dfli = np.where(same, np.abs(o1["fli"] - o["fli"]), 0.0)
             s_fli_all = np.maximum(s_fli_all, dfli)
@@ -121,6 +140,29 @@ def ulp_spreads(run, y0, o, calibration):
                 s_integ = np.maximum(s_integ, np.where(same[:, None],
                                                        np.abs(o1["integrals"] - o["integrals"]), 0.0))
     o["s_fli_all"] = s_fli_all
+
+    def ulps(x, k):
+        for _ in range(abs(k)):
+            x = np.nextafter(x, np.inf if k > 0 else -np.inf)
+        return x
+
+    def refine_fli(idx):
+        idx = np.asarray(idx)
+        base = y0[idx]
+        spread = s_fli_all[idx].copy()
+        states = [base] + [np.where(np.arange(12) == comp, np.nextafter(base, d), base)
+                           for comp in range(12) for d in (np.inf, -np.inf)]
+        for kh in (0, -1, 1, -2, 2):
+            for kd in (0, -1, 1):
+                for k, y1 in enumerate(states):
+                    if kh == 0 and kd == 0 and k == 0:
+                        continue
+                    o1 = run(np.ascontiguousarray(y1), ulps(h, kh), idx, ulps(d0, kd))
+                    same = o1["status"] == o["status"][idx]
+                    spread = np.maximum(spread, np.where(same, np.abs(o1["fli"] - o["fli"][idx]), 0.0))
+        return spread
+
+    o["refine_fli"] = refine_fli
     return s_state, s_fli, s_integ
 
 
@@ -133,7 +175,11 @@ def oracle_sensitivity(cells, nsteps, h=1.0, **cfg):
     o = orc_run(cells, nsteps, h, **cfg)
     y0 = oracle.setup_cells(cells[:, :9])
     calibration = range(12) if cfg.get("rr") else (0, 4, 6)
-    s_state, s_fli, s_integ = ulp_spreads(lambda y1: orc_run(cells, nsteps, h, y0=y1, **cfg), y0, o, calibration)
+    d0 = cfg.get("fli_d0", 1e-9)
+    s_state, s_fli, s_integ = ulp_spreads(
+        lambda y1, hh, idx, dd: orc_run(cells if idx is None else cells[idx], nsteps, hh, y0=y1,
+                                        **dict(cfg, fli_d0=dd)),
+        y0, o, calibration, h, d0)
     # the integrals' own spread: at rounding level for a conservative run,
     # where they are restored every step; with radiation reaction the
     # reference E and |J| are integrals along the trajectory (Sec. 3B) and
@@ -185,7 +231,13 @@ def assert_parity(g, o, s_state, s_fli, nsteps):
         # moves (+1e-3)
         sfa = o["s_fli_all"][done] if "s_fli_all" in o else sf
         bad = np.flatnonzero(df > 3 * sfa + 1e-3)
-        assert bad.size == 0, ("fli", bad.size, df[bad][:5], sf[bad][:5])
+        if bad.size and "refine_fli" in o:
+            # the orbits beyond the 24-move estimate: their spread over 375 samples
+            sfr = o["refine_fli"](np.flatnonzero(done)[bad])
+            bad = bad[df[bad] > 3 * sfr + 1e-3]
+            sfa = sfa.copy()
+            sfa[np.flatnonzero(df > 3 * sfa + 1e-3)] = sfr
+        assert bad.size == 0, ("fli", bad.size, df[bad][:5], sfa[bad][:5])
         agree = (g["fli"][done] > FLI_THRESH) == (o["fli"][done] > FLI_THRESH)
         assert agree.mean() >= 0.995
     return float(err.max()) if err.size else 0.0
@@ -267,6 +319,10 @@ def test_qm_parity(pn):
                                   dict(correct=0),
                                   dict(r_merge=0.0, r_escape=0.0, fli_renorm_steps=37),
                                   dict(newton_det_min=0.0),
+                                  dict(newton_det_min=1e-3),          # many steps take the split scaling
+                                  dict(newton_split_min=0.0),         # singular steps: velocity scaling only
+                                  dict(newton_cond_switch=0.0),       # dual scaling down to det_min
+                                  dict(newton_cond_switch=0.1),       # split scaling in a wider band
                                   dict(rk_order=5),
                                   dict(newton_apply_small=0, newton_tol=1e-8),
                                   dict(correct=2), dict(correct=3),
@@ -327,8 +383,11 @@ def test_random_orientation_states_parity(pn, schedule):
     # every component moved by one ulp: in random orientations the spread over
     # all 12 is up to 3x the spread over (x, p_y, S1_x) that grid states need
     s_state, s_fli, _ = ulp_spreads(
-        lambda y1: oracle.scan(y1, beta, 1.0, 400, oracle.config(use_qm=1), kappa1=k1, kappa2=k2),
-        y0, o, range(12))
+        lambda y1, hh, idx, dd: oracle.scan(y1, beta if idx is None else beta[idx], hh, 400,
+                                            oracle.config(use_qm=1, fli_d0=dd),
+                                            kappa1=k1 if idx is None else k1[idx],
+                                            kappa2=k2 if idx is None else k2[idx]),
+        y0, o, range(12), 1.0)
     assert_parity(g, o, s_state, s_fli, 400)
 
 
@@ -461,8 +520,12 @@ def test_radiation_reaction_random_orientation_parity(pn):
     o = oracle.scan(y0, beta, 1.0, 400, cfg, kappa1=k1, kappa2=k2)
     counts = np.bincount(o["status"], minlength=6)
     assert counts[oracle.MERGED] > 0 and counts[oracle.ESCAPED] > 0 and counts[oracle.DONE] > 0
-    s_state, s_fli, s_int = ulp_spreads(lambda y1: oracle.scan(y1, beta, 1.0, 400, cfg, kappa1=k1, kappa2=k2),
-                                        y0, o, range(12))
+    s_state, s_fli, s_int = ulp_spreads(
+        lambda y1, hh, idx, dd: oracle.scan(y1, beta if idx is None else beta[idx], hh, 400,
+                                            oracle.config(use_qm=1, rr=1, r_escape=38.0, fli_d0=dd),
+                                            kappa1=k1 if idx is None else k1[idx],
+                                            kappa2=k2 if idx is None else k2[idx]),
+        y0, o, range(12), 1.0)
     o["s_integrals"] = s_int
     o["integ_floor"] = 4 * 400 * 2.0 ** -52
     assert_parity(g, o, s_state, s_fli, 400)
@@ -683,17 +746,16 @@ def test_summary_matches_host_reduction(pn):
 # ----------------------------------------- full-length scan: drift, classes
 @pytest.mark.slow
 def test_full_scan_drift_and_classification(pn):
-    """314 x 314 scan to t = 2e4.  Energy drift <= 1e-12 on every orbit that
-    reached t_end; |J| drift <= 1e-12 on every such orbit whose last step was
-    dual-scaled (where the scaling is singular only E can be restored, so a
-    run that ends there carries at most a few steps' RK4 error in |J|, here
-    bounded by 1e-10); and the chaotic/regular class of a seeded 400-orbit
+    """314 x 314 scan to t = 2e4.  Energy, |J| and spin-length drift <= 1e-12
+    on every orbit that reached t_end, whatever the kind of its last
+    correction (where the dual scaling is singular the split scaling restores
+    both integrals); and the chaotic/regular class of a seeded 400-orbit
     sample agrees with the oracle for >= 99.5 % of the cells."""
     cells = W.full_scan(seed=2)
     g = gpu_run(pn, cells, 20000)
     s = g["summary"]
     assert s["max_dE"] <= 1e-12 and s["max_dJ"] <= 1e-12 and s["max_dS"] <= 1e-12, s
-    assert s["max_dJ_all"] <= 1e-10 and s["n_final_fallback"] <= 1e-3 * s["status_count"][1], s
+    assert s["max_dJ_all"] <= 1e-12, s
     sub, idx = W.subset(cells, 400, seed=22)
     o = orc_run(sub, 20000)
     np.testing.assert_array_equal(g["status"][idx], o["status"])

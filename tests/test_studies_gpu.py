@@ -24,11 +24,13 @@ def test_qm_drift_with_and_without_correction():
 
 
 def test_newton_tolerance_ablation_over_a_grid():
-    """Fig. 4 over a 24 x 24 grid to t = 3000: under the stop-before-applying
-    rule the Newton steps at eps = 1e-6 and 1e-8 are rarely applied, so the
-    energy drift follows the uncorrected growth (the oracle gives medians
-    8.9e-12 / 1.7e-12), while eps = 1e-10 holds it ~100x lower (6.3e-14);
-    under the default rule every eps leaves round-off (oracle: max 1.6e-15)."""
+    """Fig. 4 over a 24 x 24 grid to t = 3000, with the paper's dual scaling
+    wherever it is not singular (newton_cond_switch 0): under the
+    stop-before-applying rule the Newton steps at eps = 1e-6 and 1e-8 are
+    rarely applied, so the energy drift follows the uncorrected growth (the
+    oracle gives medians 8.9e-12 / 1.7e-12), while eps = 1e-10 holds it
+    ~100x lower (6.3e-14); under the default rule every eps leaves round-off
+    (oracle: max 1.6e-15)."""
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -70,9 +72,12 @@ def test_correction_ablation_over_a_grid():
 
 
 def test_fli_curves_of_the_paper_case_II_orbits():
-    """Fig. 3 / Sec. 3B: along t the FLI of case II orbit 1 grows slowly
-    (regular) and that of orbit 2 outgrows it and crosses the threshold 5.8
-    by t = 1e5 (chaotic); the end values agree with the oracle's classification."""
+    """Fig. 3 / Sec. 3B: the FLI curves of case II orbits 1 and 2 sampled
+    along t (runs to t1, t2, ... on one handle) agree with the oracle's FLI
+    at t = 2.5e4, 5e4 and 1e5 within 3x the oracle's own spread over 24
+    one-ulp moves of the initial state (these close orbits' FLI carries a
+    spread of ~1 by t = 1e5); both are below the 5.8 threshold at 1e5 -- the
+    oracle pins orbit 2's exponential growth, which sets in near 8e5."""
     import numpy as np
     import torch
     if not torch.cuda.is_available():
@@ -86,12 +91,20 @@ def test_fli_curves_of_the_paper_case_II_orbits():
     pick = [names.index("case_II_orbit_1"), names.index("case_II_orbit_2")]
     t, fli = studies.fli_curves(cells[pick], 1.0e5, 5000.0, r_merge=0.0, r_escape=0.0)
     assert t.size == 20 and fli.shape == (20, 2)
-    assert fli[-1, 0] < 5.8 < fli[-1, 1]
-    # faster growth late in the run (oracle, t = 5e4 -> 1e5: +2.05 vs +1.03)
-    assert fli[-1, 1] - fli[9, 1] > 1.5 * (fli[-1, 0] - fli[9, 0])
-    o = oracle.scan(oracle.setup_cells(cells[pick, :9]), cells[pick, W.BETA], 1.0, 100_000,
-                    oracle.config(r_merge=0, r_escape=0))
-    assert (o["fli"] > 5.8).tolist() == [False, True]
+    c = cells[pick]
+    y0 = oracle.setup_cells(c[:, :9])
+    cfg = oracle.config(r_merge=0, r_escape=0)
+    for k in (4, 9, 19):                                   # t = 2.5e4, 5e4, 1e5
+        n = int(t[k])
+        o = oracle.scan(y0, c[:, W.BETA], 1.0, n, cfg)
+        spread = np.zeros(2)
+        for comp in range(12):
+            for d in (np.inf, -np.inf):
+                y1 = y0.copy()
+                y1[:, comp] = np.nextafter(y1[:, comp], d)
+                spread = np.maximum(spread, np.abs(oracle.scan(y1, c[:, W.BETA], 1.0, n, cfg)["fli"] - o["fli"]))
+        assert np.all(np.abs(fli[k] - o["fli"]) <= 3 * spread + 1e-3), (t[k], fli[k], o["fli"], spread)
+    assert np.all(fli[-1] < 5.8)
 
 
 def test_orbit3_inspiral_study():
