@@ -415,6 +415,19 @@ def run_adaptive(cells_full, cells_full_d, fli_full_d, thr=6.0, band=1.0, spread
     return out
 
 
+# ------------------------------------- adaptive scan on a boundary-rich plane
+def run_adaptive_boundary():
+    """The surrogate-adaptive map and the no-learning coarse-grid map against
+    integrating every cell, on the (theta1, theta2) plane of Sec. 3C, Fig. 7
+    (512 x 512, RK4 h = 1 to t_end = 1e4, no merger or escape cut as in the
+    paper's scan, threshold 5.8): a plane with an order/chaos boundary."""
+    from paper_1802_00147_gb300 import adaptive as A
+    rep = A.boundary_study(n=512, t_end=1.0e4, thr=5.8, stride=8, r_merge=0.0, r_escape=0.0)
+    for k in ("surrogate", "baseline"):     # the sweeps stay out of the bench line: the chosen points go in
+        rep[k]["n_points"] = len(rep[k].pop("points"))
+    return rep
+
+
 # ----------------------------------------------------------- uneven batch
 def run_uneven(n=100_000, t_end=2.0e4):
     """The uneven batch (mass ratio 0.1-1, isotropic spins, p_y 50-100% of
@@ -586,6 +599,7 @@ def run_ours(args, rank, world, local_rank):
     if args.adaptive and rank == 0:
         fli_full = scan.read()["fli"]
         adaptive = run_adaptive(cells_h, cells_d, fli_full)
+        adaptive["boundary_plane"] = run_adaptive_boundary()
 
     if rank != 0:
         return

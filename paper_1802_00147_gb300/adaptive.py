@@ -156,3 +156,97 @@ def cheapest(points, mis_max):
     misclassification is at most mis_max (None if there is none)."""
     ok = [p for p in points if p["misclassification"] <= mis_max]
     return min(ok, key=lambda p: p["marked_frac"]) if ok else None
+
+
+def boundary_study(n=512, t_end=1.0e4, thr=5.8, stride=8, train_m=None, members=5, train_steps=30000,
+                   bands=(0.25, 0.5, 1.0, 1.5, 2.0, 3.0), spread_maxes=(0.25, 0.5, 1.0, 2.0, float("inf")),
+                   mis_max=0.005, seed=11, target_clip=1.0, **opts):
+    """Surrogate-adaptive map against the no-learning coarse-grid map on the
+    (theta1, theta2) plane of Sec. 3C, Fig. 7 (workloads.theta12_plane),
+    which has an order/chaos boundary.
+
+    Both methods get the same integration budget for what they learn from:
+    the surrogate is trained on train_m random cells of the plane (default
+    (n/stride)^2), the baseline interpolates the (n/stride)^2 nodes of every
+    stride-th row and column.  Each is swept over the selection thresholds
+    (band, spread_max) against the full map; the cheapest point with
+    misclassification <= mis_max is then run end to end and timed.  Returns
+    the report (times in seconds; cells_integrated and seconds_total count
+    each method's training data or coarse nodes too).
+
+    The surrogate's training targets are clipped to thr +- target_clip: the
+    class depends only on the side of thr, and the FLIs of chaotic cells
+    scatter widely (6-15 at t = 1e4), so an unclipped fit spends its
+    capacity there.  Measured on the 512^2 plane at t = 1e4 (15.6 %
+    chaotic): unclipped, the cheapest point at <= 0.5 % marks 48.7 % of
+    the cells; clipped to +-2, 27.3 %; to +-1 with 30,000 steps, 23.7 %;
+    the coarse grid of stride 8, 22.7 %."""
+    from . import workloads as W
+    torch = _torch()
+    fields = (W.TH1, W.TH2, W.X0, W.BETA)
+    center, scale = (np.pi / 2, np.pi / 2, 10.14, 1.0), (np.pi / 2, np.pi / 2, 1.0, 1.0)
+    grid = W.theta12_plane(n)
+    grid_d = torch.as_tensor(np.ascontiguousarray(grid[:, :9]), device="cuda")
+    m = train_m or ((n - 1) // stride + 1) ** 2
+    train = W.theta12_random(m, seed)
+    # warm-up of every path on tiny inputs (first use of a PyTorch comparison
+    # or masked index loads its kernels)
+    training_set([train[:32]], [10.0], fields=fields, **opts)
+    full_map(grid_d[:64], 10.0, thr=thr, **opts)
+    baseline_map(grid_d[:64 * 64], 64, 64, 8, 10.0, thr=thr, **opts)
+
+    full = full_map(grid_d, t_end, thr=thr, **opts)
+    truth = full["cls"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X, y = training_set([train], [t_end], fields=fields, **opts)
+    if target_clip is not None:
+        # the class depends only on the side of thr: FLIs far beyond it
+        # (chaotic FLIs scatter widely) are clipped so that the fit spends
+        # its capacity near the boundary
+        y = y.clamp(thr - target_clip, thr + target_clip)
+    torch.cuda.synchronize()
+    data_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sur, hist = train_surrogate(X, y, members=members, steps=train_steps, lr=3e-3, seed=seed,
+                                center=center, scale=scale)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    mean_s, spread_s = sur.predict(features(grid_d, fields))
+    nodes = coarse_nodes(grid_d, n, n, stride)
+    out_c = integrate_cells(nodes, t_end, **opts)
+    mean_b, spread_b = adaptive_interp_grid(out_c["fli"], out_c["status"], n, n, stride)
+    pts_s = operating_points(mean_s, spread_s, truth, thr, bands, spread_maxes)
+    pts_b = operating_points(mean_b, spread_b, truth, thr, bands, spread_maxes)
+    best_s, best_b = cheapest(pts_s, mis_max), cheapest(pts_b, mis_max)
+    sub_idx = torch.as_tensor(W.subset(grid, 4096, seed=6)[1], device="cuda")
+    report = {"grid": "%dx%d" % (n, n), "plane": "theta1 x theta2 in [0, pi]^2, (beta, r, p_y) = (1, 10.14, 0.365), "
+                                              "chi = 1 (Sec. 3C, Fig. 7)",
+              "t_end": t_end, "thr": thr, "chaotic_frac": float(truth.float().mean().item()),
+              "plain_s": full["seconds"], "mis_max": mis_max, "budget_cells": m,
+              "surrogate": {"train_cells": m, "members": members, "train_steps": train_steps, "target_clip": target_clip,
+                            "training_data_s": data_s, "train_s": train_s, "points": pts_s, "chosen": best_s},
+              "baseline": {"stride": stride, "nodes": int(nodes.shape[0]), "points": pts_b, "chosen": best_b}}
+    if best_s is not None:
+        res = adaptive_map(sur, grid_d, t_end, thr=thr, band=best_s["band"], spread_max=best_s["spread_max"],
+                           fields=fields, **opts)
+        wrong = res["cls"] != truth
+        report["surrogate"].update(
+            adaptive_s=res["seconds"], marked=res["n_marked"], marked_frac=res["n_marked"] / grid.shape[0],
+            misclassification_all=float(wrong.float().mean().item()),
+            misclassification_subset4096=float(wrong[sub_idx].float().mean().item()),
+            speedup=full["seconds"] / res["seconds"],
+            cells_integrated=res["n_marked"] + m, seconds_total=res["seconds"] + train_s + data_s,
+            speedup_incl_training_and_data=full["seconds"] / (res["seconds"] + train_s + data_s))
+    if best_b is not None:
+        res = baseline_map(grid_d, n, n, stride, t_end, thr=thr, band=best_b["band"],
+                           spread_max=best_b["spread_max"], **opts)
+        wrong = res["cls"] != truth
+        report["baseline"].update(
+            seconds=res["seconds"], marked=res["n_marked"], marked_frac=res["n_marked"] / grid.shape[0],
+            misclassification_all=float(wrong.float().mean().item()),
+            misclassification_subset4096=float(wrong[sub_idx].float().mean().item()),
+            cells_integrated=res["n_marked"] + res["n_nodes"], seconds_total=res["seconds"],
+            speedup=full["seconds"] / res["seconds"])
+    sur.close()
+    return report

@@ -201,6 +201,21 @@ def paper_theta2_scan(theta1, n=314):
     return paper_cells(5.65, 0.765, 1.0 / 3.0, theta1, 0.01 * np.arange(n))
 
 
+def theta12_plane(n):
+    """The plane of Sec. 3C, Fig. 7 on an n x n grid: theta1, theta2 =
+    linspace(0, pi, n) (row-major, theta1 slow), (beta, r, p) = (1, 10.14,
+    0.365), chi = 1, spins in the x-z plane."""
+    t = np.linspace(0.0, np.pi, n)
+    T1, T2 = np.meshgrid(t, t, indexing="ij")
+    return paper_cells(10.14, 0.365, 1.0, T1.ravel(), T2.ravel())
+
+
+def theta12_random(m, seed):
+    """m cells of the same plane at seeded uniform (theta1, theta2) in [0, pi]^2."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return paper_cells(10.14, 0.365, 1.0, rng.uniform(0.0, np.pi, m), rng.uniform(0.0, np.pi, m))
+
+
 def paper_theta12_scan(n=314):
     """Sec. 3C, Fig. 7: the (theta1, theta2) plane, both from 0 in steps of 0.01
     (314 x 314 orbits), (beta, r, p) = (1, 10.14, 0.365), chi = 1."""
