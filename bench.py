@@ -67,14 +67,13 @@ FP64_PEAK_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # for the kernel sources they were taken with: reported as null once any of
 # these files differs from the recorded SHA-256.
 TRAFFIC_SOURCES = {
-    "paper_1802_00147_gb300/csrc/pn_device.cuh": "1ba3eb6333bd1e411f267c0bc37fa71ffb149ce0d367828de1004ef0516033f3",
-    "paper_1802_00147_gb300/csrc/pn_kernels.cu": "e5a0d16a1bb8bfffbae00d40bf2737be6f36f56eee4c40ea8cc094d9ad33477c",
+    "paper_1802_00147_gb300/csrc/pn_device.cuh": "e22fe987286c9d7ba0e9e1905bce0a69aaf9bcb652a8aaae78be78dd8fb03e9f",
+    "paper_1802_00147_gb300/csrc/pn_kernels.cu": "84935a0453daa6cb20d1bc396c23cef73dd06325d31f203d88ac27a8ea2dde4e",
     "paper_1802_00147_gb300/csrc/pn_kernels.cuh": "b96896c16a4511134e2587dfacf70a1be233dedbea094e41872b6caf91cdbc00",
 }
 # ncu --cache-control none, as the bench runs: the set-up kernels leave the
 # state in L2 right before the run.
-TRAFFIC_BYTES_PER_RUN = {2: 5017344 + 36455680,      # work-queue schedule, chunk 125
-                         3: 5540096 + 14816000}      # compacting schedule, chunk 62 (7 epochs)
+TRAFFIC_BYTES_PER_RUN = {3: 7345920 + 42324992}      # compacting schedule, chunk 62 (7 epochs)
 
 
 def traffic_per_run(schedule):
@@ -499,7 +498,11 @@ def run_ours(args, rank, world, local_rank):
     dist = world > 1
     if dist:
         import torch.distributed as td
-    cells_h = workload(rank, args.orbits)
+    if args.profile and args.uneven:
+        # the uneven batch (or a seeded subset of it), for profiling only
+        cells_h = W.uneven_batch(args.orbits or 100_000, seed=3)
+    else:
+        cells_h = workload(rank, args.orbits)
     n = cells_h.shape[0]
     t_end = args.t_end
     dev = torch.device("cuda", local_rank)
@@ -511,6 +514,8 @@ def run_ours(args, rank, world, local_rank):
     prof_opts = dict(schedule=sched_code, chunk_steps=args.chunk, block_size=args.block) if args.profile else {}
     if args.profile and args.dissipative:
         prof_opts["radiation_reaction"] = 1
+    if args.profile and args.uneven:
+        prof_opts["fli_cap"] = 12.0
     scan = pn.Scan(cells_h[:, W.BETA], device=True, **prof_opts)
     scan.setup(cells_d)
     if args.profile:
@@ -672,6 +677,8 @@ def main():
                     help="time the device path only (no autotune, e2e or CPU leg) for ncu runs")
     ap.add_argument("--dissipative", action="store_true",
                     help="--profile runs with the 2.5PN radiation reaction")
+    ap.add_argument("--uneven", action="store_true",
+                    help="--profile runs on the uneven batch (--orbits of it; FLI cap 12)")
     args = ap.parse_args()
     spawn = launch_check(args.gpus, os.environ)
     if spawn:

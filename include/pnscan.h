@@ -306,9 +306,10 @@ int scan_waveform(scan_handle *h, double R, const double *P, const double *Q, do
 int scan_last_run_timing(scan_handle *h, double *ms, int *launches);
 
 /* Not in the paper: the measured denominator of the integrator's FP64
- * roofline.  Time iters x 8 x (256 threads on every SM) DFMA -- 8
- * independent chains per thread -- on the handle's stream and return the
- * achieved FP64 rate (TFLOP/s, 2 flops per DFMA).  Errors: ARG, OOM, CUDA. */
+ * roofline.  Time iters x 8 DFMA per thread -- 8 independent chains -- with
+ * one block of 128, 256 and 512 threads on every SM, on the handle's
+ * stream, and return the best achieved FP64 rate (TFLOP/s, 2 flops per
+ * DFMA).  Errors: ARG, OOM, CUDA. */
 int scan_fp64_peak(scan_handle *h, int iters, double *tflops);
 
 /* ---- reduction without run-time allocation ----

@@ -111,6 +111,11 @@ def _declare(L):
     L.orc_trace.argtypes = [dp, d, d, d, P(Config), d, i64, i64, dp]
     L.orc_trace.restype = i
     L.orc_max_threads.restype = i
+    try:
+        L.orc_ext_trace.argtypes = [dp, d, d, d, P(Config), d, i64, dp]
+        L.orc_ext_trace.restype = i
+    except AttributeError:      # an older build of the file, loaded for comparison
+        pass
     return L
 
 
@@ -277,6 +282,19 @@ def trace(y0, beta, h, nsteps, every=1, cfg=None, kappa1=1.0, kappa2=1.0):
     out = _np.zeros((m, 12))
     lib().orc_trace(_dp(y0), float(beta), float(kappa1), float(kappa2), _ct.byref(cfg),
                     float(h), int(nsteps), int(every), _dp(out))
+    return out
+
+
+def ext_trace(y0, beta, h, nsteps, cfg=None, kappa1=1.0, kappa2=1.0):
+    """Final state of one corrected trajectory (no FLI shadow) after nsteps,
+    computed in the library's arithmetic type (double, or long double in a
+    build_variant with -DORC_LONG_DOUBLE); double in and out."""
+    cfg = cfg or config()
+    y0 = _vec(y0)
+    out = _np.zeros(12)
+    if lib().orc_ext_trace(_dp(y0), float(beta), float(kappa1), float(kappa2), _ct.byref(cfg), float(h),
+                           int(nsteps), _dp(out)) != 0:
+        raise ValueError("orc_ext_trace rejected its arguments")
     return out
 
 

@@ -27,23 +27,24 @@
  * by the gauge-invariant circular-orbit energy in tests/test_oracle_pins.py.
  */
 #include "pn_oracle.h"
-#include <math.h>
+#include <tgmath.h> /* sqrt, fabs, log10 ... of the argument's type (double or long double) */
+#undef I             /* tgmath.h brings complex.h's imaginary unit; not used here */
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
 
 /* ---------------------------------------------------------------- vectors */
-static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
-static void cross3(const double *a, const double *b, double *c)
+static orc_real dot3(const orc_real *a, const orc_real *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const orc_real *a, const orc_real *b, orc_real *c)
 {
     c[0] = a[1] * b[2] - a[2] * b[1];
     c[1] = a[2] * b[0] - a[0] * b[2];
     c[2] = a[0] * b[1] - a[1] * b[0];
 }
-static double norm3(const double *a) { return sqrt(dot3(a, a)); }
+static orc_real norm3(const orc_real *a) { return sqrt(dot3(a, a)); }
 
-void orc_sys_init(orc_sys *s, double beta, double kappa1, double kappa2,
+void orc_sys_init(orc_sys *s, orc_real beta, orc_real kappa1, orc_real kappa2,
                   int pn_order, int use_so, int use_ss, int use_qm)
 {
     /* Sec. 2: m1 <= m2, beta = m1/m2, M = m1 + m2 = 1, eta = mu/M = m1 m2. */
@@ -61,18 +62,18 @@ void orc_sys_init(orc_sys *s, double beta, double kappa1, double kappa2,
 
 /* ------------------------------------------------------------ Hamiltonian */
 /* H_N = p^2/2 - 1/r */
-double orc_H_newton(const orc_sys *s, const double y[12])
+orc_real orc_H_newton(const orc_sys *s, const orc_real y[12])
 {
     (void)s;
-    const double *r = y, *p = y + 3;
+    const orc_real *r = y, *p = y + 3;
     return 0.5 * dot3(p, p) - 1.0 / norm3(r);
 }
 
 /* H_1PN = (3 eta - 1) p^4 / 8 - [(3 + eta) p^2 + eta (n.p)^2] / (2 r) + 1/(2 r^2) */
-double orc_H_1pn(const orc_sys *s, const double y[12])
+orc_real orc_H_1pn(const orc_sys *s, const orc_real y[12])
 {
-    const double *r = y, *p = y + 3;
-    double eta = s->eta, rr = norm3(r), p2 = dot3(p, p), np = dot3(r, p) / rr;
+    const orc_real *r = y, *p = y + 3;
+    orc_real eta = s->eta, rr = norm3(r), p2 = dot3(p, p), np = dot3(r, p) / rr;
     return (3.0 * eta - 1.0) * p2 * p2 / 8.0
          - ((3.0 + eta) * p2 + eta * np * np) / (2.0 * rr)
          + 1.0 / (2.0 * rr * rr);
@@ -82,10 +83,10 @@ double orc_H_1pn(const orc_sys *s, const double y[12])
  *       + [(5 - 20 eta - 3 eta^2) p^4 - 2 eta^2 p^2 (n.p)^2 - 3 eta^2 (n.p)^4] / (8 r)
  *       + [(5 + 8 eta) p^2 + 3 eta (n.p)^2] / (2 r^2)
  *       - (1 + 3 eta) / (4 r^3) */
-double orc_H_2pn(const orc_sys *s, const double y[12])
+orc_real orc_H_2pn(const orc_sys *s, const orc_real y[12])
 {
-    const double *r = y, *p = y + 3;
-    double eta = s->eta, rr = norm3(r), p2 = dot3(p, p), np = dot3(r, p) / rr;
+    const orc_real *r = y, *p = y + 3;
+    orc_real eta = s->eta, rr = norm3(r), p2 = dot3(p, p), np = dot3(r, p) / rr;
     return (1.0 - 5.0 * eta + 5.0 * eta * eta) * p2 * p2 * p2 / 16.0
          + ((5.0 - 20.0 * eta - 3.0 * eta * eta) * p2 * p2
             - 2.0 * eta * eta * p2 * np * np
@@ -95,42 +96,42 @@ double orc_H_2pn(const orc_sys *s, const double y[12])
 }
 
 /* Spin-orbit coefficients read off the L/r^3 terms of Eqs. 8-9. */
-static double g_so1(const orc_sys *s) { return 2.0 + 3.0 / (2.0 * s->beta); }
-static double g_so2(const orc_sys *s) { return 2.0 + 3.0 * s->beta / 2.0; }
+static orc_real g_so1(const orc_sys *s) { return 2.0 + 3.0 / (2.0 * s->beta); }
+static orc_real g_so2(const orc_sys *s) { return 2.0 + 3.0 * s->beta / 2.0; }
 
 /* H_SO = (1/r^3) L . [(2 + 3/(2 beta)) S1 + (2 + 3 beta/2) S2],  L = r x p */
-double orc_H_so(const orc_sys *s, const double y[12])
+orc_real orc_H_so(const orc_sys *s, const orc_real y[12])
 {
-    const double *r = y, *p = y + 3, *S1 = y + 6, *S2 = y + 9;
-    double L[3], rr = norm3(r);
+    const orc_real *r = y, *p = y + 3, *S1 = y + 6, *S2 = y + 9;
+    orc_real L[3], rr = norm3(r);
     cross3(r, p, L);
     return (g_so1(s) * dot3(L, S1) + g_so2(s) * dot3(L, S2)) / (rr * rr * rr);
 }
 
 /* Eq. 3 with the 1/eta of Eqs. 8-9:  H_S1S2 = [3 (S1.n)(S2.n) - S1.S2] / (eta r^3) */
-double orc_H_s1s2(const orc_sys *s, const double y[12])
+orc_real orc_H_s1s2(const orc_sys *s, const orc_real y[12])
 {
-    const double *r = y, *S1 = y + 6, *S2 = y + 9;
-    double rr = norm3(r), n[3] = {r[0] / rr, r[1] / rr, r[2] / rr};
+    const orc_real *r = y, *S1 = y + 6, *S2 = y + 9;
+    orc_real rr = norm3(r), n[3] = {r[0] / rr, r[1] / rr, r[2] / rr};
     return (3.0 * dot3(S1, n) * dot3(S2, n) - dot3(S1, S2)) / (s->eta * rr * rr * rr);
 }
 
 /* Eqs. 4-5 with the 1/eta of Eqs. 8-9 and multipliers kappa_i:
  * H_QM = kappa1 [3 (S1.n)^2 - S1^2] / (2 beta eta r^3)
  *      + kappa2 beta [3 (S2.n)^2 - S2^2] / (2 eta r^3) */
-double orc_H_qm(const orc_sys *s, const double y[12])
+orc_real orc_H_qm(const orc_sys *s, const orc_real y[12])
 {
-    const double *r = y, *S1 = y + 6, *S2 = y + 9;
-    double rr = norm3(r), n[3] = {r[0] / rr, r[1] / rr, r[2] / rr};
-    double a1 = dot3(S1, n), a2 = dot3(S2, n), r3 = rr * rr * rr;
+    const orc_real *r = y, *S1 = y + 6, *S2 = y + 9;
+    orc_real rr = norm3(r), n[3] = {r[0] / rr, r[1] / rr, r[2] / rr};
+    orc_real a1 = dot3(S1, n), a2 = dot3(S2, n), r3 = rr * rr * rr;
     return s->kappa1 * (3.0 * a1 * a1 - dot3(S1, S1)) / (2.0 * s->beta * s->eta * r3)
          + s->kappa2 * s->beta * (3.0 * a2 * a2 - dot3(S2, S2)) / (2.0 * s->eta * r3);
 }
 
 /* Eq. 1 (conservative part, 3PN not given). */
-double orc_hamiltonian(const orc_sys *s, const double y[12])
+orc_real orc_hamiltonian(const orc_sys *s, const orc_real y[12])
 {
-    double H = orc_H_newton(s, y);
+    orc_real H = orc_H_newton(s, y);
     if (s->pn_order >= 1) H += orc_H_1pn(s, y);
     if (s->pn_order >= 2) H += orc_H_2pn(s, y);
     if (s->use_so) H += orc_H_so(s, y);
@@ -144,13 +145,13 @@ double orc_hamiltonian(const orc_sys *s, const double y[12])
  *   dH/dp = 2 H_p2 p + H_np n
  *   dH/dr = H_rr n + H_np (p - np n) / rr
  * Spin terms are differentiated directly, with d(S.n)/dr = (S - (S.n) n)/rr. */
-void orc_gradient(const orc_sys *s, const double y[12], double g[12])
+void orc_gradient(const orc_sys *s, const orc_real y[12], orc_real g[12])
 {
-    const double *r = y, *p = y + 3, *S1 = y + 6, *S2 = y + 9;
-    double eta = s->eta;
-    double rr = norm3(r), n[3] = {r[0] / rr, r[1] / rr, r[2] / rr};
-    double p2 = dot3(p, p), np = dot3(n, p);
-    double H_p2, H_np, H_rr;
+    const orc_real *r = y, *p = y + 3, *S1 = y + 6, *S2 = y + 9;
+    orc_real eta = s->eta;
+    orc_real rr = norm3(r), n[3] = {r[0] / rr, r[1] / rr, r[2] / rr};
+    orc_real p2 = dot3(p, p), np = dot3(n, p);
+    orc_real H_p2, H_np, H_rr;
     int i;
 
     /* H_N */
@@ -165,7 +166,7 @@ void orc_gradient(const orc_sys *s, const double y[12], double g[12])
     }
     /* H_2PN */
     if (s->pn_order >= 2) {
-        double c4 = 5.0 - 20.0 * eta - 3.0 * eta * eta;
+        orc_real c4 = 5.0 - 20.0 * eta - 3.0 * eta * eta;
         H_p2 += 3.0 * (1.0 - 5.0 * eta + 5.0 * eta * eta) * p2 * p2 / 16.0
               + (2.0 * c4 * p2 - 2.0 * eta * eta * np * np) / (8.0 * rr)
               + (5.0 + 8.0 * eta) / (2.0 * rr * rr);
@@ -185,12 +186,12 @@ void orc_gradient(const orc_sys *s, const double y[12], double g[12])
 
     if (s->use_so) {
         /* H_SO = (L . Seff) / rr^3 with L . Seff = p . (Seff x r) = r . (p x Seff) */
-        double Seff[3], L[3], Sxr[3], pxS[3], r3 = rr * rr * rr, g1 = g_so1(s), g2 = g_so2(s);
+        orc_real Seff[3], L[3], Sxr[3], pxS[3], r3 = rr * rr * rr, g1 = g_so1(s), g2 = g_so2(s);
         for (i = 0; i < 3; i++) Seff[i] = g1 * S1[i] + g2 * S2[i];
         cross3(r, p, L);
         cross3(Seff, r, Sxr);
         cross3(p, Seff, pxS);
-        double LS = dot3(L, Seff);
+        orc_real LS = dot3(L, Seff);
         for (i = 0; i < 3; i++) {
             g[i] += pxS[i] / r3 - 3.0 * LS * n[i] / (r3 * rr);
             g[3 + i] += Sxr[i] / r3;
@@ -199,8 +200,8 @@ void orc_gradient(const orc_sys *s, const double y[12], double g[12])
         }
     }
     if (s->use_ss) {
-        double a1 = dot3(S1, n), a2 = dot3(S2, n), S12 = dot3(S1, S2);
-        double k = 1.0 / (eta * rr * rr * rr);
+        orc_real a1 = dot3(S1, n), a2 = dot3(S2, n), S12 = dot3(S1, S2);
+        orc_real k = 1.0 / (eta * rr * rr * rr);
         for (i = 0; i < 3; i++) {
             g[i] += -3.0 * k * (3.0 * a1 * a2 - S12) * n[i] / rr
                   + 3.0 * k * (a2 * (S1[i] - a1 * n[i]) + a1 * (S2[i] - a2 * n[i])) / rr;
@@ -209,9 +210,9 @@ void orc_gradient(const orc_sys *s, const double y[12], double g[12])
         }
     }
     if (s->use_qm) {
-        double a1 = dot3(S1, n), a2 = dot3(S2, n), r3 = rr * rr * rr;
-        double q1 = s->kappa1 / (2.0 * s->beta * eta), q2 = s->kappa2 * s->beta / (2.0 * eta);
-        double Q = q1 * (3.0 * a1 * a1 - dot3(S1, S1)) + q2 * (3.0 * a2 * a2 - dot3(S2, S2));
+        orc_real a1 = dot3(S1, n), a2 = dot3(S2, n), r3 = rr * rr * rr;
+        orc_real q1 = s->kappa1 / (2.0 * s->beta * eta), q2 = s->kappa2 * s->beta / (2.0 * eta);
+        orc_real Q = q1 * (3.0 * a1 * a1 - dot3(S1, S1)) + q2 * (3.0 * a2 * a2 - dot3(S2, S2));
         for (i = 0; i < 3; i++) {
             g[i] += -3.0 * Q * n[i] / (r3 * rr)
                   + (6.0 * q1 * a1 * (S1[i] - a1 * n[i]) + 6.0 * q2 * a2 * (S2[i] - a2 * n[i])) / (r3 * rr);
@@ -222,9 +223,9 @@ void orc_gradient(const orc_sys *s, const double y[12], double g[12])
 }
 
 /* ------------------------------------------------------ equations of motion */
-void orc_rhs(const orc_sys *s, const double y[12], double dy[12])
+void orc_rhs(const orc_sys *s, const orc_real y[12], orc_real dy[12])
 {
-    double g[12];
+    orc_real g[12];
     int i;
     orc_gradient(s, y, g);
     for (i = 0; i < 3; i++) {
@@ -236,9 +237,9 @@ void orc_rhs(const orc_sys *s, const double y[12], double dy[12])
 }
 
 /* Classical fourth-order Runge-Kutta step. */
-void orc_rk4_step(const orc_sys *s, double y[12], double h)
+void orc_rk4_step(const orc_sys *s, orc_real y[12], orc_real h)
 {
-    double k1[12], k2[12], k3[12], k4[12], tmp[12];
+    orc_real k1[12], k2[12], k3[12], k4[12], tmp[12];
     int i;
     orc_rhs(s, y, k1);
     for (i = 0; i < 12; i++) tmp[i] = y[i] + 0.5 * h * k1[i];
@@ -252,18 +253,18 @@ void orc_rk4_step(const orc_sys *s, double y[12], double h)
 
 /* Fifth-order explicit Runge-Kutta step with the tableau of Dormand & Prince
  * (1980), fifth-order weights, fixed step (the paper's RK5 is not named). */
-void orc_rk5_step(const orc_sys *s, double y[12], double h)
+void orc_rk5_step(const orc_sys *s, orc_real y[12], orc_real h)
 {
-    static const double a21 = 1.0 / 5.0;
-    static const double a31 = 3.0 / 40.0, a32 = 9.0 / 40.0;
-    static const double a41 = 44.0 / 45.0, a42 = -56.0 / 15.0, a43 = 32.0 / 9.0;
-    static const double a51 = 19372.0 / 6561.0, a52 = -25360.0 / 2187.0, a53 = 64448.0 / 6561.0,
+    static const orc_real a21 = 1.0 / 5.0;
+    static const orc_real a31 = 3.0 / 40.0, a32 = 9.0 / 40.0;
+    static const orc_real a41 = 44.0 / 45.0, a42 = -56.0 / 15.0, a43 = 32.0 / 9.0;
+    static const orc_real a51 = 19372.0 / 6561.0, a52 = -25360.0 / 2187.0, a53 = 64448.0 / 6561.0,
                         a54 = -212.0 / 729.0;
-    static const double a61 = 9017.0 / 3168.0, a62 = -355.0 / 33.0, a63 = 46732.0 / 5247.0,
+    static const orc_real a61 = 9017.0 / 3168.0, a62 = -355.0 / 33.0, a63 = 46732.0 / 5247.0,
                         a64 = 49.0 / 176.0, a65 = -5103.0 / 18656.0;
-    static const double b1 = 35.0 / 384.0, b3 = 500.0 / 1113.0, b4 = 125.0 / 192.0,
+    static const orc_real b1 = 35.0 / 384.0, b3 = 500.0 / 1113.0, b4 = 125.0 / 192.0,
                         b5 = -2187.0 / 6784.0, b6 = 11.0 / 84.0;
-    double k1[12], k2[12], k3[12], k4[12], k5[12], k6[12], t[12];
+    orc_real k1[12], k2[12], k3[12], k4[12], k5[12], k6[12], t[12];
     int i;
     orc_rhs(s, y, k1);
     for (i = 0; i < 12; i++) t[i] = y[i] + h * (a21 * k1[i]);
@@ -291,12 +292,12 @@ void orc_rk5_step(const orc_sys *s, double y[12], double h)
  * the harmonic-gauge force.  For every (ga, gb) the losses of energy and
  * angular momentum averaged over a Kepler orbit are those of the quadrupole
  * formula (Peters & Mathews 1963), which the tests check. */
-void orc_rr_accel(const orc_sys *s, double ga, double gb, const double y[12], double a[3])
+void orc_rr_accel(const orc_sys *s, orc_real ga, orc_real gb, const orc_real y[12], orc_real a[3])
 {
-    const double *r = y, *v = y + 3;
-    double rr = norm3(r);
-    double u = 1.0 / rr;
-    double n[3], nv, v2, A, B, k;
+    const orc_real *r = y, *v = y + 3;
+    orc_real rr = norm3(r);
+    orc_real u = 1.0 / rr;
+    orc_real n[3], nv, v2, A, B, k;
     int i;
     for (i = 0; i < 3; i++) n[i] = r[i] / rr;
     nv = dot3(n, v);
@@ -312,9 +313,9 @@ void orc_rr_accel(const orc_sys *s, double ga, double gb, const double y[12], do
  *       = (dH/dp).a  (the conservative parts cancel, Omega_i.(Omega_i x S_i) = 0),
  * and dJ/dt = r x a (the conservative flow conserves J = L + S1 + S2), so
  * d|J|/dt = J.(r x a)/|J|: the integral-invariant relations of Sec. 3B. */
-void orc_rhs_rr(const orc_sys *s, double ga, double gb, const double y[14], double dy[14])
+void orc_rhs_rr(const orc_sys *s, orc_real ga, orc_real gb, const orc_real y[14], orc_real dy[14])
 {
-    double g[12], a[3], L[3], J[3], ra[3];
+    orc_real g[12], a[3], L[3], J[3], ra[3];
     int i;
     orc_gradient(s, y, g);
     orc_rr_accel(s, ga, gb, y, a);
@@ -333,20 +334,20 @@ void orc_rhs_rr(const orc_sys *s, double ga, double gb, const double y[14], doub
 
 /* The RK4 and fifth-order steps of orc_rk4_step / orc_rk5_step on the
  * 14-component system orc_rhs_rr. */
-void orc_rk_step_rr(const orc_sys *s, double ga, double gb, int rk_order, double y[14], double h)
+void orc_rk_step_rr(const orc_sys *s, orc_real ga, orc_real gb, int rk_order, orc_real y[14], orc_real h)
 {
     int i;
     if (rk_order == 5) {
-        static const double a21 = 1.0 / 5.0;
-        static const double a31 = 3.0 / 40.0, a32 = 9.0 / 40.0;
-        static const double a41 = 44.0 / 45.0, a42 = -56.0 / 15.0, a43 = 32.0 / 9.0;
-        static const double a51 = 19372.0 / 6561.0, a52 = -25360.0 / 2187.0, a53 = 64448.0 / 6561.0,
+        static const orc_real a21 = 1.0 / 5.0;
+        static const orc_real a31 = 3.0 / 40.0, a32 = 9.0 / 40.0;
+        static const orc_real a41 = 44.0 / 45.0, a42 = -56.0 / 15.0, a43 = 32.0 / 9.0;
+        static const orc_real a51 = 19372.0 / 6561.0, a52 = -25360.0 / 2187.0, a53 = 64448.0 / 6561.0,
                             a54 = -212.0 / 729.0;
-        static const double a61 = 9017.0 / 3168.0, a62 = -355.0 / 33.0, a63 = 46732.0 / 5247.0,
+        static const orc_real a61 = 9017.0 / 3168.0, a62 = -355.0 / 33.0, a63 = 46732.0 / 5247.0,
                             a64 = 49.0 / 176.0, a65 = -5103.0 / 18656.0;
-        static const double b1 = 35.0 / 384.0, b3 = 500.0 / 1113.0, b4 = 125.0 / 192.0,
+        static const orc_real b1 = 35.0 / 384.0, b3 = 500.0 / 1113.0, b4 = 125.0 / 192.0,
                             b5 = -2187.0 / 6784.0, b6 = 11.0 / 84.0;
-        double k1[14], k2[14], k3[14], k4[14], k5[14], k6[14], t[14];
+        orc_real k1[14], k2[14], k3[14], k4[14], k5[14], k6[14], t[14];
         orc_rhs_rr(s, ga, gb, y, k1);
         for (i = 0; i < 14; i++) t[i] = y[i] + h * (a21 * k1[i]);
         orc_rhs_rr(s, ga, gb, t, k2);
@@ -362,7 +363,7 @@ void orc_rk_step_rr(const orc_sys *s, double ga, double gb, int rk_order, double
         for (i = 0; i < 14; i++)
             y[i] = y[i] + h * (b1 * k1[i] + b3 * k3[i] + b4 * k4[i] + b5 * k5[i] + b6 * k6[i]);
     } else {
-        double k1[14], k2[14], k3[14], k4[14], tmp[14];
+        orc_real k1[14], k2[14], k3[14], k4[14], tmp[14];
         orc_rhs_rr(s, ga, gb, y, k1);
         for (i = 0; i < 14; i++) tmp[i] = y[i] + 0.5 * h * k1[i];
         orc_rhs_rr(s, ga, gb, tmp, k2);
@@ -375,9 +376,9 @@ void orc_rk_step_rr(const orc_sys *s, double ga, double gb, int rk_order, double
 }
 
 /* --------------------------------------------------------------- integrals */
-void orc_integrals(const orc_sys *s, const double y[12], double out[7])
+void orc_integrals(const orc_sys *s, const orc_real y[12], orc_real out[7])
 {
-    double L[3], J[3];
+    orc_real L[3], J[3];
     int i;
     cross3(y, y + 3, L);
     for (i = 0; i < 3; i++) J[i] = L[i] + y[6 + i] + y[9 + i]; /* J = L + S1 + S2 */
@@ -399,10 +400,10 @@ void orc_integrals(const orc_sys *s, const double y[12], double out[7])
  *     h_cross = (P_i Q_j + Q_i P_j) h_ij / 2,
  * P, Q the unit vectors of the radiation frame orthogonal to N (the
  * contraction with them takes the transverse-traceless part). */
-void orc_waveform(const orc_sys *s, const double y[12], double R, const double P[3], const double Q[3],
-                  double out[2])
+void orc_waveform(const orc_sys *s, const orc_real y[12], orc_real R, const orc_real P[3], const orc_real Q[3],
+                  orc_real out[2])
 {
-    double g[12], h[3][3], r, hp = 0.0, hc = 0.0;
+    orc_real g[12], h[3][3], r, hp = 0.0, hc = 0.0;
     int i, j;
     orc_gradient(s, y, g);                 /* g[3..5] = dH/dp = dr/dt */
     r = norm3(y);
@@ -419,9 +420,9 @@ void orc_waveform(const orc_sys *s, const double y[12], double R, const double P
 }
 
 /* ------------------------------------------------------ manifold correction */
-int orc_correct(const orc_sys *s, double y[12], const double ref[4],
-                double newton_tol, int newton_max, double det_min,
-                int *iters, double alpha_beta[2])
+int orc_correct(const orc_sys *s, orc_real y[12], const orc_real ref[4],
+                orc_real newton_tol, int newton_max, orc_real det_min,
+                int *iters, orc_real alpha_beta[2])
 {
     return orc_correct_rule(s, y, ref, newton_tol, newton_max, det_min, 0.0, 0.0, 1, ORC_MODE_DUAL, iters,
                             alpha_beta);
@@ -432,11 +433,11 @@ int orc_correct(const orc_sys *s, double y[12], const double ref[4],
  * y holds (r*, p*, S); returns 0 and the step (da, db) to subtract, or -1
  * where the dual scaling is singular (|det| <= det_min (|J11 J22| + |J12 J21|))
  * or not finite. */
-static int dual_newton_step(const orc_sys *s, const double y[12], const double ref[4], double alpha,
-                            double beta, double det_min, double *da, double *db)
+static int dual_newton_step(const orc_sys *s, const orc_real y[12], const orc_real ref[4], orc_real alpha,
+                            orc_real beta, orc_real det_min, orc_real *da, orc_real *db)
 {
-    double yb[12], g[12], rs[3], ps[3];
-    double J[3], rxp[3], rsxp[3], rxps[3], Jn, F1, F2, A, B, C, D, det;
+    orc_real yb[12], g[12], rs[3], ps[3];
+    orc_real J[3], rxp[3], rsxp[3], rxps[3], Jn, F1, F2, A, B, C, D, det;
     int i;
     memcpy(yb, y, sizeof(yb));
     for (i = 0; i < 3; i++) {
@@ -478,11 +479,11 @@ static int dual_newton_step(const orc_sys *s, const double y[12], const double r
  * is triangular.  It is singular where the radial part vanishes (turning
  * points, circular orbits) or L*.J = 0; -1 is returned there, below det_min
  * of the row or column it is compared with, or if not finite. */
-static int split_newton_step(const orc_sys *s, const double y[12], const double ref[4],
-                             const double pt[3], const double pr[3], double a, double g,
-                             double split_min, double *da, double *dg)
+static int split_newton_step(const orc_sys *s, const orc_real y[12], const orc_real ref[4],
+                             const orc_real pt[3], const orc_real pr[3], orc_real a, orc_real g,
+                             orc_real split_min, orc_real *da, orc_real *dg)
 {
-    double yb[12], grad[12], J[3], L[3], Ls[3], Jn, F1, F2, A, B, C;
+    orc_real yb[12], grad[12], J[3], L[3], Ls[3], Jn, F1, F2, A, B, C;
     int i;
     memcpy(yb, y, sizeof(yb));
     for (i = 0; i < 3; i++) yb[3 + i] = a * pt[i] + g * pr[i];
@@ -504,10 +505,10 @@ static int split_newton_step(const orc_sys *s, const double y[12], const double 
     return 0;
 }
 
-int orc_newton_trace(const orc_sys *s, const double y[12], const double ref[4], int kmax,
-                     double *alpha, double *beta)
+int orc_newton_trace(const orc_sys *s, const orc_real y[12], const orc_real ref[4], int kmax,
+                     orc_real *alpha, orc_real *beta)
 {
-    double a = 1.0, b = 1.0, da, db;
+    orc_real a = 1.0, b = 1.0, da, db;
     int k;
     for (k = 0; k < kmax; k++) {
         if (dual_newton_step(s, y, ref, a, b, 0.0, &da, &db)) break;
@@ -524,10 +525,10 @@ int orc_newton_trace(const orc_sys *s, const double y[12], const double ref[4], 
  * A = p*.dH/dp and B = r*.dH/dr (its two |J| derivatives are equal there);
  * and the split scaling's |p_r.dH/dp| / (|p_t.dH/dp| + |p_r.dH/dp|), or 0
  * where its |J| row is degenerate (|L*.J|/|J| <= split_min |L*|). */
-static void conditioning(const orc_sys *s, const double y[12], double split_min, double *c_dual,
-                         double *c_split)
+static void conditioning(const orc_sys *s, const orc_real y[12], orc_real split_min, orc_real *c_dual,
+                         orc_real *c_split)
 {
-    double g[12], pr[3], pt[3], L[3], J[3], A, B, As, Bs, rn, np_;
+    orc_real g[12], pr[3], pt[3], L[3], J[3], A, B, As, Bs, rn, np_;
     int i;
     orc_gradient(s, y, g);
     A = dot3(g + 3, y + 3);
@@ -549,17 +550,17 @@ static void conditioning(const orc_sys *s, const double y[12], double split_min,
     if (!isfinite(*c_split)) *c_split = 0.0;
 }
 
-int orc_correct_rule(const orc_sys *s, double y[12], const double ref[4],
-                     double newton_tol, int newton_max, double det_min, double split_min,
-                     double cond_switch, int apply_small, int mode, int *iters, double alpha_beta[2])
+int orc_correct_rule(const orc_sys *s, orc_real y[12], const orc_real ref[4],
+                     orc_real newton_tol, int newton_max, orc_real det_min, orc_real split_min,
+                     orc_real cond_switch, int apply_small, int mode, int *iters, orc_real alpha_beta[2])
 {
-    double rs[3], ps[3], yb[12];
-    double alpha = 1.0, beta = 1.0;
+    orc_real rs[3], ps[3], yb[12];
+    orc_real alpha = 1.0, beta = 1.0;
     int it = 0, i, converged = 0, prefer_split = 0;
 
     /* Eq. 10: restore both spin lengths (skipped for a zero-length spin). */
     for (i = 0; i < 2; i++) {
-        double *S = y + 6 + 3 * i, len = norm3(S);
+        orc_real *S = y + 6 + 3 * i, len = norm3(S);
         if (ref[2 + i] > 0.0 && len > 0.0) {
             S[0] = S[0] * (ref[2 + i] / len);
             S[1] = S[1] * (ref[2 + i] / len);
@@ -592,12 +593,12 @@ int orc_correct_rule(const orc_sys *s, double y[12], const double ref[4],
      * inverse conditioning, and kicks that differ between the two FLI
      * trajectories would masquerade as divergence. */
     if (mode == ORC_MODE_DUAL && cond_switch > 0.0 && split_min > 0.0) {
-        double cd, cs;
+        orc_real cd, cs;
         conditioning(s, y, split_min, &cd, &cs);
         if (cd <= cond_switch && cs > cd && cs > split_min) prefer_split = 1;
     }
     for (it = 1; mode == ORC_MODE_DUAL && !prefer_split && it <= newton_max; it++) {
-        double da, db;
+        orc_real da, db;
         if (dual_newton_step(s, y, ref, alpha, beta, det_min, &da, &db)) break;
         /* stopping rule: apply the step and then test it (default), or stop
          * before applying a step already within the tolerance */
@@ -633,14 +634,14 @@ int orc_correct_rule(const orc_sys *s, double y[12], const double ref[4],
      * p*.dH/dp = r*.dH/dr (for a Kepler ellipse at r = a, where
      * |p_r| / |p| = e), away from the turning points where this one is. */
     if (mode == ORC_MODE_DUAL && split_min > 0.0) {
-        double pt[3], pr[3], rn = norm3(rs), np_ = dot3(rs, ps) / rn, a = 1.0, g = 1.0;
+        orc_real pt[3], pr[3], rn = norm3(rs), np_ = dot3(rs, ps) / rn, a = 1.0, g = 1.0;
         int k, ok = 0;
         for (i = 0; i < 3; i++) {
             pr[i] = np_ * (rs[i] / rn);
             pt[i] = ps[i] - pr[i];
         }
         for (k = 1; k <= newton_max; k++) {
-            double da, dg;
+            orc_real da, dg;
             if (split_newton_step(s, y, ref, pt, pr, a, g, split_min, &da, &dg)) break;
             if (!apply_small && fabs(da) <= newton_tol && fabs(dg) <= newton_tol) {
                 ok = 1;
@@ -671,11 +672,11 @@ int orc_correct_rule(const orc_sys *s, double y[12], const double ref[4],
      * (the momentum-scaling correction of Sec. 1, Wu et al. 2007).  |J| is
      * left to the next step. */
     {
-        double a = 1.0, g2[12];
+        orc_real a = 1.0, g2[12];
         int k, ok = 0;
         memcpy(yb, y, sizeof(yb));
         for (k = 1; k <= newton_max; k++) {
-            double F, A, da;
+            orc_real F, A, da;
             for (i = 0; i < 3; i++) yb[3 + i] = a * ps[i];
             F = orc_hamiltonian(s, yb) - ref[0];
             orc_gradient(s, yb, g2);
@@ -705,11 +706,11 @@ int orc_correct_rule(const orc_sys *s, double y[12], const double ref[4],
 }
 
 /* ------------------------------------------------------------ cell set-up */
-void orc_setup_cell(const double cell[9], double y[12])
+void orc_setup_cell(const orc_real cell[9], orc_real y[12])
 {
-    double x0 = cell[0], pfac = cell[1];
-    double beta = cell[6], m1 = beta / (1.0 + beta), m2 = 1.0 / (1.0 + beta);
-    double s1 = cell[7] * m1 * m1, s2 = cell[8] * m2 * m2;
+    orc_real x0 = cell[0], pfac = cell[1];
+    orc_real beta = cell[6], m1 = beta / (1.0 + beta), m2 = 1.0 / (1.0 + beta);
+    orc_real s1 = cell[7] * m1 * m1, s2 = cell[8] * m2 * m2;
     y[0] = x0;
     y[1] = 0.0;
     y[2] = 0.0;
@@ -725,9 +726,9 @@ void orc_setup_cell(const double cell[9], double y[12])
 }
 
 /* ------------------------------------------------------------- integrator */
-static void reference_integrals(const orc_sys *s, const double y[12], double ref[4])
+static void reference_integrals(const orc_sys *s, const orc_real y[12], orc_real ref[4])
 {
-    double I[7];
+    orc_real I[7];
     orc_integrals(s, y, I);
     ref[0] = I[0];
     ref[1] = I[1];
@@ -735,7 +736,7 @@ static void reference_integrals(const orc_sys *s, const double y[12], double ref
     ref[3] = I[3];
 }
 
-static int all_finite(const double y[12])
+static int all_finite(const orc_real y[12])
 {
     int i;
     for (i = 0; i < 12; i++)
@@ -743,9 +744,9 @@ static int all_finite(const double y[12])
     return 1;
 }
 
-static double distance12(const double a[12], const double b[12])
+static orc_real distance12(const orc_real a[12], const orc_real b[12])
 {
-    double d2 = 0.0;
+    orc_real d2 = 0.0;
     int i;
     for (i = 0; i < 12; i++) d2 += (b[i] - a[i]) * (b[i] - a[i]);
     return sqrt(d2);
@@ -754,15 +755,15 @@ static double distance12(const double a[12], const double b[12])
 /* One integration step of a trajectory.  Without radiation reaction the
  * reference integrals stay fixed; with it, ref[0] = E and ref[1] = |J|
  * advance with the state by their integral-invariant relations. */
-static void step(const orc_config *cfg, const orc_sys *s, double y[12], double ref[4], double h)
+static void step(const orc_config *cfg, const orc_sys *s, orc_real y[12], orc_real ref[4], orc_real h)
 {
     if (cfg->rr) {
-        double y14[14];
-        memcpy(y14, y, 12 * sizeof(double));
+        orc_real y14[14];
+        memcpy(y14, y, 12 * sizeof(orc_real));
         y14[12] = ref[0];
         y14[13] = ref[1];
         orc_rk_step_rr(s, cfg->rr_gauge_a, cfg->rr_gauge_b, cfg->rk_order, y14, h);
-        memcpy(y, y14, 12 * sizeof(double));
+        memcpy(y, y14, 12 * sizeof(orc_real));
         ref[0] = y14[12];
         ref[1] = y14[13];
     } else if (cfg->rk_order == 5) {
@@ -772,19 +773,19 @@ static void step(const orc_config *cfg, const orc_sys *s, double y[12], double r
     }
 }
 
-static void integrate_one(const orc_config *cfg, const orc_sys *s, const double y0[12],
-                          double h, int64_t nsteps, double y[12], double ys[12],
-                          double integ[6], double *fli_out, int32_t *status_out,
-                          double *t_stop_out, int64_t *iters_out, int32_t *skip_out,
+static void integrate_one(const orc_config *cfg, const orc_sys *s, const orc_real y0[12],
+                          orc_real h, int64_t nsteps, orc_real y[12], orc_real ys[12],
+                          orc_real integ[6], orc_real *fli_out, int32_t *status_out,
+                          orc_real *t_stop_out, int64_t *iters_out, int32_t *skip_out,
                           int32_t *last_kind_out)
 {
-    double ref[4], refs[4], acc = 0.0, d0 = cfg->fli_d0;
+    orc_real ref[4], refs[4], acc = 0.0, d0 = cfg->fli_d0;
     int64_t k, iters = 0;
     int32_t st = ORC_DONE, skips = 0, last_kind = ORC_CORR_OK;
-    double t_stop = (double)nsteps * h;
+    orc_real t_stop = (orc_real)nsteps * h;
 
-    memcpy(y, y0, 12 * sizeof(double));
-    memcpy(ys, y0, 12 * sizeof(double));
+    memcpy(y, y0, 12 * sizeof(orc_real));
+    memcpy(ys, y0, 12 * sizeof(orc_real));
     ys[0] = ys[0] + d0; /* shadow displaced by d0 along x */
     reference_integrals(s, y, ref);
     reference_integrals(s, ys, refs);
@@ -806,24 +807,24 @@ static void integrate_one(const orc_config *cfg, const orc_sys *s, const double 
             iters += it;
         }
         /* termination tests on the main trajectory */
-        if (!all_finite(y) || !all_finite(ys)) { st = ORC_NONFINITE; t_stop = (double)k * h; break; }
+        if (!all_finite(y) || !all_finite(ys)) { st = ORC_NONFINITE; t_stop = (orc_real)k * h; break; }
         {
-            double rr = norm3(y);
-            if (cfg->r_merge > 0.0 && rr < cfg->r_merge) { st = ORC_MERGED; t_stop = (double)k * h; break; }
-            if (cfg->r_escape > 0.0 && rr > cfg->r_escape) { st = ORC_ESCAPED; t_stop = (double)k * h; break; }
+            orc_real rr = norm3(y);
+            if (cfg->r_merge > 0.0 && rr < cfg->r_merge) { st = ORC_MERGED; t_stop = (orc_real)k * h; break; }
+            if (cfg->r_escape > 0.0 && rr > cfg->r_escape) { st = ORC_ESCAPED; t_stop = (orc_real)k * h; break; }
         }
         /* FLI renormalisation every fli_renorm steps */
         if (cfg->fli_renorm > 0 && k % cfg->fli_renorm == 0) {
-            double d = distance12(y, ys);
+            orc_real d = distance12(y, ys);
             int i;
             acc += log10(d / d0);
             for (i = 0; i < 12; i++) ys[i] = y[i] + (d0 / d) * (ys[i] - y[i]);
             reference_integrals(s, ys, refs); /* the shadow keeps its own integrals */
-            if (cfg->fli_cap > 0.0 && acc >= cfg->fli_cap) { st = ORC_FLI_SATURATED; t_stop = (double)k * h; break; }
+            if (cfg->fli_cap > 0.0 && acc >= cfg->fli_cap) { st = ORC_FLI_SATURATED; t_stop = (orc_real)k * h; break; }
         }
     }
     {
-        double I[7];
+        orc_real I[7];
         orc_integrals(s, y, I);
         integ[0] = ref[0];
         integ[1] = I[0];
@@ -840,11 +841,11 @@ static void integrate_one(const orc_config *cfg, const orc_sys *s, const double 
     *last_kind_out = last_kind;
 }
 
-int orc_scan(int64_t n, const double *y0, const double *beta,
-             const double *kappa1, const double *kappa2,
-             const orc_config *cfg, double h, int64_t nsteps,
-             double *y_out, double *ys_out, double *integrals, double *fli,
-             int32_t *status, double *t_stop, int64_t *newton_iters,
+int orc_scan(int64_t n, const orc_real *y0, const orc_real *beta,
+             const orc_real *kappa1, const orc_real *kappa2,
+             const orc_config *cfg, orc_real h, int64_t nsteps,
+             orc_real *y_out, orc_real *ys_out, orc_real *integrals, orc_real *fli,
+             int32_t *status, orc_real *t_stop, int64_t *newton_iters,
              int32_t *n_skip, int32_t *last_kind, int nthreads)
 {
     int64_t i;
@@ -867,12 +868,12 @@ int orc_scan(int64_t n, const double *y0, const double *beta,
     return 0;
 }
 
-int orc_trace(const double y0[12], double beta, double kappa1, double kappa2,
-              const orc_config *cfg, double h, int64_t nsteps, int64_t every,
-              double *trace)
+int orc_trace(const orc_real y0[12], orc_real beta, orc_real kappa1, orc_real kappa2,
+              const orc_config *cfg, orc_real h, int64_t nsteps, int64_t every,
+              orc_real *trace)
 {
     orc_sys s;
-    double y[12], ref[4];
+    orc_real y[12], ref[4];
     int64_t k, m = 0;
     if (every <= 0 || !trace) return -1;
     orc_sys_init(&s, beta, kappa1, kappa2, cfg->pn_order, cfg->use_so, cfg->use_ss, cfg->use_qm);
@@ -889,6 +890,28 @@ int orc_trace(const double y0[12], double beta, double kappa1, double kappa2,
             m++;
         }
     }
+    return 0;
+}
+
+int orc_ext_trace(const double y0[12], double beta, double kappa1, double kappa2,
+                  const orc_config *cfg, double h, int64_t nsteps, double y_out[12])
+{
+    orc_sys s;
+    orc_real y[12], ref[4];
+    int64_t k;
+    int i;
+    if (!y0 || !cfg || !y_out || nsteps < 0) return -1;
+    orc_sys_init(&s, beta, kappa1, kappa2, cfg->pn_order, cfg->use_so, cfg->use_ss, cfg->use_qm);
+    for (i = 0; i < 12; i++) y[i] = y0[i];
+    reference_integrals(&s, y, ref);
+    for (k = 1; k <= nsteps; k++) {
+        int it;
+        step(cfg, &s, y, ref, h);
+        if (cfg->correct)
+            orc_correct_rule(&s, y, ref, cfg->newton_tol, cfg->newton_max, cfg->det_min,
+                             cfg->split_min, cfg->cond_switch, cfg->newton_apply_small, cfg->correct, &it, 0);
+    }
+    for (i = 0; i < 12; i++) y_out[i] = (double)y[i];
     return 0;
 }
 
