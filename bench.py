@@ -422,8 +422,13 @@ def run_adaptive_boundary():
     paper's scan, threshold 5.8): a plane with an order/chaos boundary."""
     from paper_1802_00147_gb300 import adaptive as A
     rep = A.boundary_study(n=512, t_end=1.0e4, thr=5.8, stride=8, r_merge=0.0, r_escape=0.0)
-    for k in ("surrogate", "baseline"):     # the sweeps stay out of the bench line: the chosen points go in
-        rep[k]["n_points"] = len(rep[k].pop("points"))
+    # the surrogate trained on the neighbouring planes only (x0 = 9.9 ... 10.4 at the same fraction of
+    # the circular momentum): no cell of the mapped plane is integrated before the map
+    tr = A.boundary_study(n=512, t_end=1.0e4, thr=5.8, stride=8, r_merge=0.0, r_escape=0.0,
+                          train_x0=(9.9, 10.0, 10.3, 10.4))
+    rep["surrogate_trained_on_other_planes"] = tr["surrogate"]
+    for r in (rep["surrogate"], rep["baseline"], rep["surrogate_trained_on_other_planes"]):
+        r["n_points"] = len(r.pop("points"))   # the sweeps stay out of the bench line: the chosen points go in
     return rep
 
 

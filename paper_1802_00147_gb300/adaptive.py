@@ -160,7 +160,7 @@ def cheapest(points, mis_max):
 
 def boundary_study(n=512, t_end=1.0e4, thr=5.8, stride=8, train_m=None, members=5, train_steps=30000,
                    bands=(0.25, 0.5, 1.0, 1.5, 2.0, 3.0), spread_maxes=(0.25, 0.5, 1.0, 2.0, float("inf")),
-                   mis_max=0.005, seed=11, target_clip=1.0, **opts):
+                   mis_max=0.005, seed=11, target_clip=1.0, train_x0=None, **opts):
     """Surrogate-adaptive map against the no-learning coarse-grid map on the
     (theta1, theta2) plane of Sec. 3C, Fig. 7 (workloads.theta12_plane),
     which has an order/chaos boundary.
@@ -188,7 +188,11 @@ def boundary_study(n=512, t_end=1.0e4, thr=5.8, stride=8, train_m=None, members=
     grid = W.theta12_plane(n)
     grid_d = torch.as_tensor(np.ascontiguousarray(grid[:, :9]), device="cuda")
     m = train_m or ((n - 1) // stride + 1) ** 2
-    train = W.theta12_random(m, seed)
+    if train_x0:
+        # transfer: training cells from the neighbouring planes only, none of the target plane
+        train = np.concatenate([W.theta12_random(m, seed + k, x0=x) for k, x in enumerate(train_x0)])
+    else:
+        train = W.theta12_random(m, seed)
     # warm-up of every path on tiny inputs (first use of a PyTorch comparison
     # or masked index loads its kernels)
     training_set([train[:32]], [10.0], fields=fields, **opts)
@@ -224,7 +228,8 @@ def boundary_study(n=512, t_end=1.0e4, thr=5.8, stride=8, train_m=None, members=
                                               "chi = 1 (Sec. 3C, Fig. 7)",
               "t_end": t_end, "thr": thr, "chaotic_frac": float(truth.float().mean().item()),
               "plain_s": full["seconds"], "mis_max": mis_max, "budget_cells": m,
-              "surrogate": {"train_cells": m, "members": members, "train_steps": train_steps, "target_clip": target_clip,
+              "surrogate": {"train_cells": int(train.shape[0]), "train_x0": list(train_x0) if train_x0 else None,
+                            "members": members, "train_steps": train_steps, "target_clip": target_clip,
                             "training_data_s": data_s, "train_s": train_s, "points": pts_s, "chosen": best_s},
               "baseline": {"stride": stride, "nodes": int(nodes.shape[0]), "points": pts_b, "chosen": best_b}}
     if best_s is not None:
@@ -236,7 +241,9 @@ def boundary_study(n=512, t_end=1.0e4, thr=5.8, stride=8, train_m=None, members=
             misclassification_all=float(wrong.float().mean().item()),
             misclassification_subset4096=float(wrong[sub_idx].float().mean().item()),
             speedup=full["seconds"] / res["seconds"],
-            cells_integrated=res["n_marked"] + m, seconds_total=res["seconds"] + train_s + data_s,
+            cells_integrated=res["n_marked"] + (0 if train_x0 else m),
+            training_cells_other_planes=int(train.shape[0]) if train_x0 else 0,
+            seconds_total=res["seconds"] + train_s + data_s,
             speedup_incl_training_and_data=full["seconds"] / (res["seconds"] + train_s + data_s))
     if best_b is not None:
         res = baseline_map(grid_d, n, n, stride, t_end, thr=thr, band=best_b["band"],

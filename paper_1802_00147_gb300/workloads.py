@@ -210,10 +210,13 @@ def theta12_plane(n):
     return paper_cells(10.14, 0.365, 1.0, T1.ravel(), T2.ravel())
 
 
-def theta12_random(m, seed):
-    """m cells of the same plane at seeded uniform (theta1, theta2) in [0, pi]^2."""
+def theta12_random(m, seed, x0=10.14):
+    """m cells of the same plane at seeded uniform (theta1, theta2) in [0, pi]^2;
+    with another x0, the neighbouring plane at that separation and the same
+    fraction of the circular momentum (p_y sqrt(x0) = 0.365 sqrt(10.14))."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    return paper_cells(10.14, 0.365, 1.0, rng.uniform(0.0, np.pi, m), rng.uniform(0.0, np.pi, m))
+    p_y = 0.365 * np.sqrt(10.14 / x0)
+    return paper_cells(x0, p_y, 1.0, rng.uniform(0.0, np.pi, m), rng.uniform(0.0, np.pi, m))
 
 
 def paper_theta12_scan(n=314):
