@@ -96,7 +96,12 @@ orc_real orc_H_2pn(const orc_sys *s, const orc_real y[12])
 }
 
 /* Spin-orbit coefficients read off the L/r^3 terms of Eqs. 8-9. */
-static orc_real g_so1(const orc_sys *s) { return 2.0 + 3.0 / (2.0 * s->beta); }
+/* Tests build a variant with a planted mistake here (-DORC_PLANTED_SO_FACTOR=...)
+ * to show that the parity bounds catch it; 1.0 (exact) otherwise. */
+#ifndef ORC_PLANTED_SO_FACTOR
+#define ORC_PLANTED_SO_FACTOR 1.0
+#endif
+static orc_real g_so1(const orc_sys *s) { return ORC_PLANTED_SO_FACTOR * (2.0 + 3.0 / (2.0 * s->beta)); }
 static orc_real g_so2(const orc_sys *s) { return 2.0 + 3.0 * s->beta / 2.0; }
 
 /* H_SO = (1/r^3) L . [(2 + 3/(2 beta)) S1 + (2 + 3 beta/2) S2],  L = r x p */

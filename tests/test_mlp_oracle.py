@@ -112,3 +112,44 @@ def test_batch_rows_are_uniform_and_distinct_per_member_and_step():
     a, b, c = M.batch_rows(99, 0, 1, n), M.batch_rows(99, 1, 1, n), M.batch_rows(99, 0, 2, n)
     assert not np.array_equal(a, b) and not np.array_equal(a, c)
     assert np.array_equal(a, M.batch_rows(99, 0, 1, n))
+
+
+def _adam_variant(p, g, m, v, step, lr, kind, beta1=0.9, beta2=0.999, eps=1e-8):
+    """adam_step with one planted mistake (for the criterion's power only)."""
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    if kind == "no_bias_correction":
+        mhat, vhat = m, v
+    elif kind == "step_from_zero":
+        mhat, vhat = m / (1.0 - beta1 ** (step + 1)), v / (1.0 - beta2 ** (step + 1))
+    else:
+        mhat, vhat = m / (1.0 - beta1 ** step), v / (1.0 - beta2 ** step)
+    if kind == "eps_inside_sqrt":
+        return p - lr * mhat / np.sqrt(vhat + eps), m, v
+    return p - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+@pytest.mark.parametrize("kind", ["no_bias_correction", "step_from_zero", "eps_inside_sqrt"])
+def test_adam_parity_criterion_catches_planted_mistakes(kind):
+    """The GPU Adam test's criterion -- >= 99 % of the parameter updates within
+    1e-3 lr per step of the oracle's, after 1 and 5 steps -- fails for an
+    update with a missing or mis-stepped bias correction or with eps inside
+    the square root, on gradients of the test's scale (the network's own
+    gradients of a random minibatch)."""
+    rng = np.random.default_rng(8)
+    p0 = rand_params(rng, 0.3)
+    z = rng.uniform(-1, 1, size=(128, 4))
+    t = 2.0 + rng.normal(size=128)
+    lr = 1e-3
+    caught = []
+    for steps in (1, 5):
+        p_ok, m_ok, v_ok = p0.copy(), np.zeros_like(p0), np.zeros_like(p0)
+        p_bad, m_bad, v_bad = p0.copy(), np.zeros_like(p0), np.zeros_like(p0)
+        for k in range(1, steps + 1):
+            _, g_ok = M.loss_and_grad(p_ok, z, t)
+            _, g_bad = M.loss_and_grad(p_bad, z, t)
+            p_ok, m_ok, v_ok = M.adam_step(p_ok, g_ok, m_ok, v_ok, k, lr)
+            p_bad, m_bad, v_bad = _adam_variant(p_bad, g_bad, m_bad, v_bad, k, lr, kind)
+        within = np.abs((p_bad - p0) - (p_ok - p0)) <= 1e-3 * lr * steps
+        caught.append(within.mean() < 0.99)
+    assert any(caught), kind

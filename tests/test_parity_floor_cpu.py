@@ -93,3 +93,26 @@ def test_fma_rounding_lies_within_the_per_orbit_floor(fma_lib, which, cond_switc
     idx = np.flatnonzero(done)[:2]
     assert np.all(o["refine_fli"](idx) >= o["s_fli_all"][idx])
     assert np.array_equal(f["fli"][done] > 6.0, o["fli"][done] > 6.0)
+
+
+@pytest.mark.slow
+def test_per_orbit_state_bound_catches_a_planted_mistake():
+    """The GPU parity bound err_i <= max(1e-10, 3 s_i) has power: an oracle
+    build whose spin-orbit coefficient (Eqs. 8-9's g1) is off by 1e-7
+    relative lands beyond it on every orbit of the small scan at t = 1000
+    (median error 1.2e-7), although it is the same program otherwise."""
+    cells = W.small_scan(seed=1)
+    nsteps = 1000
+    o = run(cells, nsteps)
+    y0 = oracle.setup_cells(cells[:, :9])
+    s_state, _, _ = ulp_spreads(
+        lambda y1, hh, idx, dd: run(cells if idx is None else cells[idx], nsteps, y0=y1, h=hh, d0=dd),
+        y0, o, (0, 4, 6), 1.0)
+    d = tempfile.mkdtemp()
+    planted = oracle.load_variant(ob.build_variant(os.path.join(d, "libpnoracle_planted.so"),
+                                                   ["-ffp-contract=off", "-DORC_PLANTED_SO_FACTOR=1.0000001"]))
+    with oracle.using(planted):
+        g = run(cells, nsteps)
+    ok = o["status"] != oracle.NONFINITE
+    err = block_relerr(g["y"][ok], o["y"][ok])
+    assert np.all(err > np.maximum(1e-10, 3 * s_state[ok])), np.sort(err)[:3]
