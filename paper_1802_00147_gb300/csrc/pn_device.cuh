@@ -711,7 +711,7 @@ __device__ __forceinline__ int correct(const C& c, Vec12& y, const Ref& ref,
             const double Bs = 2.0 * NP2 * (Hq1 + Hw1);
             prefer_split = fabs(Bs) * (fabs(p1) + fabs(p2)) > fabs(det) * (fabs(As) + fabs(Bs)) &&
                            fabs(Bs) > nc.split_min * (fabs(As) + fabs(Bs)) &&
-                           fabs(dJ) > nc.split_min * (LL * rsqrt(LL));
+                           dJ * dJ > (nc.split_min * nc.split_min) * LL;       // |dJ| > split_min |L*|
             if (prefer_split) {
                 // the split scaling's first Newton step at (1, 1): H, F and the
                 // |J| derivative are the dual scaling's at its own (1, 1)
@@ -794,7 +794,8 @@ __device__ __forceinline__ int correct(const C& c, Vec12& y, const Ref& ref,
     //       + R^2 (D1 q + D2 w) + a E1 + (B0 + C0 + D0),
     // and |J|^2 = a^2 LL + 2 a LJ + SSq.  Newton on (a, g) from (1, 1); the
     // Jacobian [[H_a, H_g], [J_a, 0]] is triangular.  It is used only where
-    // |H_g| > split_min (|H_a| + |H_g|) and |J_a| > split_min |L*|: near a
+    // |H_g| > split_min (|H_a| + |H_g|) and |J_a| > split_min |L*| (compared
+    // as squares): near a
     // circular orbit E and |J| cannot be moved independently, and it is as
     // ill-conditioned as the dual scaling.  State quantities are recomputed
     // from (r*, p*), which are still unchanged here.
@@ -807,7 +808,7 @@ __device__ __forceinline__ int correct(const C& c, Vec12& y, const Ref& ref,
         const double hq0 = fma(Rr, c[K_B1], fma(RR2, c[K_D1], 0.5));    // dH/dq at q = w = 0
         const double hw0 = fma(Rr, c[K_B2], RR2 * c[K_D2]);             // dH/dw at q = w = 0
         const double Hc = (B0 + C0) + D0;
-        const double Lmag = LL * rsqrt(LL);
+        const double smin2LL = (nc.split_min * nc.split_min) * LL;     // (split_min |L*|)^2
         while (!sok && ks < nc.max_iter) {
             ++ks;
             const double w = sg * sg * NP2s;
@@ -824,7 +825,7 @@ __device__ __forceinline__ int correct(const C& c, Vec12& y, const Ref& ref,
             const double Jn2 = fma(sa, fma(sa, LL, LJx2), SSq);
             const double rJ = rsqrt(Jn2);
             const double Ja = fma(sa, LL, LJ) * rJ;
-            if (!(fabs(Hg) > nc.split_min * (fabs(Ha) + fabs(Hg))) || !(fabs(Ja) > nc.split_min * Lmag))
+            if (!(fabs(Hg) > nc.split_min * (fabs(Ha) + fabs(Hg))) || !(Ja * Ja > smin2LL))
                 break;   // ill-conditioned (or NaN)
             const double F1 = H - ref.E;
             const double F2 = fma(Jn2, rJ, -ref.J);
@@ -841,13 +842,10 @@ __device__ __forceinline__ int correct(const C& c, Vec12& y, const Ref& ref,
             if (!(fabs(sa) < 1e300) || !(fabs(sg) < 1e300)) break;
         }
         if (sok) {
-            // p = a (p* - p_r) + g p_r, p_r = (n.p*) n = (NPs Rr) r*
-            const double f = NPs * Rr;
+            // p = a (p* - p_r) + g p_r = a p* + (g - a) p_r, p_r = (n.p*) n = (NPs Rr) r*
+            const double f = (sg - sa) * (NPs * Rr);
 #pragma unroll
-            for (int i = 0; i < 3; i++) {
-                const double pr = f * y.r[i];
-                y.p[i] = fma(sa, y.p[i] - pr, sg * pr);
-            }
+            for (int i = 0; i < 3; i++) y.p[i] = fma(sa, y.p[i], f * y.r[i]);
             *kind = CORR_SPLIT;
             return it + ks;
         }
