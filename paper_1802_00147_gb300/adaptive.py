@@ -159,7 +159,8 @@ def cheapest(points, mis_max):
 
 
 def boundary_study(n=512, t_end=1.0e4, thr=5.8, stride=8, train_m=None, members=5, train_steps=30000,
-                   bands=(0.25, 0.5, 1.0, 1.5, 2.0, 3.0), spread_maxes=(0.25, 0.5, 1.0, 2.0, float("inf")),
+                   bands=(0.125, 0.25, 0.375, 0.5, 0.625, 0.75, 0.875, 1.0, 1.5, 2.0, 3.0),
+                   spread_maxes=(0.125, 0.25, 0.375, 0.5, 0.75, 1.0, 2.0, float("inf")),
                    mis_max=0.005, seed=11, target_clip=1.0, train_x0=None, **opts):
     """Surrogate-adaptive map against the no-learning coarse-grid map on the
     (theta1, theta2) plane of Sec. 3C, Fig. 7 (workloads.theta12_plane),
@@ -196,6 +197,7 @@ def boundary_study(n=512, t_end=1.0e4, thr=5.8, stride=8, train_m=None, members=
     # warm-up of every path on tiny inputs (first use of a PyTorch comparison
     # or masked index loads its kernels)
     training_set([train[:32]], [10.0], fields=fields, **opts)
+    training_set([train], [10.0], fields=fields, **opts)           # the training set's own batch size
     full_map(grid_d[:64], 10.0, thr=thr, **opts)
     baseline_map(grid_d[:64 * 64], 64, 64, 8, 10.0, thr=thr, **opts)
 

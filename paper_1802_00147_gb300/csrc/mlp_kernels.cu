@@ -51,21 +51,36 @@ struct Smem {
 
 size_t smem_bytes() { return sizeof(Smem); }
 
-// Training keeps the member's fp32 master weights in shared memory for the
-// whole run (the Adam moments live in registers) and reduces per-warp sums
-// of the batch's squared errors and output errors.
+// Training: one CTA of NT threads (8 warps, two per SM sub-partition) per
+// member.  The member's fp32 master weights stay in shared memory for the
+// whole run, with a bfloat16 copy of W2 that the Adam update refreshes; the
+// Adam moments live in registers.  The output layer is folded into the
+// epilogue of the second layer's contraction (row sums by warp shuffles), so
+// the second hidden layer never goes to shared memory.
+constexpr int NT = 256;
+constexpr int NWT = NT / 32;
+
 struct TrainSmem {
-    Smem s;
-    float P[NPARAM];        // fp32 master weights of this member
-    float err_part[TILE / 32];
-    float d3_part[TILE / 32];
-    float red_out[2][2][NH];           // output-layer / b2 gradient partials over two row halves
-    float red_in[2][NIN + 1][NH];      // first-layer gradient partials over two row halves
+    float P[NPARAM];                   // fp32 master weights of this member
+    float gW2[NH * NH];                // gradient of W2, [n][k]
+    float gout[2][NH];                 // gradients of w3 and b2
+    float z[TILE][NIN];
+    float t[TILE];
+    float H1f[TILE][LDF];
+    float D1f[TILE][LDF];
+    alignas(16) __nv_bfloat16 W2b[NH][LDB];   // 16-byte aligned rows for ldmatrix
+    alignas(16) __nv_bfloat16 H1b[TILE][LDB];
+    alignas(16) __nv_bfloat16 D2b[TILE][LDB];
+    float red_out[NWT][2][NH];         // per-warp partials of the w3 and b2 gradients
+    float red_in[4][NIN + 1][NH];      // first-layer gradient partials over four row quarters
+    float err_part[NWT];
+    float d3_part[NWT];
+    float gb3, loss;
 };
 
 size_t smem_train_bytes() { return sizeof(TrainSmem); }
 
-constexpr int PER_THREAD = (NPARAM + TILE - 1) / TILE;   // parameters per thread in the Adam update
+constexpr int PER_THREAD = (NPARAM + NT - 1) / NT;   // parameters per thread in the Adam update
 
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
 {
@@ -110,6 +125,52 @@ __device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const 
         "{%0,%1,%2,%3};"
         : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// The same fragments by ldmatrix (four 8 x 8 b16 matrices per instruction,
+// one 16-byte row address per lane; rows must be 16-byte aligned).  `ld` is
+// the row stride of the shared array in elements.
+__device__ __forceinline__ void ldsm_x4(uint32_t r[4], const __nv_bfloat16* p)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t r[4], const __nv_bfloat16* p)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a));
+}
+
+// A fragment of the 16 x 16 tile at (m0, k0) of A stored [m][k] (k contiguous).
+__device__ __forceinline__ void ldsm_a(uint32_t a[4], const __nv_bfloat16* S, int ld, int m0, int k0, int lane)
+{
+    const int mi = lane >> 3, rr = lane & 7;
+    ldsm_x4(a, S + (m0 + rr + 8 * (mi & 1)) * ld + k0 + 8 * (mi >> 1));
+}
+
+// A fragment of the tile at (m0, k0) of A stored transposed, S[k][m] (m contiguous).
+__device__ __forceinline__ void ldsm_a_t(uint32_t a[4], const __nv_bfloat16* S, int ld, int m0, int k0, int lane)
+{
+    const int mi = lane >> 3, rr = lane & 7;
+    ldsm_x4_t(a, S + (k0 + rr + 8 * (mi >> 1)) * ld + m0 + 8 * (mi & 1));
+}
+
+// B fragments of two adjacent 16 x 8 tiles at (k0, n0) and (k0, n0 + 8) of B
+// stored S[n][k] (k contiguous): b[0..1] the first tile, b[2..3] the second.
+__device__ __forceinline__ void ldsm_b2(uint32_t b[4], const __nv_bfloat16* S, int ld, int k0, int n0, int lane)
+{
+    const int mi = lane >> 3, rr = lane & 7;
+    ldsm_x4(b, S + (n0 + rr + 8 * (mi >> 1)) * ld + k0 + 8 * (mi & 1));
+}
+
+// The same for B stored S[k][n] (n contiguous).
+__device__ __forceinline__ void ldsm_b2_t(uint32_t b[4], const __nv_bfloat16* S, int ld, int k0, int n0, int lane)
+{
+    const int mi = lane >> 3, rr = lane & 7;
+    ldsm_x4_t(b, S + (k0 + rr + 8 * (mi & 1)) * ld + n0 + 8 * (mi >> 1));
 }
 
 // Positions of accumulator element i of a 16 x 8 tile for this lane.
@@ -191,203 +252,318 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-__global__ void __launch_bounds__(TILE) k_mlp_train(TrainArgs A)
+// Row of minibatch slot r at Adam step `step` of this launch: SplitMix64 of
+// (seed, member, step0 + step, r) modulo N (mode 0); rows 0..TILE-1 in
+// order (mode 1, clamped to row 0 past N).
+__device__ __forceinline__ long long batch_row(const TrainArgs& A, int member, int step, int r)
+{
+    if (A.mode == 1) return r < A.N ? r : 0;
+    const uint64_t h = splitmix64(A.seed ^ splitmix64(((uint64_t)member << 40) ^ ((uint64_t)(A.step0 + step) << 8) ^ (uint64_t)r));
+    return (long long)(h % (uint64_t)A.N);
+}
+
+// Gradient of parameter i once a step's reductions are complete: the
+// first layer's from its four row-quarter partials, the rest as stored.
+__device__ __forceinline__ float grad_at(const TrainSmem& ts, int i)
+{
+    if (i < OFF_W2) {
+        const int j = i < OFF_B1 ? i / NIN : i - OFF_B1;
+        const int c = i < OFF_B1 ? i % NIN : NIN;
+        return ((ts.red_in[0][c][j] + ts.red_in[1][c][j]) + ts.red_in[2][c][j]) + ts.red_in[3][c][j];
+    }
+    if (i < OFF_B2) return ts.gW2[i - OFF_W2];
+    if (i < OFF_W3) return ts.gout[1][i - OFF_B2];
+    if (i < OFF_B3) return ts.gout[0][i - OFF_W3];
+    return ts.gb3;
+}
+
+__global__ void __launch_bounds__(NT) k_mlp_train(TrainArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TrainSmem& ts = *reinterpret_cast<TrainSmem*>(smem_raw);
-    Smem& s = ts.s;
     const int member = blockIdx.x;
-    const int r = threadIdx.x, lane = r & 31, warp = r >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, q = lane & 3;
     float* P = A.params + (size_t)member * NPARAM;
     float* M = A.adam_m + (size_t)member * NPARAM;
     float* V = A.adam_v + (size_t)member * NPARAM;
     const int nsteps = A.mode == 1 ? 1 : A.steps;
+    const float* W1 = ts.P + OFF_W1;
+    const float* b1 = ts.P + OFF_B1;
+    const float* b2 = ts.P + OFF_B2;
+    const float* w3 = ts.P + OFF_W3;
 
-    // master weights to shared memory, this thread's Adam moments to registers
-    // (parameter i = r + TILE k)
+    // master weights (and the bfloat16 W2) to shared memory, this thread's
+    // Adam moments to registers (parameter i = tid + NT k)
     float m_reg[PER_THREAD], v_reg[PER_THREAD];
 #pragma unroll
     for (int k = 0; k < PER_THREAD; k++) {
-        const int i = r + TILE * k;
+        const int i = tid + NT * k;
         if (i < NPARAM) {
-            ts.P[i] = P[i];
+            const float p = P[i];
+            ts.P[i] = p;
+            if (i >= OFF_W2 && i < OFF_B2) ts.W2b[(i - OFF_W2) / NH][(i - OFF_W2) % NH] = __float2bfloat16_rn(p);
             m_reg[k] = M[i];
             v_reg[k] = V[i];
         }
     }
-    __syncthreads();
+    // the first minibatch row of slot tid; later rows are fetched one step ahead
+    float xr[NIN], yr = 0.f;
+    if (tid < TILE) {
+        const long long idx = batch_row(A, member, 0, tid);
+#pragma unroll
+        for (int i = 0; i < NIN; i++) xr[i] = A.X[idx * NIN + i];
+        yr = A.Y[idx];
+    }
 
     for (int step = 0; step < nsteps; step++) {
-        load_params(s, ts.P);
-        // minibatch rows
-        long long idx;
-        if (A.mode == 1) idx = r < A.N ? r : 0;
-        else {
-            const uint64_t h = splitmix64(A.seed ^ splitmix64(((uint64_t)member << 40) ^ ((uint64_t)(A.step0 + step) << 8) ^ (uint64_t)r));
-            idx = (long long)(h % (uint64_t)A.N);
-        }
+        // (1) this step's rows to shared memory, the next step's loads issued
+        if (tid < TILE) {
 #pragma unroll
-        for (int i = 0; i < NIN; i++) s.z[r][i] = (A.X[idx * NIN + i] - A.center[i]) / A.scale[i];
-        s.t[r] = A.Y[idx];
-        __syncthreads();
-        const float y = forward_tile(s);
-        const float e = y - s.t[r];
-        const float d3 = 2.f * e / (float)TILE;
-        s.d3[r] = d3;
-        s.err2[r] = e * e;
-        {
-            const float pe = warp_sum(e * e), pd = warp_sum(d3);
-            if (lane == 0) {
-                ts.err_part[warp] = pe;
-                ts.d3_part[warp] = pd;
+            for (int i = 0; i < NIN; i++) ts.z[tid][i] = (xr[i] - A.center[i]) / A.scale[i];
+            ts.t[tid] = yr;
+            if (step + 1 < nsteps) {
+                const long long idx = batch_row(A, member, step + 1, tid);
+#pragma unroll
+                for (int i = 0; i < NIN; i++) xr[i] = A.X[idx * NIN + i];
+                yr = A.Y[idx];
             }
         }
-        for (int n = 0; n < NH; n++) {
-            const float h2 = s.H2f[r][n];
-            s.D2b[r][n] = __float2bfloat16_rn(d3 * s.w3[n] * (1.f - h2 * h2));
+        __syncthreads();
+        // (2) layer 1 (K = 4, plain FP32): lane <-> hidden unit, warp <-> 32 rows
+        {
+            const int j = lane + 32 * (warp & 1);
+            float wj[NIN];
+#pragma unroll
+            for (int i = 0; i < NIN; i++) wj[i] = W1[j * NIN + i];
+            const float bj = b1[j];
+            const int row0 = 32 * (warp >> 1);
+            for (int row = row0; row < row0 + 32; row++) {
+                float a = bj;
+#pragma unroll
+                for (int i = 0; i < NIN; i++) a = fmaf(wj[i], ts.z[row][i], a);
+                const float h = tanhf(a);
+                ts.H1f[row][j] = h;
+                ts.H1b[row][j] = __float2bfloat16_rn(h);
+            }
         }
         __syncthreads();
-        // output layer and b2 gradients (reductions over the batch): thread r
-        // sums unit r % NH over half r / NH of the rows; halves combined below
+        // (3) layer 2 and the output: Z2[t][n] = sum_k H1[t][k] W2[n][k], warp
+        // owns rows [16 warp, +16); h2 = tanh(Z2 + b2) stays in registers
         {
-            static_assert(TILE == 2 * NH, "two row halves per hidden unit");
-            const int u = r % NH, half = r / NH;
-            float gw3 = 0.f, gb2 = 0.f;
-            for (int t = half * (TILE / 2); t < (half + 1) * (TILE / 2); t++) {
-                gw3 = fmaf(s.d3[t], s.H2f[t][u], gw3);
-                gb2 += __bfloat162float(s.D2b[t][u]);
-            }
-            ts.red_out[half][0][u] = gw3;
-            ts.red_out[half][1][u] = gb2;
-        }
-        // gW2[n][k] = sum_t D2[t][n] H1[t][k]: M = 64 (n), N = 64 (k), K = 128 (t); warp owns n-rows [16 warp, +16)
-        {
+            const int R0 = 16 * warp;
             float acc[8][4];
 #pragma unroll
             for (int nt = 0; nt < 8; nt++)
 #pragma unroll
                 for (int i = 0; i < 4; i++) acc[nt][i] = 0.f;
 #pragma unroll
+            for (int kk = 0; kk < NH / 16; kk++) {
+                uint32_t a[4];
+                ldsm_a(a, &ts.H1b[0][0], LDB, R0, 16 * kk, lane);
+#pragma unroll
+                for (int nt = 0; nt < 8; nt += 2) {
+                    uint32_t b[4];
+                    ldsm_b2(b, &ts.W2b[0][0], LDB, 16 * kk, 8 * nt, lane);     // (k, n) -> W2b[n][k]
+                    mma16816(acc[nt], a, b);
+                    mma16816(acc[nt + 1], a, b + 2);
+                }
+            }
+            // elements i = 0, 1 are row R0 + g, i = 2, 3 row R0 + g + 8; columns 8 nt + 2 q + (i & 1)
+            float ya = 0.f, yb = 0.f;
+#pragma unroll
+            for (int nt = 0; nt < 8; nt++)
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const int col = 8 * nt + c_col(lane, i);
+                    const float h = tanhf(acc[nt][i] + b2[col]);
+                    acc[nt][i] = h;
+                    if (i < 2) ya = fmaf(w3[col], h, ya);
+                    else yb = fmaf(w3[col], h, yb);
+                }
+            ya += __shfl_xor_sync(0xffffffffu, ya, 1);
+            ya += __shfl_xor_sync(0xffffffffu, ya, 2);
+            yb += __shfl_xor_sync(0xffffffffu, yb, 1);
+            yb += __shfl_xor_sync(0xffffffffu, yb, 2);
+            const float b3 = ts.P[OFF_B3];
+            const float ea = (ya + b3) - ts.t[R0 + g], eb = (yb + b3) - ts.t[R0 + g + 8];
+            const float d3a = 2.f * ea / (float)TILE, d3b = 2.f * eb / (float)TILE;
+            // output-layer error through tanh: D2 = d3 w3 (1 - h2^2), rounded to bfloat16
+            // for the two contractions below; w3 and b2 gradient partials over the warp's rows
+            float pw[8][2], pb[8][2];
+#pragma unroll
+            for (int nt = 0; nt < 8; nt++) {
+                const int c0 = 8 * nt + 2 * q;
+                const float ha0 = acc[nt][0], ha1 = acc[nt][1], hb0 = acc[nt][2], hb1 = acc[nt][3];
+                const __nv_bfloat16 da0 = __float2bfloat16_rn(d3a * w3[c0] * (1.f - ha0 * ha0));
+                const __nv_bfloat16 da1 = __float2bfloat16_rn(d3a * w3[c0 + 1] * (1.f - ha1 * ha1));
+                const __nv_bfloat16 db0 = __float2bfloat16_rn(d3b * w3[c0] * (1.f - hb0 * hb0));
+                const __nv_bfloat16 db1 = __float2bfloat16_rn(d3b * w3[c0 + 1] * (1.f - hb1 * hb1));
+                *reinterpret_cast<uint32_t*>(&ts.D2b[R0 + g][c0]) = pack2(da0, da1);
+                *reinterpret_cast<uint32_t*>(&ts.D2b[R0 + g + 8][c0]) = pack2(db0, db1);
+                pw[nt][0] = fmaf(d3b, hb0, d3a * ha0);
+                pw[nt][1] = fmaf(d3b, hb1, d3a * ha1);
+                pb[nt][0] = __bfloat162float(da0) + __bfloat162float(db0);
+                pb[nt][1] = __bfloat162float(da1) + __bfloat162float(db1);
+            }
+            // sums over the warp's 8 row pairs (lanes of equal q) by recursive
+            // halving: at lane-mask bit b the lane keeps the half of its 2^(3-b) x 2
+            // partials selected by bit b of g and adds its partner's; afterwards it
+            // holds the sums of partial index c = 2 nt + j with c >> 1 =
+            // 4 (g & 1) + 2 ((g >> 1) & 1) + ((g >> 2) & 1)
+            float* vw = &pw[0][0];
+            float* vb = &pb[0][0];
+#pragma unroll
+            for (int lvl = 0, half = 8; lvl < 3; lvl++, half >>= 1) {
+                const bool hi = (g >> lvl) & 1;
+#pragma unroll
+                for (int i = 0; i < half; i++) {
+                    const float sw = __shfl_xor_sync(0xffffffffu, hi ? vw[i] : vw[i + half], 4 << lvl);
+                    const float sb = __shfl_xor_sync(0xffffffffu, hi ? vb[i] : vb[i + half], 4 << lvl);
+                    vw[i] = (hi ? vw[i + half] : vw[i]) + sw;
+                    vb[i] = (hi ? vb[i + half] : vb[i]) + sb;
+                }
+            }
+            {
+                const int nt = 4 * (g & 1) + 2 * ((g >> 1) & 1) + ((g >> 2) & 1);
+#pragma unroll
+                for (int j = 0; j < 2; j++) {
+                    ts.red_out[warp][0][8 * nt + 2 * q + j] = vw[j];
+                    ts.red_out[warp][1][8 * nt + 2 * q + j] = vb[j];
+                }
+            }
+            const float le = warp_sum(q == 0 ? fmaf(ea, ea, eb * eb) : 0.f);
+            const float ld = warp_sum(q == 0 ? d3a + d3b : 0.f);
+            if (lane == 0) {
+                ts.err_part[warp] = le;
+                ts.d3_part[warp] = ld;
+            }
+        }
+        __syncthreads();
+        // (4) gW2[n][k] = sum_t D2[t][n] H1[t][k] (M = 64 n, N = 64 k, K = 128 t; warp owns
+        // n-rows [16 (warp & 3), +16) and k-columns [32 (warp >> 2), +32)), then
+        // D1[t][k] = (sum_n D2[t][n] W2[n][k]) (1 - H1[t][k]^2) (M = 128 t, N = 64 k, K = 64 n;
+        // warp owns rows [16 warp, +16))
+        {
+            const int n0 = 16 * (warp & 3), nt0 = 4 * (warp >> 2);
+            float acc[4][4];
+#pragma unroll
+            for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+                for (int i = 0; i < 4; i++) acc[nt][i] = 0.f;
+#pragma unroll
             for (int kk = 0; kk < TILE / 16; kk++) {
                 uint32_t a[4];
-                load_a(a, &s.D2b[0][0], 1, LDB, 16 * warp, 16 * kk, lane);     // (n, t) -> D2b[t][n]
+                ldsm_a_t(a, &ts.D2b[0][0], LDB, n0, 16 * kk, lane);              // (n, t) -> D2b[t][n]
 #pragma unroll
-                for (int nt = 0; nt < 8; nt++) {
-                    uint32_t b[2];
-                    load_b(b, &s.H1b[0][0], LDB, 1, 16 * kk, 8 * nt, lane);    // (t, k) -> H1b[t][k]
+                for (int nt = 0; nt < 4; nt += 2) {
+                    uint32_t b[4];
+                    ldsm_b2_t(b, &ts.H1b[0][0], LDB, 16 * kk, 8 * (nt0 + nt), lane);   // (t, k) -> H1b[t][k]
                     mma16816(acc[nt], a, b);
+                    mma16816(acc[nt + 1], a, b + 2);
+                }
+            }
+#pragma unroll
+            for (int nt = 0; nt < 4; nt++)
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+                    ts.gW2[(n0 + c_row(lane, i)) * NH + 8 * (nt0 + nt) + c_col(lane, i)] = acc[nt][i];
+        }
+        {
+            const int R0 = 16 * warp;
+            float acc[8][4];
+#pragma unroll
+            for (int nt = 0; nt < 8; nt++)
+#pragma unroll
+                for (int i = 0; i < 4; i++) acc[nt][i] = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < NH / 16; kk++) {
+                uint32_t a[4];
+                ldsm_a(a, &ts.D2b[0][0], LDB, R0, 16 * kk, lane);
+#pragma unroll
+                for (int nt = 0; nt < 8; nt += 2) {
+                    uint32_t b[4];
+                    ldsm_b2_t(b, &ts.W2b[0][0], LDB, 16 * kk, 8 * nt, lane);   // (n, k) -> W2b[n][k]
+                    mma16816(acc[nt], a, b);
+                    mma16816(acc[nt + 1], a, b + 2);
                 }
             }
 #pragma unroll
             for (int nt = 0; nt < 8; nt++)
 #pragma unroll
                 for (int i = 0; i < 4; i++) {
-                    const int n = 16 * warp + c_row(lane, i), k = 8 * nt + c_col(lane, i);
-                    s.grad[OFF_W2 + n * NH + k] = acc[nt][i];
+                    const int row = R0 + c_row(lane, i), col = 8 * nt + c_col(lane, i);
+                    const float h1 = ts.H1f[row][col];
+                    ts.D1f[row][col] = acc[nt][i] * (1.f - h1 * h1);
                 }
         }
-        // D1[t][k] = (sum_n D2[t][n] W2[n][k]) (1 - H1[t][k]^2): M = 128, N = 64, K = 64
-        {
-            float acc[2][8][4];
+        // w3 and b2 gradients over the warps' partials; b3 and the loss
+        if (tid < 2 * NH) {
+            const int col = tid & (NH - 1), which = tid >> 6;
+            float s = 0.f;
 #pragma unroll
-            for (int mt = 0; mt < 2; mt++)
+            for (int w = 0; w < NWT; w++) s += ts.red_out[w][which][col];
+            ts.gout[which][col] = s;
+        } else if (tid == 2 * NH) {
+            float gb3 = 0.f, l = 0.f;
 #pragma unroll
-                for (int nt = 0; nt < 8; nt++)
-#pragma unroll
-                    for (int i = 0; i < 4; i++) acc[mt][nt][i] = 0.f;
-#pragma unroll
-            for (int kk = 0; kk < NH / 16; kk++) {
-                uint32_t a[2][4];
-#pragma unroll
-                for (int mt = 0; mt < 2; mt++) load_a(a[mt], &s.D2b[0][0], LDB, 1, 32 * warp + 16 * mt, 16 * kk, lane);
-#pragma unroll
-                for (int nt = 0; nt < 8; nt++) {
-                    uint32_t b[2];
-                    load_b(b, &s.W2b[0][0], LDB, 1, 16 * kk, 8 * nt, lane);    // (n, k) -> W2b[n][k]
-#pragma unroll
-                    for (int mt = 0; mt < 2; mt++) mma16816(acc[mt][nt], a[mt], b);
-                }
+            for (int w = 0; w < NWT; w++) {
+                gb3 += ts.d3_part[w];
+                l += ts.err_part[w];
             }
-#pragma unroll
-            for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-                for (int nt = 0; nt < 8; nt++)
-#pragma unroll
-                    for (int i = 0; i < 4; i++) {
-                        const int row = 32 * warp + 16 * mt + c_row(lane, i), col = 8 * nt + c_col(lane, i);
-                        const float h1 = s.H1f[row][col];
-                        s.D1f[row][col] = acc[mt][nt][i] * (1.f - h1 * h1);
-                    }
+            ts.gb3 = gb3;
+            ts.loss = l / (float)TILE;
         }
         __syncthreads();
-        // first-layer gradients: gW1[j][i] = sum_t D1[t][j] z[t][i], gb1[j] = sum_t D1[t][j];
-        // thread r sums unit r % NH over half r / NH of the rows
+        // (5) first-layer gradients: gW1[j][i] = sum_t D1[t][j] z[t][i], gb1[j] = sum_t D1[t][j];
+        // thread sums unit tid % 64 over row quarter tid / 64
         {
-            const int j = r % NH, half = r / NH;
-            float g[NIN + 1];
+            const int j = tid & (NH - 1), quarter = tid >> 6;
+            float gz[NIN + 1];
 #pragma unroll
-            for (int i = 0; i <= NIN; i++) g[i] = 0.f;
-            for (int t = half * (TILE / 2); t < (half + 1) * (TILE / 2); t++) {
-                const float d = s.D1f[t][j];
+            for (int i = 0; i <= NIN; i++) gz[i] = 0.f;
+            for (int t = quarter * (TILE / 4); t < (quarter + 1) * (TILE / 4); t++) {
+                const float d = ts.D1f[t][j];
 #pragma unroll
-                for (int i = 0; i < NIN; i++) g[i] = fmaf(d, s.z[t][i], g[i]);
-                g[NIN] += d;
+                for (int i = 0; i < NIN; i++) gz[i] = fmaf(d, ts.z[t][i], gz[i]);
+                gz[NIN] += d;
             }
 #pragma unroll
-            for (int i = 0; i <= NIN; i++) ts.red_in[half][i][j] = g[i];
-        }
-        __syncthreads();
-        // combine the two row halves
-        if (r < NH) {
-            s.grad[OFF_W3 + r] = ts.red_out[0][0][r] + ts.red_out[1][0][r];
-            s.grad[OFF_B2 + r] = ts.red_out[0][1][r] + ts.red_out[1][1][r];
-#pragma unroll
-            for (int i = 0; i < NIN; i++) s.grad[OFF_W1 + r * NIN + i] = ts.red_in[0][i][r] + ts.red_in[1][i][r];
-            s.grad[OFF_B1 + r] = ts.red_in[0][NIN][r] + ts.red_in[1][NIN][r];
-        } else if (r == NH) {
-            float gb3 = 0.f;
-#pragma unroll
-            for (int w = 0; w < TILE / 32; w++) gb3 += ts.d3_part[w];
-            s.grad[OFF_B3] = gb3;
+            for (int i = 0; i <= NIN; i++) ts.red_in[quarter][i][j] = gz[i];
         }
         __syncthreads();
         if (A.mode == 1) {
-            for (int i = r; i < NPARAM; i += TILE) A.grad_out[(size_t)member * NPARAM + i] = s.grad[i];
-            if (r == 0) {
-                float l = 0.f;
-#pragma unroll
-                for (int w = 0; w < TILE / 32; w++) l += ts.err_part[w];
-                A.loss_out[member] = l / (float)TILE;
-            }
+            for (int i = tid; i < NPARAM; i += NT) A.grad_out[(size_t)member * NPARAM + i] = grad_at(ts, i);
+            if (tid == 0) A.loss_out[member] = ts.loss;
             return;
         }
-        // Adam (Kingma & Ba 2015), bias-corrected moments
+        // (6) Adam (Kingma & Ba 2015), bias-corrected moments; the bfloat16 W2
+        // follows its master weight.  The next step's first shared-memory
+        // reads of P and W2b come after its first barrier.
         const int tstep = A.step0 + step + 1;
-        const float c1 = 1.f - powf(0.9f, (float)tstep), c2 = 1.f - powf(0.999f, (float)tstep);
+        // (the bias corrections' reciprocals once per step)
+        const float ic1 = 1.f / (1.f - powf(0.9f, (float)tstep)), ic2 = 1.f / (1.f - powf(0.999f, (float)tstep));
 #pragma unroll
         for (int k = 0; k < PER_THREAD; k++) {
-            const int i = r + TILE * k;
+            const int i = tid + NT * k;
             if (i < NPARAM) {
-                const float g = s.grad[i];
-                const float m = 0.9f * m_reg[k] + 0.1f * g;
-                const float v = 0.999f * v_reg[k] + 0.001f * g * g;
+                const float gr = grad_at(ts, i);
+                const float m = 0.9f * m_reg[k] + 0.1f * gr;
+                const float v = 0.999f * v_reg[k] + 0.001f * gr * gr;
                 m_reg[k] = m;
                 v_reg[k] = v;
-                ts.P[i] = ts.P[i] - A.lr * (m / c1) / (sqrtf(v / c2) + 1e-8f);
+                const float p = ts.P[i] - A.lr * (m * ic1) / (sqrtf(v * ic2) + 1e-8f);
+                ts.P[i] = p;
+                if (i >= OFF_W2 && i < OFF_B2) ts.W2b[(i - OFF_W2) / NH][(i - OFF_W2) % NH] = __float2bfloat16_rn(p);
             }
         }
-        if (A.loss_hist && r == 0) {
-            float l = 0.f;
-#pragma unroll
-            for (int w = 0; w < TILE / 32; w++) l += ts.err_part[w];
-            A.loss_hist[(size_t)member * A.steps + step] = l / (float)TILE;
-        }
-        __syncthreads();
+        if (A.loss_hist && tid == 0) A.loss_hist[(size_t)member * A.steps + step] = ts.loss;
     }
+    __syncthreads();
     // the trained weights and moments back to the handle
 #pragma unroll
     for (int k = 0; k < PER_THREAD; k++) {
-        const int i = r + TILE * k;
+        const int i = tid + NT * k;
         if (i < NPARAM) {
             P[i] = ts.P[i];
             M[i] = m_reg[k];
@@ -616,7 +792,7 @@ cudaError_t launch_train(const TrainArgs& A, int members, cudaStream_t st)
     const size_t sm = smem_train_bytes();
     cudaError_t e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_mlp_train<<<members, TILE, sm, st>>>(A);
+    k_mlp_train<<<members, NT, sm, st>>>(A);
     return cudaGetLastError();
 }
 
