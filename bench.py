@@ -67,13 +67,13 @@ FP64_PEAK_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # for the kernel sources they were taken with: reported as null once any of
 # these files differs from the recorded SHA-256.
 TRAFFIC_SOURCES = {
-    "paper_1802_00147_gb300/csrc/pn_device.cuh": "e22fe987286c9d7ba0e9e1905bce0a69aaf9bcb652a8aaae78be78dd8fb03e9f",
+    "paper_1802_00147_gb300/csrc/pn_device.cuh": "842840ddc516186f903346f6170f158988a3850a8ae369f0bc67e598617b7c45",
     "paper_1802_00147_gb300/csrc/pn_kernels.cu": "84935a0453daa6cb20d1bc396c23cef73dd06325d31f203d88ac27a8ea2dde4e",
     "paper_1802_00147_gb300/csrc/pn_kernels.cuh": "b96896c16a4511134e2587dfacf70a1be233dedbea094e41872b6caf91cdbc00",
 }
 # ncu --cache-control none, as the bench runs: the set-up kernels leave the
 # state in L2 right before the run.
-TRAFFIC_BYTES_PER_RUN = {3: 7345920 + 42324992}      # compacting schedule, chunk 62 (7 epochs)
+TRAFFIC_BYTES_PER_RUN = {3: 6599168 + 40400128}      # compacting schedule, chunk 62 (7 epochs)
 
 
 def traffic_per_run(schedule):
@@ -663,6 +663,30 @@ def run_ours(args, rank, world, local_rank):
     scan.close()
 
 
+def run_profile_surrogate(steps):
+    """Surrogate training alone, for ncu runs: 5 members on 20,000 seeded
+    synthetic rows (the scan's input ranges, a smooth target); one untimed
+    launch of 200 Adam steps, then one timed launch of `steps`."""
+    import torch
+    import paper_1802_00147_gb300 as pn
+    from paper_1802_00147_gb300 import build as pnbuild
+    pnbuild.build()
+    rng = np.random.default_rng(4)
+    X = np.stack([rng.uniform(10, 50, 20000), rng.uniform(0, np.pi, 20000), rng.uniform(0.1, 1, 20000),
+                  rng.uniform(0, 1, 20000)], axis=1).astype(np.float32)
+    y = (np.sin(X[:, 0] / 10) + 2.0).astype(np.float32)
+    Xd, yd = torch.as_tensor(X, device="cuda"), torch.as_tensor(y, device="cuda")
+    with pn.Surrogate(members=5, seed=11) as sur:
+        sur.train(Xd, yd, steps=200, lr=3e-3, seed=5)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hist = sur.train(Xd, yd, steps=steps, lr=3e-3, seed=6)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    print(json.dumps({"profile_surrogate": True, "members": 5, "steps": steps, "seconds": dt,
+                      "us_per_step": dt / steps * 1e6, "loss_last": float(hist[:, -1].mean())}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -684,7 +708,12 @@ def main():
                     help="--profile runs with the 2.5PN radiation reaction")
     ap.add_argument("--uneven", action="store_true",
                     help="--profile runs on the uneven batch (--orbits of it; FLI cap 12)")
+    ap.add_argument("--profile-surrogate", type=int, default=0, metavar="STEPS",
+                    help="time STEPS steps of surrogate training alone (5 members), for ncu runs")
     args = ap.parse_args()
+    if args.profile_surrogate:
+        run_profile_surrogate(args.profile_surrogate)
+        return
     spawn = launch_check(args.gpus, os.environ)
     if spawn:
         # one process per GPU: re-run this script under torch.distributed.run
