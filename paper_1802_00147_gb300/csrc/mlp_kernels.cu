@@ -29,6 +29,8 @@ namespace mlp {
 constexpr int TILE = 128;        // rows (cells or samples) per CTA
 constexpr int LDB = NH + 8;      // padded bf16 row stride
 constexpr int LDF = NH + 1;      // padded fp32 row stride
+constexpr int LDT = NH + 8;      // fp32 row stride of the training arrays written from MMA fragments
+                                 // (8-byte pairs of a half-warp land in distinct banks)
 
 struct Smem {
     float W1[NH * NIN];
@@ -62,12 +64,12 @@ constexpr int NWT = NT / 32;
 
 struct TrainSmem {
     float P[NPARAM];                   // fp32 master weights of this member
-    float gW2[NH * NH];                // gradient of W2, [n][k]
+    alignas(16) float gW2[NH][LDT];    // gradient of W2, [n][k]
     float gout[2][NH];                 // gradients of w3 and b2
     float z[TILE][NIN];
     float t[TILE];
-    float H1f[TILE][LDF];
-    float D1f[TILE][LDF];
+    alignas(16) float H1f[TILE][LDT];
+    alignas(16) float D1f[TILE][LDT];
     alignas(16) __nv_bfloat16 W2b[NH][LDB];   // 16-byte aligned rows for ldmatrix
     alignas(16) __nv_bfloat16 H1b[TILE][LDB];
     alignas(16) __nv_bfloat16 D2b[TILE][LDB];
@@ -271,7 +273,7 @@ __device__ __forceinline__ float grad_at(const TrainSmem& ts, int i)
         const int c = i < OFF_B1 ? i % NIN : NIN;
         return ((ts.red_in[0][c][j] + ts.red_in[1][c][j]) + ts.red_in[2][c][j]) + ts.red_in[3][c][j];
     }
-    if (i < OFF_B2) return ts.gW2[i - OFF_W2];
+    if (i < OFF_B2) return ts.gW2[(i - OFF_W2) / NH][(i - OFF_W2) % NH];
     if (i < OFF_W3) return ts.gout[1][i - OFF_B2];
     if (i < OFF_B3) return ts.gout[0][i - OFF_W3];
     return ts.gb3;
@@ -463,11 +465,13 @@ __global__ void __launch_bounds__(NT) k_mlp_train(TrainArgs A)
                     mma16816(acc[nt + 1], a, b + 2);
                 }
             }
+            // accumulator pairs (i, i + 1) are adjacent columns of one row
 #pragma unroll
             for (int nt = 0; nt < 4; nt++)
 #pragma unroll
-                for (int i = 0; i < 4; i++)
-                    ts.gW2[(n0 + c_row(lane, i)) * NH + 8 * (nt0 + nt) + c_col(lane, i)] = acc[nt][i];
+                for (int i = 0; i < 4; i += 2)
+                    *reinterpret_cast<float2*>(&ts.gW2[n0 + c_row(lane, i)][8 * (nt0 + nt) + c_col(lane, i)]) =
+                        make_float2(acc[nt][i], acc[nt][i + 1]);
         }
         {
             const int R0 = 16 * warp;
@@ -491,10 +495,11 @@ __global__ void __launch_bounds__(NT) k_mlp_train(TrainArgs A)
 #pragma unroll
             for (int nt = 0; nt < 8; nt++)
 #pragma unroll
-                for (int i = 0; i < 4; i++) {
+                for (int i = 0; i < 4; i += 2) {
                     const int row = R0 + c_row(lane, i), col = 8 * nt + c_col(lane, i);
-                    const float h1 = ts.H1f[row][col];
-                    ts.D1f[row][col] = acc[nt][i] * (1.f - h1 * h1);
+                    const float2 h1 = *reinterpret_cast<const float2*>(&ts.H1f[row][col]);
+                    *reinterpret_cast<float2*>(&ts.D1f[row][col]) =
+                        make_float2(acc[nt][i] * (1.f - h1.x * h1.x), acc[nt][i + 1] * (1.f - h1.y * h1.y));
                 }
         }
         // w3 and b2 gradients over the warps' partials; b3 and the loss
