@@ -433,13 +433,24 @@ __global__ void __launch_bounds__(128) k_integrate_pair(DevState S, RunCfg rc)
 
 // ------------------------------------------- persistent work-queue integrator
 // Tasks are (chunk c, group g): advance the 32 orbits of group g (one warp)
-// through steps [c K, (c+1) K) of the run.  Warps claim tasks in order from
-// one atomic counter; task (c, g) waits for (c-1, g), which was claimed
-// earlier by a running warp, so the oldest unfinished task can always make
-// progress.  Because every group advances chunk by chunk, all SM
-// sub-partitions stay busy until the last chunk, whatever the number of
-// orbits.  Every wait is bounded in time (rc.wait_limit_ns, global timer);
-// on expiry the kernel sets the error flag and all warps return.
+// through steps [c K, (c+1) K) of the run; task (c, g) waits for (c-1, g).
+// How the W resident warps get their tasks depends on the G groups:
+// - G >= 2W: warps claim tasks from one atomic counter in chunk-major order,
+//   so every group advances chunk by chunk and the load balances itself.  A
+//   group's next chunk is claimed about G / W task times after its previous
+//   one, so with G >= 2W the claiming warp rarely finds it unfinished.
+// - G < 2W: that claim order would make warps wait on their predecessors'
+//   chunks.  Instead the G x (chunks) units, taken group by group, are cut
+//   into min(G, W) contiguous shares of equal size (to one unit), one per
+//   warp (McNaughton's wrap-around rule).  A group cut between the end of
+//   warp w's share and the start of warp w + 1's runs its first chunks first
+//   on warp w and its last chunks last on warp w + 1, which is after them
+//   whenever every share is at least one group long (G >= W); for G < W each
+//   warp runs one whole group.  Equal task times then leave no warp waiting.
+// Either way an orbit's steps and their arithmetic are the same, so results
+// are bit-identical.  Every wait is bounded in time (rc.wait_limit_ns,
+// global timer); on expiry the kernel sets the error flag and all warps
+// return.
 __device__ __forceinline__ int ld_acquire(const int* p)
 {
     int v;
@@ -479,13 +490,56 @@ __global__ void __launch_bounds__(128, MINB) k_integrate_queue(DevState S, RunCf
     const long long nchunks = (rc.nsteps + chunk - 1) / chunk;
     const unsigned long long ntasks = (unsigned long long)(groups * nchunks);
     const int32_t end_run = rc.final_step;
-    for (;;) {
-        unsigned long long task = 0;
-        if (lane == 0) task = (*(volatile int*)q.error) ? ntasks : atomicAdd(q.next, 1ull);
-        task = __shfl_sync(0xffffffffu, task, 0);
-        if (task >= ntasks) break;
-        const long long c = (long long)(task / (unsigned long long)groups);
-        const long long g = (long long)(task % (unsigned long long)groups);
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const bool claim = groups >= 2 * nwarps;
+    // static share (G < 2W): units [u0, u1) of the group-major order u = g nchunks + c,
+    // run as: the first pe chunks of the last group (if it is cut at u1), the whole
+    // groups, then the last ps chunks of the first group (if it is cut at u0)
+    const long long wshare = groups < nwarps ? groups : nwarps;
+    long long u0 = 0, len = 0, pe = 0, ps = 0, gA = 0, gB = 0, cA = 0;
+    if (!claim && gw < wshare) {
+        // balanced cut: every share has floor or ceil of units / wshare units, so
+        // at least nchunks when G >= W
+        const long long units = groups * nchunks;
+        u0 = gw * units / wshare;
+        const long long u1 = (gw + 1) * units / wshare;
+        len = u1 - u0;
+        if (len > 0) {
+            gA = u0 / nchunks;
+            cA = u0 % nchunks;
+            gB = (u1 - 1) / nchunks;
+            const long long cBend = (u1 - 1) % nchunks + 1;
+            pe = (gA < gB && cBend < nchunks) ? cBend : 0;
+            ps = (gA < gB && cA > 0) ? nchunks - cA : 0;
+        }
+    }
+    for (long long k = 0;; k++) {
+        long long c, g;
+        if (claim) {
+            unsigned long long task = 0;
+            if (lane == 0) task = (*(volatile int*)q.error) ? ntasks : atomicAdd(q.next, 1ull);
+            task = __shfl_sync(0xffffffffu, task, 0);
+            if (task >= ntasks) break;
+            c = (long long)(task / (unsigned long long)groups);
+            g = (long long)(task % (unsigned long long)groups);
+        } else {
+            int stop = 0;
+            if (lane == 0) stop = *(volatile int*)q.error;
+            stop = __shfl_sync(0xffffffffu, stop, 0);
+            if (k >= len || stop) break;
+            if (k < pe) {
+                g = gB;
+                c = k;
+            } else if (k < len - ps) {
+                const long long u = u0 + ps + (k - pe);
+                g = u / nchunks;
+                c = u % nchunks;
+            } else {
+                g = gA;
+                c = cA + (k - (len - ps));
+            }
+        }
         int ok = 1;
         if (c > 0 && lane == 0) {
             const unsigned long long t0 = globaltimer_ns();
