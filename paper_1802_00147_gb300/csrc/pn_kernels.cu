@@ -442,7 +442,8 @@ __global__ void __launch_bounds__(128) k_integrate_pair(DevState S, RunCfg rc)
 // - G < 2W: that claim order would make warps wait on their predecessors'
 //   chunks.  Instead the G x (chunks) units, taken group by group, are cut
 //   into min(G, W) contiguous shares of equal size (to one unit), one per
-//   warp (McNaughton's wrap-around rule).  A group cut between the end of
+//   warp (McNaughton's wrap-around rule), unless the run is one chunk long
+//   (then no task waits, and claims balance the whole groups).  A group cut between the end of
 //   warp w's share and the start of warp w + 1's runs its first chunks first
 //   on warp w and its last chunks last on warp w + 1, which is after them
 //   whenever every share is at least one group long (G >= W); for G < W each
@@ -470,6 +471,68 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
     return t;
 }
 
+// One task: advance group g through chunk c (after waiting for chunk c - 1),
+// then publish the group's progress.  Returns false when the kernel must stop
+// (a wait ran out).
+template <bool QM, bool SMEM, int RK, bool ROLLED, bool RR>
+__device__ __forceinline__ bool queue_task(const DevState& S, const RunCfg& rc, const QueueState& q, int chunk,
+                                           int use_order, long long nslots, long long c, long long g, int lane,
+                                           double* scoef, const double* hab)
+{
+    int ok = 1;
+    if (c > 0 && lane == 0) {
+        const unsigned long long t0 = globaltimer_ns();
+        while (ld_acquire(q.group_done + g) < c) {
+            if (globaltimer_ns() - t0 > rc.wait_limit_ns) {
+                atomicExch(q.error, 1);
+                ok = 0;
+                break;
+            }
+            __nanosleep(200);
+        }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) return false;
+    const int64_t slot = g * 32 + lane;
+    if (slot < nslots) {
+        const int64_t i = use_order ? (int64_t)__ldcg(S.order + slot) : slot;
+        const int32_t st = __ldcg(S.status + i);
+        if (st == ORBIT_RUNNING || (c == 0 && rc.first_epoch && st == ORBIT_DONE)) {
+            Orbit o;
+            load_orbit<true>(S, i, o);
+            o.status = ORBIT_RUNNING;
+            const long long e = (c + 1) * (long long)chunk;
+            const int32_t end = rc.nstep_base + (int32_t)(e < rc.nsteps ? e : rc.nsteps);
+            if (SMEM) {
+                const Coef cf = load_coef<true>(S, i, rc.flags);
+                volatile double* mine = scoef + threadIdx.x;
+#pragma unroll
+                for (int k = 0; k < NCOEF; k++) mine[k * (int)blockDim.x] = cf.v[k];
+                const CoefShared cs{mine, (int)blockDim.x};
+                advance<QM, RK, CoefShared, ROLLED>(rc, cs, o, end, hab);
+            } else {
+                const Coef cf = load_coef<true>(S, i, rc.flags);
+                double k8eta = 0.0;
+                if (RR) {
+                    const double beta = __ldcg(S.beta + i);
+                    k8eta = 1.6 * (beta / ((1.0 + beta) * (1.0 + beta)));
+                }
+                advance<QM, RK, Coef, ROLLED, RR>(rc, cf, o, end, hab, k8eta);
+            }
+            if (o.status == ORBIT_RUNNING && o.nstep == rc.final_step) o.status = ORBIT_DONE;
+            store_orbit(S, i, o);
+            if (RR) {
+                S.ref[0 * S.ld + i] = o.ref.E;
+                S.ref[1 * S.ld + i] = o.ref.J;
+            }
+        }
+    }
+    __threadfence();
+    __syncwarp();
+    if (lane == 0 && !(c == 0 && g == rc.stall_group)) st_release(q.group_done + g, (int)(c + 1));
+    return true;
+}
+
 // SMEM: keep the per-orbit constants in shared memory (one plane per constant)
 // instead of registers, which is what lets MINB = 3 blocks fit without spills.
 template <bool QM, int MINB, bool SMEM, int RK, bool ROLLED = false, bool RR = false>
@@ -488,109 +551,56 @@ __global__ void __launch_bounds__(128, MINB) k_integrate_queue(DevState S, RunCf
     const long long nslots = use_order ? (long long)__ldcg(q.count) : S.n;
     const long long groups = (nslots + 31) / 32;
     const long long nchunks = (rc.nsteps + chunk - 1) / chunk;
-    const unsigned long long ntasks = (unsigned long long)(groups * nchunks);
-    const int32_t end_run = rc.final_step;
+    const long long units = groups * nchunks;
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const bool claim = groups >= 2 * nwarps;
-    // static share (G < 2W): units [u0, u1) of the group-major order u = g nchunks + c,
-    // run as: the first pe chunks of the last group (if it is cut at u1), the whole
-    // groups, then the last ps chunks of the first group (if it is cut at u0)
     const long long wshare = groups < nwarps ? groups : nwarps;
-    long long u0 = 0, len = 0, pe = 0, ps = 0, gA = 0, gB = 0, cA = 0;
-    if (!claim && gw < wshare) {
-        // balanced cut: every share has floor or ceil of units / wshare units, so
-        // at least nchunks when G >= W
-        const long long units = groups * nchunks;
-        u0 = gw * units / wshare;
-        const long long u1 = (gw + 1) * units / wshare;
-        len = u1 - u0;
-        if (len > 0) {
-            gA = u0 / nchunks;
-            cA = u0 % nchunks;
-            gB = (u1 - 1) / nchunks;
-            const long long cBend = (u1 - 1) % nchunks + 1;
-            pe = (gA < gB && cBend < nchunks) ? cBend : 0;
-            ps = (gA < gB && cA > 0) ? nchunks - cA : 0;
-        }
-    }
-    for (long long k = 0;; k++) {
-        long long c, g;
-        if (claim) {
+    // claims when there are at least two groups per warp, or when the run is one
+    // chunk (no task waits; whole-group shares could not balance)
+    if (groups >= 2 * nwarps || nchunks == 1) {
+        for (;;) {
             unsigned long long task = 0;
-            if (lane == 0) task = (*(volatile int*)q.error) ? ntasks : atomicAdd(q.next, 1ull);
+            if (lane == 0) task = (*(volatile int*)q.error) ? (unsigned long long)units : atomicAdd(q.next, 1ull);
             task = __shfl_sync(0xffffffffu, task, 0);
-            if (task >= ntasks) break;
-            c = (long long)(task / (unsigned long long)groups);
-            g = (long long)(task % (unsigned long long)groups);
+            if (task >= (unsigned long long)units) break;
+            const long long c = (long long)(task / (unsigned long long)groups);
+            const long long g = (long long)(task % (unsigned long long)groups);
+            if (!queue_task<QM, SMEM, RK, ROLLED, RR>(S, rc, q, chunk, use_order, nslots, c, g, lane, scoef, hab))
+                break;
+        }
+        return;
+    }
+    // static share: units [u0, u1) of the group-major order u = g nchunks + c (a
+    // balanced cut: every share has floor or ceil of units / wshare units, so at
+    // least nchunks when G >= W), run as the first pe chunks of the last group
+    // (if it is cut at u1), the whole groups, then the last ps chunks of the
+    // first group (if it is cut at u0)
+    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (gw >= wshare) return;
+    const long long u0 = gw * units / wshare, u1 = (gw + 1) * units / wshare, len = u1 - u0;
+    if (len <= 0) return;
+    const long long gA = u0 / nchunks, cA = u0 % nchunks, gB = (u1 - 1) / nchunks;
+    const long long cBend = (u1 - 1) % nchunks + 1;
+    const long long pe = (gA < gB && cBend < nchunks) ? cBend : 0;
+    const long long ps = (gA < gB && cA > 0) ? nchunks - cA : 0;
+    for (long long k = 0; k < len; k++) {
+        int stop = 0;
+        if (lane == 0) stop = *(volatile int*)q.error;
+        stop = __shfl_sync(0xffffffffu, stop, 0);
+        if (stop) break;
+        long long c, g;
+        if (k < pe) {
+            g = gB;
+            c = k;
+        } else if (k < len - ps) {
+            const long long u = u0 + ps + (k - pe);
+            g = u / nchunks;
+            c = u % nchunks;
         } else {
-            int stop = 0;
-            if (lane == 0) stop = *(volatile int*)q.error;
-            stop = __shfl_sync(0xffffffffu, stop, 0);
-            if (k >= len || stop) break;
-            if (k < pe) {
-                g = gB;
-                c = k;
-            } else if (k < len - ps) {
-                const long long u = u0 + ps + (k - pe);
-                g = u / nchunks;
-                c = u % nchunks;
-            } else {
-                g = gA;
-                c = cA + (k - (len - ps));
-            }
+            g = gA;
+            c = cA + (k - (len - ps));
         }
-        int ok = 1;
-        if (c > 0 && lane == 0) {
-            const unsigned long long t0 = globaltimer_ns();
-            while (ld_acquire(q.group_done + g) < c) {
-                if (globaltimer_ns() - t0 > rc.wait_limit_ns) {
-                    atomicExch(q.error, 1);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(200);
-            }
-        }
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) break;
-        const int64_t slot = g * 32 + lane;
-        if (slot < nslots) {
-            const int64_t i = use_order ? (int64_t)__ldcg(S.order + slot) : slot;
-            const int32_t st = __ldcg(S.status + i);
-            if (st == ORBIT_RUNNING || (c == 0 && rc.first_epoch && st == ORBIT_DONE)) {
-                Orbit o;
-                load_orbit<true>(S, i, o);
-                o.status = ORBIT_RUNNING;
-                const long long e = (c + 1) * (long long)chunk;
-                const int32_t end = rc.nstep_base + (int32_t)(e < rc.nsteps ? e : rc.nsteps);
-                if (SMEM) {
-                    const Coef cf = load_coef<true>(S, i, rc.flags);
-                    volatile double* mine = scoef + threadIdx.x;
-#pragma unroll
-                    for (int k = 0; k < NCOEF; k++) mine[k * (int)blockDim.x] = cf.v[k];
-                    const CoefShared cs{mine, (int)blockDim.x};
-                    advance<QM, RK, CoefShared, ROLLED>(rc, cs, o, end, hab);
-                } else {
-                    const Coef cf = load_coef<true>(S, i, rc.flags);
-                    double k8eta = 0.0;
-                    if (RR) {
-                        const double beta = __ldcg(S.beta + i);
-                        k8eta = 1.6 * (beta / ((1.0 + beta) * (1.0 + beta)));
-                    }
-                    advance<QM, RK, Coef, ROLLED, RR>(rc, cf, o, end, hab, k8eta);
-                }
-                if (o.status == ORBIT_RUNNING && o.nstep == end_run) o.status = ORBIT_DONE;
-                store_orbit(S, i, o);
-                if (RR) {
-                    S.ref[0 * S.ld + i] = o.ref.E;
-                    S.ref[1 * S.ld + i] = o.ref.J;
-                }
-            }
-        }
-        __threadfence();
-        __syncwarp();
-        if (lane == 0 && !(c == 0 && g == rc.stall_group)) st_release(q.group_done + g, (int)(c + 1));
+        if (!queue_task<QM, SMEM, RK, ROLLED, RR>(S, rc, q, chunk, use_order, nslots, c, g, lane, scoef, hab))
+            break;
     }
 }
 
