@@ -73,7 +73,8 @@ TRAFFIC_SOURCES = {
 }
 # ncu --cache-control none, as the bench runs: the set-up kernels leave the
 # state in L2 right before the run.
-TRAFFIC_BYTES_PER_RUN = {3: 7070464 + 37494528}      # compacting schedule, chunk 62 (7 epochs)
+TRAFFIC_BYTES_PER_RUN = {3: 7070464 + 37494528,      # compacting schedule, chunk 62 (7 epochs)
+                         2: 5622528 + 43234304}      # work-queue schedule, chunk 125 (one launch)
 
 
 def traffic_per_run(schedule):

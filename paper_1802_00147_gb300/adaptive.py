@@ -179,9 +179,11 @@ def boundary_study(n=512, t_end=1.0e4, thr=5.8, stride=8, train_m=None, members=
     class depends only on the side of thr, and the FLIs of chaotic cells
     scatter widely (6-15 at t = 1e4), so an unclipped fit spends its
     capacity there.  Measured on the 512^2 plane at t = 1e4 (15.6 %
-    chaotic): unclipped, the cheapest point at <= 0.5 % marks 48.7 % of
-    the cells; clipped to +-2, 27.3 %; to +-1 with 30,000 steps, 23.7 %;
-    the coarse grid of stride 8, 22.7 %."""
+    chaotic) over the coarser sweep band in (0.25, 0.5, 1, 1.5, 2, 3),
+    spread_max in (0.25, 0.5, 1, 2, inf): unclipped, the cheapest point at
+    <= 0.5 % marks 48.7 % of the cells; clipped to +-2, 27.3 %; to +-1 with
+    30,000 steps, 23.7 %; the coarse grid of stride 8, 22.7 %.  Over the
+    default sweep: the surrogate 19.7 %, the coarse grid 22.5 %."""
     from . import workloads as W
     torch = _torch()
     fields = (W.TH1, W.TH2, W.X0, W.BETA)
