@@ -438,6 +438,25 @@ def test_schedules_chunks_and_pointers_are_bit_identical(pn):
     assert np.median(err) <= 1e-13 and err.max() <= 1e-9
 
 
+@pytest.mark.parametrize("n,block,bps", [(7000, 32, 1), (5000, 32, 1), (3000, 32, 1), (50000, 128, 0)])
+def test_work_queue_shares_are_bit_identical(pn, n, block, bps):
+    """The work queue's task assignment at every ratio of 32-orbit groups G to
+    resident warps W: one 32-thread block per SM (W = one warp per SM) puts
+    7,000 orbits at 1.44 groups per warp and 5,000 at 1.03 (fixed shares with
+    groups cut between two warps), 3,000 at 0.62 (one group per warp); the
+    default launch puts 50,000 orbits at about 1.3 (cut groups again).  Five
+    chunks, so that cut groups have chunks on both warps; the compacting
+    schedule re-partitions every epoch.  All against the static kernel."""
+    cells = W.subset(W.full_scan(), n, seed=9)[0]
+    steps = 200
+    a = gpu_run(pn, cells, steps, schedule=1)
+    for sched in (2, 3):
+        o = gpu_run(pn, cells, steps, schedule=sched, chunk_steps=40, block_size=block, blocks_per_sm=bps)
+        for k in ("states", "fli", "status", "t_stop", "integrals"):
+            np.testing.assert_array_equal(a[k], o[k], err_msg="schedule %d %s" % (sched, k))
+        assert o["summary"]["orbit_steps"] == a["summary"]["orbit_steps"]
+
+
 def test_qm_and_ablation_modes_are_bit_identical_across_kernels(pn):
     """The QM term and the correction ablations through the static kernel and
     the work-queue / compacting kernels (rolled and unrolled loops): same
