@@ -277,11 +277,11 @@ def test_ragged_batch_parity(pn):
 @pytest.mark.parametrize("schedule", [1, 2, 3])
 def test_full_scan_sampled_parity_bench_shape(pn, schedule):
     """The 314 x 314 scan in the launch configurations the benchmark times
-    (the autotuner's compacting schedule at chunk 62, the work-queue kernel;
-    and the static kernel), checked on a seeded sample of orbits the oracle
-    integrates one by one."""
+    (the autotuner's picks: the compacting schedule at chunk 62 and the
+    work-queue kernel at chunk 125; and the static kernel), checked on a
+    seeded sample of orbits the oracle integrates one by one."""
     cells = W.full_scan(seed=2)
-    g = gpu_run(pn, cells, 1000, schedule=schedule, chunk_steps=62 if schedule == 3 else 0, read_diag=True)
+    g = gpu_run(pn, cells, 1000, schedule=schedule, chunk_steps={1: 0, 2: 125, 3: 62}[schedule], read_diag=True)
     sub, idx = W.subset(cells, 64, seed=21)
     o, s_state, s_fli = oracle_sensitivity(sub, 1000)
     gs = {k: v[idx] for k, v in g.items() if isinstance(v, np.ndarray)}
