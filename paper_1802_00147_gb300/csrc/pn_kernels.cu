@@ -447,7 +447,9 @@ __global__ void __launch_bounds__(128) k_integrate_pair(DevState S, RunCfg rc)
 //   warp w's share and the start of warp w + 1's runs its first chunks first
 //   on warp w and its last chunks last on warp w + 1, which is after them
 //   whenever every share is at least one group long (G >= W); for G < W each
-//   warp runs one whole group.  Equal task times then leave no warp waiting.
+//   warp runs one whole group.  Equal task times then leave no warp waiting;
+//   otherwise warp w + 1 waits only on chunks that warp w runs first, and
+//   the grid is sized so that every warp is resident.
 // Either way an orbit's steps and their arithmetic are the same, so results
 // are bit-identical.  Every wait is bounded in time (rc.wait_limit_ns,
 // global timer); on expiry the kernel sets the error flag and all warps
