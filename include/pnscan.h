@@ -70,7 +70,8 @@ extern "C" {
 /* ---- integrator scheduling ---- */
 #define PNSCAN_SCHED_AUTO 0    /* use the autotuned choice (scan_autotune); else, at block 32, PAIR for
                                   n <= 128 x SMs and STATIC for n <= 256 x SMs (every orbit in one
-                                  wave of one-warp blocks); QUEUE otherwise */
+                                  wave of one-warp blocks); COMPACT otherwise, at 62-step tasks
+                                  unless chunk_steps is set */
 #define PNSCAN_SCHED_STATIC 1  /* one orbit per thread, one pass over the batch */
 #define PNSCAN_SCHED_QUEUE 2   /* persistent work-queue kernel over (32-orbit group, step chunk) tasks */
 #define PNSCAN_SCHED_COMPACT 3 /* the work queue over epochs of 256, 512, 1024, ... steps, the running
@@ -113,7 +114,7 @@ typedef struct scan_params {
     void *cuda_stream;       /* cudaStream_t for all work of the handle (default NULL) */
     int schedule;            /* PNSCAN_SCHED_* (default AUTO) */
     int block_size;          /* threads per block, 32..128, multiple of 32 (0: 128) */
-    int chunk_steps;         /* steps per work-queue task (0: 500) */
+    int chunk_steps;         /* steps per work-queue task (0: 500; 62 where AUTO picks COMPACT) */
     int epoch_steps;         /* compacting schedule: steps per epoch (0: 256, 512, 1024, ... doubling) */
     int blocks_per_sm;       /* resident blocks per SM for the queue kernel (0: occupancy maximum) */
     int register_variant;    /* RK4 queue kernel variant: 2 -- up to 255 registers/thread, 2 resident
