@@ -257,7 +257,8 @@ int scan_summary(scan_handle *h, scan_summary_t *out);
 /* Not in the paper (its launch shape is fixed, Sec. 3A).  Pick the
  * integrator schedule, block size, chunk length, blocks per SM and
  * register variant by timing candidate launches on a copy of the handle's current state for
- * `steps` steps (the state itself is left unchanged).  The choice is kept in
+ * `steps` steps (the state itself is left unchanged); candidates within 1 % of
+ * the fastest are timed again over 4 x `steps` steps.  The choice is kept in
  * the handle and used by later scan_run calls with schedule AUTO; it is also
  * written to the optional outputs.  Errors: ARG, STATE, CUDA. */
 int scan_autotune(scan_handle *h, int steps, int *schedule, int *block_size, int *chunk_steps,

@@ -661,23 +661,51 @@ int scan_autotune(scan_handle* h, int steps, int* schedule, int* block_size, int
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        const RunCfg rc = make_run(h, 1.0, steps);
-        for (const Cand& c : cands) {
-            if (cudaMemcpyAsync(blk, h->state_block, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess) {
-                r = PNSCAN_ERR_CUDA;
-                break;
-            }
+        // time one candidate over `n` steps on a fresh copy of the state
+        auto time_cand = [&](const Cand& c, const RunCfg& rcn, float* ms) -> int {
+            if (cudaMemcpyAsync(blk, h->state_block, bytes, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+                return PNSCAN_ERR_CUDA;
             cudaEventRecord(e0, h->stream);
-            r = launch_run(h, rc, c.sched, c.block, c.chunk, c.bps, c.minb, T, h->stream);
+            int rr2 = launch_run(h, rcn, c.sched, c.block, c.chunk, c.bps, c.minb, T, h->stream);
             cudaEventRecord(e1, h->stream);
-            if (r != PNSCAN_OK) break;
-            r = sync(h);
-            if (r != PNSCAN_OK) break;
+            if (rr2 != PNSCAN_OK) return rr2;
+            rr2 = sync(h);
+            if (rr2 != PNSCAN_OK) return rr2;
+            cudaEventElapsedTime(ms, e0, e1);
+            return PNSCAN_OK;
+        };
+        const RunCfg rc = make_run(h, 1.0, steps);
+        std::vector<float> times;
+        for (const Cand& c : cands) {
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
+            r = time_cand(c, rc, &ms);
+            if (r != PNSCAN_OK) break;
+            times.push_back(ms);
             if (ms < best) {
                 best = ms;
                 bestc = c;
+            }
+        }
+        // Shapes within 1 % of the best are re-timed over four times the trial:
+        // what separates them (e.g. compacting against plain work queue, whose
+        // order flips between 2,000 and 8,000 steps of the 314 x 314 scan) is
+        // often below a short trial's resolution.
+        if (r == PNSCAN_OK && steps <= (1 << 28)) {
+            std::vector<Cand> close;
+            for (size_t k = 0; k < times.size(); k++)
+                if (times[k] <= 1.01 * best) close.push_back(cands[k]);
+            if (close.size() > 1) {
+                const RunCfg rc4 = make_run(h, 1.0, 4 * steps);
+                double best4 = 1e300;
+                for (const Cand& c : close) {
+                    float ms = 0.f;
+                    r = time_cand(c, rc4, &ms);
+                    if (r != PNSCAN_OK) break;
+                    if (ms < best4) {
+                        best4 = ms;
+                        bestc = c;
+                    }
+                }
             }
         }
         cudaEventDestroy(e0);
