@@ -73,7 +73,9 @@ extern "C" {
                                   wave of one-warp blocks); COMPACT otherwise, at 62-step tasks
                                   unless chunk_steps is set */
 #define PNSCAN_SCHED_STATIC 1  /* one orbit per thread, one pass over the batch */
-#define PNSCAN_SCHED_QUEUE 2   /* persistent work-queue kernel over (32-orbit group, step chunk) tasks */
+#define PNSCAN_SCHED_QUEUE 2   /* persistent work-queue kernel over (32-orbit group, step chunk) tasks:
+                                  claimed in chunk-major order from two groups per resident warp up,
+                                  below that fixed contiguous shares per warp (bit-identical results) */
 #define PNSCAN_SCHED_COMPACT 3 /* the work queue over epochs of 256, 512, 1024, ... steps, the running
                                   orbits compacted into a dense list between epochs (uneven batches) */
 #define PNSCAN_SCHED_PAIR 4    /* two threads per orbit (main / shadow trajectory), one pass over the
